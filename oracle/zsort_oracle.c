@@ -1,0 +1,494 @@
+/*
+ * zsort_oracle.c -- plain, slow, sequential CPU restatement of zSort
+ * (Jain, Sabale, Shastri, Thakkar, Londhe: "zSort: Stable Distribution Sort
+ * using Z-Score Partitioning", arXiv 2605.14419).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call, link or
+ * load this file; only the tests, the package's smoke() check and the
+ * benchmark's CPU-baseline leg do.  It shares no code, header or constant
+ * with the CUDA library: every step below is written from the paper's text.
+ *
+ * Contents
+ *   oracle_stats             Alg. 1, statistics loops (min, mean, population sd)
+ *   oracle_zsort_pairs       Alg. 1 + zsortRec (section "Proposed Work"), on
+ *                            (uint64 key, uint32 payload) pairs, stable
+ *   oracle_zsort_segmented   the same, applied to each segment of a batch
+ *   oracle_key_from_i64/f64  order-preserving key encodings (not in the paper;
+ *                            definitions of two's-complement order and of the
+ *                            IEEE-754 totalOrder predicate)
+ *   oracle_splitmix64, oracle_sample_positions, oracle_pwl_train,
+ *   oracle_pwl_bucket        the learned monotone piecewise-linear bucket map
+ *                            that replaces the z-score map (not in the paper;
+ *                            restated from its written definition)
+ *
+ * Readings of the paper where it is silent or garbled (each repeated where
+ * it is used):
+ *   R1  Statistics are taken on d = key - min (exact unsigned subtraction,
+ *       then conversion to double).  The z-score is shift invariant, so the
+ *       map is unchanged; the paper's raw sum of 64-bit keys would overflow.
+ *   R2  The early exit "min == mean" is restated as "min == max".
+ *   R3  Eq. 1 adds z_min, "the minimum z-score", which is negative; Alg. 1
+ *       uses Zmin = |(min - mean)/std|.  The absolute value is taken.
+ *   R4  Buckets are floor(h) clipped to [0, k-1]; the paper clips only the
+ *       top, the bottom clip only guards rounding.
+ *   R5  k = max(2, floor(alpha * sqrt(n))) with alpha = 0.6 (the tuned value
+ *       of the alpha sensitivity study, Table 2); scale = k/4; both fixed
+ *       for every recursion level.
+ *   R6  A cluster with more than `leaf` (96) elements recurses, otherwise it
+ *       is insertion sorted.
+ *   R7  The counting-sort switch (range < 65000) is checked on entry to
+ *       every (sub)problem, after the early exit.
+ *   R8  The scatter statement of Alg. 1 is missing its right-hand side; it
+ *       is read as a stable scatter of the (key, payload) pair.
+ *   R9  zsortRec takes mean = meanEst and recomputes min, max, the standard
+ *       deviation about meanEst and Zmin over its own sub-array.
+ *   R10 Progress guard (the paper's depth argument assumes every level
+ *       shrinks the largest part): if a level puts every element of a
+ *       sub-problem with min < max into one cluster, or the depth reaches
+ *       `guard_depth`, that level uses the range map
+ *       b = floor(d * k / (range + 1)) in exact 128-bit integer arithmetic.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef unsigned __int128 u128;
+
+/* Counters describing one oracle run (returned to the caller). */
+typedef struct {
+    uint64_t partitions;      /* partition passes executed (all levels)      */
+    uint64_t max_depth;       /* deepest recursion level reached (top = 0)   */
+    uint64_t guard_levels;    /* levels that used the range map (R10)        */
+    uint64_t counting_sorts;  /* sub-problems finished by counting sort (R7) */
+    uint64_t insertion_sorts; /* clusters finished by insertion sort (R6)    */
+    uint64_t equal_exits;     /* sub-problems finished by min == max (R2)    */
+    uint64_t k;               /* number of clusters (R5)                     */
+    double scale;             /* Eq. 1 scale (R5)                            */
+} oracle_trace;
+
+typedef struct {
+    uint64_t k;
+    double scale;
+    uint64_t leaf;        /* insertion-sort cutoff, 96 in the paper        */
+    uint64_t count_range; /* counting-sort switch, 65000 in the paper      */
+    uint64_t guard_depth; /* depth from which R10 always applies           */
+    uint64_t *count;      /* counting-sort histogram, count_range entries  */
+    oracle_trace *tr;
+} zs_ctx;
+
+/* ------------------------------------------------------------------------ */
+/* Alg. 1, statistics: one pass for the sum and the minimum, one pass for the
+ * sum of squared deviations; std = sqrt(var / size) (population).  Computed
+ * on d = key - min (R1).  Also returns the maximum (needed by R2, R7). */
+void oracle_stats(const uint64_t *keys, uint64_t n, uint64_t *min_out,
+                  uint64_t *max_out, double *mean_d_out, double *sd_out)
+{
+    uint64_t mn = keys[0], mx = keys[0];
+    for (uint64_t i = 1; i < n; i++) {
+        if (keys[i] < mn) mn = keys[i];
+        if (keys[i] > mx) mx = keys[i];
+    }
+    double sum = 0.0;
+    for (uint64_t i = 0; i < n; i++) sum += (double)(keys[i] - mn);
+    double mean = sum / (double)n;
+    double var = 0.0;
+    for (uint64_t i = 0; i < n; i++) {
+        double res = (double)(keys[i] - mn) - mean;
+        var += res * res;
+    }
+    *min_out = mn;
+    *max_out = mx;
+    *mean_d_out = mean;
+    *sd_out = sqrt(var / (double)n);
+}
+
+/* Stable insertion sort of n pairs in place (Alg. 1, small clusters). */
+static void insertion_sort(uint64_t *k, uint32_t *v, uint64_t n)
+{
+    for (uint64_t i = 1; i < n; i++) {
+        uint64_t ck = k[i];
+        uint32_t cv = v[i];
+        uint64_t j = i;
+        while (j > 0 && k[j - 1] > ck) { /* strict: equal keys keep order */
+            k[j] = k[j - 1];
+            v[j] = v[j - 1];
+            j--;
+        }
+        k[j] = ck;
+        v[j] = cv;
+    }
+}
+
+/* Stable counting sort by d = key - mn over [0, range] (R7). */
+static void counting_sort(zs_ctx *c, const uint64_t *sk, const uint32_t *sv,
+                          uint64_t *dk, uint32_t *dv, uint64_t n, uint64_t mn,
+                          uint64_t range)
+{
+    uint64_t *cnt = c->count;
+    memset(cnt, 0, (size_t)(range + 1) * sizeof(uint64_t));
+    for (uint64_t i = 0; i < n; i++) cnt[sk[i] - mn]++;
+    uint64_t run = 0;
+    for (uint64_t r = 0; r <= range; r++) {
+        uint64_t t = cnt[r];
+        cnt[r] = run;
+        run += t;
+    }
+    for (uint64_t i = 0; i < n; i++) {
+        uint64_t p = cnt[sk[i] - mn]++;
+        dk[p] = sk[i];
+        dv[p] = sv[i];
+    }
+}
+
+/* Eq. 1 with R3, R4: h = ((d - mean)/std + Zmin) * scale, b = clip(floor h). */
+static uint64_t zmap(double d, double mean, double sd, double zmin,
+                     double scale, uint64_t k)
+{
+    double h = ((d - mean) / sd + zmin) * scale;
+    if (!(h >= 0.0)) return 0;
+    if (h >= (double)(k - 1)) return k - 1;
+    return (uint64_t)h; /* floor for h >= 0 */
+}
+
+/* R10: range map, exact: floor(d * k / (range + 1)). */
+static uint64_t rmap(uint64_t d, uint64_t range, uint64_t k)
+{
+    return (uint64_t)(((u128)d * (u128)k) / ((u128)range + 1));
+}
+
+/*
+ * One zSort (sub)problem: sorts src[0..size) stably into dst[0..size).
+ * src is consumed; tmp is the single auxiliary "clustersArr" of Alg. 1.
+ * have_est == 0: top level, mean computed (Alg. 1).
+ * have_est != 0: zsortRec, mean = meanEst, given in the parent's d-frame
+ *                (relative to parent_min) (R9).
+ */
+static void zs_rec(zs_ctx *c, uint64_t *sk, uint32_t *sv, uint64_t *dk,
+                   uint32_t *dv, uint64_t *tk, uint32_t *tv, uint64_t size,
+                   int have_est, double est_parent_d, uint64_t parent_min,
+                   uint64_t depth)
+{
+    oracle_trace *tr = c->tr;
+    if (depth > tr->max_depth) tr->max_depth = depth;
+    if (size == 0) return;
+    if (size == 1) {
+        dk[0] = sk[0];
+        dv[0] = sv[0];
+        return;
+    }
+
+    /* Alg. 1 first loop: sum and min (here also max, R2/R7). */
+    uint64_t mn = sk[0], mx = sk[0];
+    for (uint64_t i = 1; i < size; i++) {
+        if (sk[i] < mn) mn = sk[i];
+        if (sk[i] > mx) mx = sk[i];
+    }
+    /* R2: a set of identical keys is already sorted. */
+    if (mn == mx) {
+        memcpy(dk, sk, (size_t)size * sizeof(uint64_t));
+        memcpy(dv, sv, (size_t)size * sizeof(uint32_t));
+        tr->equal_exits++;
+        return;
+    }
+    uint64_t range = mx - mn;
+    /* R7: counting sort for small key ranges. */
+    if (range < c->count_range) {
+        counting_sort(c, sk, sv, dk, dv, size, mn, range);
+        tr->counting_sorts++;
+        return;
+    }
+
+    double mean;
+    if (!have_est) {
+        double sum = 0.0;
+        for (uint64_t i = 0; i < size; i++) sum += (double)(sk[i] - mn);
+        mean = sum / (double)size;
+    } else {
+        /* R9: meanEst moved from the parent's frame into this one. */
+        mean = est_parent_d - (double)(mn - parent_min);
+    }
+    /* Alg. 1 second loop: var = sum (x - mean)^2, std = sqrt(var/size). */
+    double var = 0.0;
+    for (uint64_t i = 0; i < size; i++) {
+        double res = (double)(sk[i] - mn) - mean;
+        var += res * res;
+    }
+    double sd = sqrt(var / (double)size);
+    double zmin = fabs((0.0 - mean) / sd); /* R3: Zmin = |(min - mean)/std| */
+    uint64_t k = c->k;
+    double scale = c->scale;
+
+    uint64_t *counts = (uint64_t *)calloc((size_t)k, sizeof(uint64_t));
+    uint64_t *offs = (uint64_t *)malloc((size_t)k * sizeof(uint64_t));
+    int guard = depth >= c->guard_depth;
+    for (int attempt = 0; attempt < 2; attempt++) {
+        memset(counts, 0, (size_t)k * sizeof(uint64_t));
+        /* Histogram of clusters (Alg. 1). */
+        for (uint64_t i = 0; i < size; i++) {
+            uint64_t d = sk[i] - mn;
+            uint64_t b = guard ? rmap(d, range, k)
+                               : zmap((double)d, mean, sd, zmin, scale, k);
+            counts[b]++;
+        }
+        if (guard) break;
+        /* R10: a level that made no progress is redone with the range map. */
+        int stuck = 0;
+        for (uint64_t b = 0; b < k; b++)
+            if (counts[b] == size) stuck = 1;
+        if (!stuck) break;
+        guard = 1;
+    }
+    if (guard) tr->guard_levels++;
+    tr->partitions++;
+
+    /* Exclusive scan of counts into offsets (Alg. 1). */
+    uint64_t run = 0;
+    for (uint64_t b = 0; b < k; b++) {
+        offs[b] = run;
+        run += counts[b];
+    }
+    /* Stable scatter in input order into the single auxiliary array (R8). */
+    for (uint64_t i = 0; i < size; i++) {
+        uint64_t d = sk[i] - mn;
+        uint64_t b = guard ? rmap(d, range, k)
+                           : zmap((double)d, mean, sd, zmin, scale, k);
+        uint64_t p = offs[b]++;
+        tk[p] = sk[i];
+        tv[p] = sv[i];
+    }
+
+    /* Per-cluster dispatch with running offset lbSum (Alg. 1). */
+    uint64_t lb = 0;
+    for (uint64_t b = 0; b < k; b++) {
+        uint64_t cnt = counts[b];
+        if (cnt == 0) continue;
+        if (cnt > c->leaf) {
+            /* meanEst = ((j + 0.5)/scale - Zmin) * std + mean (zsortRec). */
+            double est = (((double)b + 0.5) / scale - zmin) * sd + mean;
+            if (guard) {
+                /* The range map has no z-space; use the cluster midpoint. */
+                est = ((double)b + 0.5) * ((double)range + 1.0) / (double)k;
+            }
+            /* The cluster in tmp is the child's source; src is free now and
+             * serves as the child's auxiliary array. */
+            zs_rec(c, tk + lb, tv + lb, dk + lb, dv + lb, sk + lb, sv + lb, cnt,
+                   1, est, mn, depth + 1);
+        } else {
+            memcpy(dk + lb, tk + lb, (size_t)cnt * sizeof(uint64_t));
+            memcpy(dv + lb, tv + lb, (size_t)cnt * sizeof(uint32_t));
+            insertion_sort(dk + lb, dv + lb, cnt);
+            tr->insertion_sorts++;
+        }
+        lb += cnt;
+    }
+    free(counts);
+    free(offs);
+}
+
+/*
+ * Sorts n (key, payload) pairs in place, ascending by key, stably.
+ * alpha: cluster-count factor (k = max(2, floor(alpha*sqrt(n)))), 0.6 in the
+ * paper; leaf: insertion-sort cutoff (96); count_range: counting-sort switch
+ * (65000); guard_depth: depth from which the range map is always used.
+ * Returns 0, or -1 on allocation failure.
+ */
+int oracle_zsort_pairs_ex(uint64_t *keys, uint32_t *vals, uint64_t n,
+                          double alpha, uint64_t leaf, uint64_t count_range,
+                          uint64_t guard_depth, oracle_trace *trace)
+{
+    oracle_trace local;
+    oracle_trace *tr = trace ? trace : &local;
+    memset(tr, 0, sizeof(*tr));
+    if (n <= 1) return 0;
+    zs_ctx c;
+    uint64_t k = (uint64_t)floor(alpha * sqrt((double)n));
+    if (k < 2) k = 2;
+    c.k = k;
+    c.scale = (double)k / 4.0;
+    c.leaf = leaf;
+    c.count_range = count_range;
+    c.guard_depth = guard_depth;
+    c.tr = tr;
+    tr->k = k;
+    tr->scale = c.scale;
+    c.count = (uint64_t *)malloc((size_t)(count_range ? count_range : 1) *
+                                 sizeof(uint64_t));
+    uint64_t *bk = (uint64_t *)malloc((size_t)n * 2 * sizeof(uint64_t));
+    uint32_t *bv = (uint32_t *)malloc((size_t)n * 2 * sizeof(uint32_t));
+    if (!c.count || !bk || !bv) {
+        free(c.count);
+        free(bk);
+        free(bv);
+        return -1;
+    }
+    /* src = a copy of the input (consumed), dst = the caller's arrays. */
+    memcpy(bk, keys, (size_t)n * sizeof(uint64_t));
+    memcpy(bv, vals, (size_t)n * sizeof(uint32_t));
+    zs_rec(&c, bk, bv, keys, vals, bk + n, bv + n, n, 0, 0.0, 0, 0);
+    free(c.count);
+    free(bk);
+    free(bv);
+    return 0;
+}
+
+int oracle_zsort_pairs(uint64_t *keys, uint32_t *vals, uint64_t n,
+                       oracle_trace *trace)
+{
+    return oracle_zsort_pairs_ex(keys, vals, n, 0.6, 96, 65000, 32, trace);
+}
+
+/* Segment i is [off[i], off[i+1]); each is sorted on its own. */
+int oracle_zsort_segmented(uint64_t *keys, uint32_t *vals, const uint64_t *off,
+                           uint64_t nseg)
+{
+    for (uint64_t s = 0; s < nseg; s++) {
+        uint64_t a = off[s], b = off[s + 1];
+        if (b < a) return -5;
+        if (oracle_zsort_pairs(keys + a, vals + a, b - a, NULL) != 0) return -1;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Key encodings.  Two's complement order: flipping the sign bit maps int64
+ * order onto uint64 order.  IEEE-754 totalOrder: negative values (sign bit
+ * set) have all bits inverted, non-negative values get the sign bit set. */
+void oracle_key_from_i64(const int64_t *in, uint64_t *out, uint64_t n)
+{
+    for (uint64_t i = 0; i < n; i++)
+        out[i] = (uint64_t)in[i] ^ 0x8000000000000000ull;
+}
+
+void oracle_key_to_i64(const uint64_t *in, int64_t *out, uint64_t n)
+{
+    for (uint64_t i = 0; i < n; i++)
+        out[i] = (int64_t)(in[i] ^ 0x8000000000000000ull);
+}
+
+void oracle_key_from_f64(const double *in, uint64_t *out, uint64_t n)
+{
+    for (uint64_t i = 0; i < n; i++) {
+        uint64_t b;
+        memcpy(&b, &in[i], 8);
+        out[i] = (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+    }
+}
+
+void oracle_key_to_f64(const uint64_t *in, double *out, uint64_t n)
+{
+    for (uint64_t i = 0; i < n; i++) {
+        uint64_t u = in[i];
+        uint64_t b = (u >> 63) ? (u & 0x7fffffffffffffffull) : ~u;
+        memcpy(&out[i], &b, 8);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Learned piecewise-linear CDF bucket map (the z-score map's replacement). */
+
+/* SplitMix64 (Steele, Lea, Flood, OOPSLA 2014): the output of generator state
+ * x + 1 step, i.e. mix(x + golden gamma). */
+uint64_t oracle_splitmix64(uint64_t x)
+{
+    uint64_t z = x + 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+/* Stratified sample: stratum i = [floor(i*len/m), floor((i+1)*len/m)); one
+ * position drawn in it by splitmix64(seed + i) mod stratum width.  len >= m. */
+void oracle_sample_positions(uint64_t seed, uint64_t len, uint64_t m,
+                             uint64_t *pos)
+{
+    for (uint64_t i = 0; i < m; i++) {
+        uint64_t lo = (uint64_t)(((u128)i * len) / m);
+        uint64_t hi = (uint64_t)(((u128)(i + 1) * len) / m);
+        uint64_t w = hi - lo;
+        pos[i] = lo + (w ? oracle_splitmix64(seed + i) % w : 0);
+    }
+}
+
+/* Bit length of r (r >= 1): the E of the normalisation u = fl32(d) * 2^-E. */
+static int bitlen64(uint64_t r)
+{
+    int e = 0;
+    while (r) {
+        e++;
+        r >>= 1;
+    }
+    return e;
+}
+
+/* FP32-normalised key: u = fl32(key - mn) * 2^-E, E = bitlen(mx - mn).
+ * The scaling by a power of two is exact, so u lies in [0, 1]. */
+float oracle_pwl_normalise(uint64_t key, uint64_t mn, uint64_t mx)
+{
+    int e = bitlen64(mx - mn);
+    volatile float f = (float)(key - mn);
+    return f * ldexpf(1.0f, -e);
+}
+
+static int cmp_float(const void *a, const void *b)
+{
+    float x = *(const float *)a, y = *(const float *)b;
+    return (x > y) - (x < y);
+}
+
+/* Training: breakpoints q[0..P] of the empirical CDF of the normalised sample.
+ * q[0] = u(min) = 0, q[P] = u(max), q[j] = j-th P-quantile of the sorted
+ * sample, sorted[floor(j*m/P)], for 0 < j < P.  Non-decreasing by
+ * construction, so the map below is monotone. */
+void oracle_pwl_train(const uint64_t *sample, uint64_t m, uint64_t mn,
+                      uint64_t mx, uint32_t P, float *q)
+{
+    float *u = (float *)malloc((size_t)m * sizeof(float));
+    for (uint64_t i = 0; i < m; i++) u[i] = oracle_pwl_normalise(sample[i], mn, mx);
+    qsort(u, (size_t)m, sizeof(float), cmp_float);
+    q[0] = 0.0f;
+    for (uint32_t j = 1; j < P; j++) q[j] = u[(uint64_t)j * m / P];
+    q[P] = oracle_pwl_normalise(mx, mn, mx);
+    free(u);
+}
+
+/* Inference: piece s = #{ 0 < j < P : q[j] <= u }; within it the linear
+ * interpolation frac = (u - q[s]) / (q[s+1] - q[s]) (0 for an empty piece),
+ * clipped to [0, 1 - 2^-24]; bucket = s*K + min(K-1, floor(frac * K)),
+ * K = k / P.  All arithmetic is IEEE binary32 with round-to-nearest. */
+uint32_t oracle_pwl_bucket(uint64_t key, uint64_t mn, uint64_t mx,
+                           const float *q, uint32_t P, uint32_t k)
+{
+    float u = oracle_pwl_normalise(key, mn, mx);
+    uint32_t s = 0;
+    for (uint32_t j = 1; j < P; j++)
+        if (q[j] <= u) s = j;
+    uint32_t K = k / P;
+    volatile float lo = q[s], hi = q[s + 1];
+    float frac = 0.0f;
+    if (hi > lo) {
+        volatile float num = u - lo;
+        volatile float den = hi - lo;
+        frac = num / den;
+    }
+    if (frac < 0.0f) frac = 0.0f;
+    if (frac > 0.99999994f) frac = 0.99999994f; /* 1 - 2^-24 */
+    volatile float t = frac * (float)K;
+    uint32_t w = (uint32_t)t;
+    if (w > K - 1) w = K - 1;
+    return s * K + w;
+}
+
+/* Level-1 cluster of every key under Eq. 1 (Alg. 1 statistics, R1-R5), as
+ * the top level of oracle_zsort_pairs computes it before any guard. */
+void oracle_level1_buckets(const uint64_t *keys, uint64_t n, uint64_t k,
+                           uint64_t *out)
+{
+    uint64_t mn, mx;
+    double mean, sd;
+    oracle_stats(keys, n, &mn, &mx, &mean, &sd);
+    double scale = (double)k / 4.0;
+    double zmin = fabs((0.0 - mean) / sd);
+    for (uint64_t i = 0; i < n; i++)
+        out[i] = zmap((double)(keys[i] - mn), mean, sd, zmin, scale, k);
+}
