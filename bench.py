@@ -1,0 +1,388 @@
+"""Benchmark: sorted (uint64 key, uint32 index) pairs per second on GB300.
+
+Workload (default): two arrays of n = 2^28 pairs each (3 GiB of pairs per
+array), one lognormal floor(exp(N(30, 2))) and one 8-component Gaussian
+mixture (means evenly spaced over [2^60, 2^63], sd 2^55), payload = original
+index.  One step sorts both arrays in place with zsort_pairs_ex (learned
+mapper by default, Eq. 1 z-score fallback).  Inputs are restored from a
+pristine device copy between steps, outside the timed region; each restore
+writes 6 GiB, far more than the 129 MB L2, so every step starts cold.
+
+Printed: one JSON line (rank 0).  `value` = pairs sorted per second by the
+device-timed sorts; `e2e` = the same through the C ABI with the inputs copied
+from pinned host memory and the sorted pairs copied back inside the timed
+region; `roofline` = algorithmic bytes of the persistent sort kernel (the
+library's own count of bytes its passes read and write) over its measured
+duration, against the measured HBM copy bandwidth; `cpu_baseline` = the
+CPU oracle (plain sequential zSort in C) on a bounded sample of the same
+workload on this host.
+
+--impl reference runs the oracle as the reference arm on the same workload
+shape (bounded sample per step) and prints its own JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2605_14419_gb300 import inputs  # noqa: E402
+
+METRIC = "sorted 64-bit key+idx pairs/sec at 1 GB300 (plain vs learned/batched); % HBM roofline"
+UNIT = "pairs/s"
+BYTES_PER_PAIR = 12
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_workload(n: int):
+    return [("lognormal", inputs.lognormal(n, 30)), ("gmm8", inputs.gaussian_mixture(n, 31))]
+
+
+def cpu_oracle_rate(n_sample: int, budget_s: float = 12.0):
+    """Oracle pairs/s on bounded samples of the same two distributions."""
+    import oracle
+
+    samples = [inputs.lognormal(n_sample, 40), inputs.gaussian_mixture(n_sample, 41)]
+    vals = inputs.index_payload(n_sample)
+    done, t_total, reps = 0, 0.0, 0
+    while True:
+        for keys in samples:
+            t0 = time.perf_counter()
+            oracle.zsort_pairs(keys, vals)
+            t_total += time.perf_counter() - t0
+            done += n_sample
+        reps += 1
+        if t_total >= budget_s or reps >= 8:
+            break
+    return done / t_total, t_total, reps
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle, timed on this host, on the workload shape."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    n_sample = args.sample
+    arrays = [inputs.lognormal(n_sample, 40), inputs.gaussian_mixture(n_sample, 41)]
+    vals = inputs.index_payload(n_sample)
+    for _ in range(args.warmup):
+        for a in arrays:
+            oracle.zsort_pairs(a, vals)
+    t = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        for a in arrays:
+            oracle.zsort_pairs(a, vals)
+        t.append(time.perf_counter() - t0)
+    total = sum(t)
+    value = len(arrays) * n_sample * args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic (seeded numpy PCG64)",
+        "config": {"workload": f"zsort oracle (plain sequential C zSort), lognormal + gmm8 samples of "
+                               f"n={n_sample} each per step (full workload: 2 x 2^28)",
+                   "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"2 x {n_sample} pairs per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="zsort", choices=["zsort", "reference"])
+    ap.add_argument("--logn", type=int, default=28, help="log2 of pairs per array")
+    ap.add_argument("--mapper", default="learned", choices=["learned", "zscore"])
+    ap.add_argument("--sample", type=int, default=1 << 22, help="CPU oracle sample size")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip the z-score comparison run")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_2605_14419_gb300 as z
+    from paper_2605_14419_gb300 import build as zbuild
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        zbuild.build()
+    if world > 1:
+        dist.barrier()
+    z.load()
+
+    n = 1 << args.logn
+    work = make_workload(n)
+    pristine = []
+    for name, keys in work:
+        kd = torch.from_numpy(keys.view(np.int64)).to(dev)
+        vd = torch.arange(n, dtype=torch.int32, device=dev)
+        pristine.append((name, kd, vd))
+    del work
+    bufs = [(torch.empty_like(kd), torch.empty_like(vd)) for _, kd, vd in pristine]
+    stream = torch.cuda.current_stream()
+    z.reserve(n, 1, stream)
+    mapper = z.MAP_LEARNED if args.mapper == "learned" else z.MAP_ZSCORE
+
+    def restore():
+        for (_, kd, vd), (kb, vb) in zip(pristine, bufs):
+            kb.copy_(kd)
+            vb.copy_(vd)
+
+    def timed_sorts(opts):
+        """Sorts both arrays; returns per-array (ms, bytes, stats)."""
+        out = []
+        for kb, vb in bufs:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            z.sort_pairs(kb, vb, opts=opts, check=False)
+            e1.record(stream)
+            rc = z.sync_status(stream)
+            if rc != 0:
+                raise z.ZsortError(rc, "bench sort")
+            st = z.last_stats(stream)
+            out.append((e0.elapsed_time(e1), st["bytes_algorithmic"], st))
+        return out
+
+    def run(opts, steps, warmup):
+        for _ in range(warmup):
+            restore()
+            timed_sorts(opts)
+        res = []
+        for _ in range(steps):
+            restore()
+            torch.cuda.synchronize()
+            res.append(timed_sorts(opts))
+        return res
+
+    opts = z.default_opts(mapper=mapper)
+    # warm-up, then the timed steps, clocks sampled meanwhile
+    for _ in range(args.warmup):
+        restore()
+        timed_sorts(opts)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    res = []
+    for _ in range(args.steps):
+        restore()
+        torch.cuda.synchronize()
+        res.append(timed_sorts(opts))
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    step_ms = [sum(a[0] for a in step) for step in res]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    pairs_per_step = n * len(bufs)
+    value = world * pairs_per_step * args.steps / (total_ms / 1e3)
+    kernel_ms = [a[0] for step in res for a in step]
+    kernel_bytes = [a[1] for step in res for a in step]
+    avg_ms = sum(kernel_ms) / len(kernel_ms)
+    avg_bytes = sum(kernel_bytes) / len(kernel_bytes)
+    peak, peak_kind = load_peaks()
+    achieved = avg_bytes / (avg_ms / 1e3) / 1e9
+    last_stats = [a[2] for a in res[-1]]
+    # correctness of the last timed outputs (cheap device-side checks)
+    for (name, kd, _), (kb, vb) in zip(pristine, bufs):
+        s = kb ^ torch.tensor(-(2 ** 63), dtype=torch.int64, device=dev)
+        assert bool((s[1:] >= s[:-1]).all()), f"{name}: not sorted"
+        pos = vb.to(torch.int64) & 0xFFFFFFFF
+        assert bool(torch.equal(kd[pos], kb)), f"{name}: payload does not follow its key"
+
+    plain = None
+    if not args.no_plain and mapper == z.MAP_LEARNED:
+        pres = run(z.default_opts(mapper=z.MAP_ZSCORE), max(3, args.steps // 2), 1)
+        pms = sum(sum(a[0] for a in step) for step in pres)
+        plain = {"value": pairs_per_step * len(pres) / (pms / 1e3), "unit": UNIT,
+                 "mapper": "zscore (Eq. 1)",
+                 "bytes_per_pair": sum(a[1] for step in pres for a in step) / (n * len(bufs) * len(pres)),
+                 "per_array_ms": [round(sum(step[i][0] for step in pres) / len(pres), 3)
+                                  for i in range(len(bufs))]}
+
+    e2e = None
+    if not args.no_e2e:
+        hk = [torch.empty(n, dtype=torch.int64, pin_memory=True) for _ in pristine]
+        hv = [torch.empty(n, dtype=torch.int32, pin_memory=True) for _ in pristine]
+        for (_, kd, vd), a, b in zip(pristine, hk, hv):
+            a.copy_(kd)
+            b.copy_(vd)
+        ok_k = [torch.empty(n, dtype=torch.int64, pin_memory=True) for _ in pristine]
+        ok_v = [torch.empty(n, dtype=torch.int32, pin_memory=True) for _ in pristine]
+        torch.cuda.synchronize()
+
+        def e2e_step():
+            for i, (kb, vb) in enumerate(bufs):
+                kb.copy_(hk[i], non_blocking=True)
+                vb.copy_(hv[i], non_blocking=True)
+                z.sort_pairs(kb, vb, opts=opts, check=False)
+                ok_k[i].copy_(kb, non_blocking=True)
+                ok_v[i].copy_(vb, non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e_steps = max(3, args.steps // 2)
+        e0.record(stream)
+        for _ in range(e_steps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        rc = z.sync_status(stream)
+        if rc != 0:
+            raise z.ZsortError(rc, "bench e2e")
+        ems = e0.elapsed_time(e1)
+        e2e = {"value": world * pairs_per_step * e_steps / (ems / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": pairs_per_step * BYTES_PER_PAIR,
+               "d2h_bytes_per_step": pairs_per_step * BYTES_PER_PAIR}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        rate, secs, reps = cpu_oracle_rate(args.sample)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"lognormal + gmm8, {args.sample} pairs each, {reps} rounds, {secs:.1f} s"}
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic (seeded numpy PCG64)",
+        "config": {
+            "workload": f"zsort_pairs, 2 arrays x n=2^{args.logn} (u64 key, u32 index): lognormal "
+                        f"floor(exp(N(30,2))) and 8-component Gaussian mixture; mapper={args.mapper}",
+            "pairs_per_step": pairs_per_step,
+            "l2": "inputs (3 GiB per array) far larger than L2; restored between steps",
+            "parallelism": "replicas" if world > 1 else "single GPU",
+        },
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                     "kernel": "k_persistent (whole zsort_pairs call)",
+                     "algorithmic_bytes_per_launch": avg_bytes, "avg_launch_ms": avg_ms},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": clk,
+        "gpu_launches": 3 * len(bufs) * args.steps,
+        "per_array": [{"array": name, "ms": round(sum(step[i][0] for step in res) / len(res), 3),
+                       "bytes_per_pair": round(last_stats[i]["bytes_algorithmic"] / n, 2),
+                       "max_level": last_stats[i]["max_level"],
+                       "top_map": last_stats[i]["top_map"],
+                       "leaves": last_stats[i]["leaves"],
+                       "learned_accepted": last_stats[i]["learned_accepted"]}
+                      for i, (name, _, _) in enumerate(pristine)],
+        "plain_zscore": plain,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,172 @@
+/*
+ * zsort.h -- C ABI of a GB300 (sm_103a) stable distribution sort of 64-bit
+ * keys with a 32-bit payload, after zSort (Jain et al., "zSort: Stable
+ * Distribution Sort using Z-Score Partitioning", arXiv 2605.14419).
+ *
+ * The operation (section "Proposed Work", problem statement and stability
+ * paragraph): sort n (key, payload) pairs in place, ascending by key; among
+ * equal keys the input order is kept.  The result is the unique permutation
+ * that orders the tuples (key, input position) lexicographically, so it is
+ * bit-for-bit reproducible and independent of every tuning choice.
+ *
+ * The method (Alg. 1 and zsortRec): per (sub)array the mean and population
+ * standard deviation of the keys, the z-score map of Eq. 1 from a key to one
+ * of k buckets, a histogram and an exclusive scan for the bucket offsets, a
+ * stable scatter; oversized buckets repeat the same steps, small ones are
+ * finished in on-chip shared memory.  A learned monotone piecewise-linear
+ * CDF map may replace Eq. 1 (not in the paper; see ZSORT_MAP_LEARNED).
+ *
+ * Conventions for every entry point below
+ *   - keys, vals and seg_offsets are CUDA DEVICE pointers of the current
+ *     device, 16-byte aligned is recommended (8 required for keys, 4 for
+ *     vals); the caller owns them.  The library owns its scratch workspace
+ *     (about 12 bytes per element plus bookkeeping), cached per (device,
+ *     stream) and grown on demand; zsort_reserve() sizes it up front so
+ *     that later calls do not allocate.
+ *   - Calls are stream ordered and asynchronous: they return once the work
+ *     is enqueued on `stream` (NULL = the legacy default stream).  Calls on
+ *     different streams use different workspaces and may overlap.
+ *   - Host-detectable errors (bad arguments, allocation failure, launch
+ *     failure) are returned at once and nothing is enqueued.  Errors found
+ *     on the device (a wait that timed out, decreasing segment offsets, a
+ *     full internal queue) are written to a device status word that
+ *     zsort_sync_status() returns; the contents of keys/vals are then
+ *     unspecified, but no kernel traps, faults or hangs.
+ */
+#ifndef ZSORT_H
+#define ZSORT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A cudaStream_t, spelled without the CUDA headers. */
+typedef struct CUstream_st *zsort_stream_t;
+
+/* Status codes. */
+enum {
+    ZSORT_OK = 0,
+    ZSORT_ERR_INVALID = -1,     /* bad argument (null pointer, n too large) */
+    ZSORT_ERR_NOMEM = -2,       /* device allocation of the workspace failed */
+    ZSORT_ERR_CUDA = -3,        /* a CUDA runtime call or a launch failed    */
+    ZSORT_ERR_TIMEOUT = -4,     /* a bounded device-side wait expired        */
+    ZSORT_ERR_BAD_OFFSETS = -5, /* segment offsets decrease or exceed n      */
+    ZSORT_ERR_CAPACITY = -6,    /* an internal device queue overflowed       */
+    ZSORT_ERR_INTERNAL = -7     /* a device-side consistency check failed    */
+};
+
+/* Largest n accepted by every entry point (look-back status words carry
+ * 30-bit counts). */
+#define ZSORT_MAX_N ((uint64_t)1 << 30)
+
+/* Bucket maps. */
+enum {
+    ZSORT_MAP_ZSCORE = 0,  /* Eq. 1: floor(((x - mean)/sd + |z_min|) * k/4)   */
+    ZSORT_MAP_LEARNED = 1  /* piecewise-linear CDF, 256 pieces, FP32, trained
+                              on a sample; Eq. 1 is the fallback             */
+};
+
+/* Key types for zsort_pairs_ex. */
+enum {
+    ZSORT_KEY_U64 = 0,
+    ZSORT_KEY_I64 = 1, /* two's complement order                           */
+    ZSORT_KEY_F64 = 2  /* IEEE-754 totalOrder: -NaN < -inf < ... < -0.0 <
+                          +0.0 < ... < +inf < +NaN                           */
+};
+
+/* Tuning options.  Fill with zsort_default_opts() and change fields. */
+typedef struct {
+    uint32_t struct_size;    /* sizeof(zsort_opts)                            */
+    uint32_t mapper;         /* ZSORT_MAP_ZSCORE or ZSORT_MAP_LEARNED          */
+    uint32_t kmax;           /* most buckets per partition, power of 2, 16..1024 */
+    uint32_t leaf_target;    /* k = clamp(pow2ceil(len / leaf_target), 16, kmax) */
+    uint32_t large_min;      /* longer (sub)arrays are partitioned by all SMs
+                                with a decoupled look-back; shorter ones by
+                                one CTA                                      */
+    uint32_t learn_min;      /* arrays at least this long train a learned map */
+    uint32_t sample;         /* learned-map training sample, 256..65536       */
+    float fallback_ratio;    /* learned map rejected if its sampled largest
+                                bucket exceeds fallback_ratio * sample / k   */
+    uint64_t seed;           /* seed of the sample positions                  */
+    uint32_t guard_level;    /* from this depth on, the exact range map is used */
+    uint32_t ctas_per_sm;    /* persistent CTAs per SM, 0 = from occupancy     */
+    uint32_t wait_limit_ms;  /* bound of every device-side wait (no progress)  */
+    uint32_t reserved;
+} zsort_opts;
+
+/* Counters of the last completed call on a (device, stream) workspace. */
+typedef struct {
+    uint64_t n;                 /* elements of the call                         */
+    uint64_t partitions_large;  /* multi-CTA partition passes                   */
+    uint64_t partitions_small;  /* single-CTA partition passes                  */
+    uint64_t leaves;            /* shared-memory finish tasks                   */
+    uint64_t leaf_fallbacks;    /* finish tasks that took the bitonic fallback  */
+    uint64_t copies;            /* all-equal (sub)arrays copied back            */
+    uint64_t learned_accepted;  /* learned maps accepted by the load test       */
+    uint64_t learned_rejected;  /* learned maps rejected (Eq. 1 used)           */
+    uint64_t guard_levels;      /* partitions that used the range map           */
+    uint64_t max_level;         /* deepest partition level                      */
+    uint64_t bytes_algorithmic; /* bytes read + written by the method's passes  */
+    uint64_t tasks;             /* tasks executed by the persistent kernel      */
+    uint64_t persistent_ctas;   /* CTAs of the persistent launch                */
+    double top_mean_d;          /* top level: mean of key - min (segment 0)     */
+    double top_sd;              /* top level: population standard deviation     */
+    uint64_t top_min, top_max;  /* top level: exact min and max                 */
+    uint32_t top_k;             /* top level: buckets                           */
+    uint32_t top_map;           /* top level: map used (ZSORT_MAP_*, 2 = range) */
+} zsort_stats;
+
+/* Fills *o with the defaults (z-score map, kmax 1024, ...). */
+void zsort_default_opts(zsort_opts *o);
+
+/* Sorts n (uint64 key, uint32 payload) pairs in place, stably (see above).
+ * n <= ZSORT_MAX_N.  Uses the default options. */
+int zsort_pairs(uint64_t *keys, uint32_t *vals, uint64_t n, zsort_stream_t stream);
+
+/* The same for int64 keys (two's complement order) and float64 keys (IEEE
+ * totalOrder, so -0.0 sorts before +0.0).  The keys are encoded to uint64 in
+ * place on the device, sorted, and decoded. */
+int zsort_pairs_i64(int64_t *keys, uint32_t *vals, uint64_t n, zsort_stream_t stream);
+int zsort_pairs_f64(double *keys, uint32_t *vals, uint64_t n, zsort_stream_t stream);
+
+/* General form: key_type is ZSORT_KEY_*, opts may be NULL (defaults). */
+int zsort_pairs_ex(void *keys, uint32_t key_type, uint32_t *vals, uint64_t n,
+                   const zsort_opts *opts, zsort_stream_t stream);
+
+/* Batched sort: keys/vals hold n elements; segment i is
+ * [seg_offsets[i], seg_offsets[i+1]) and is sorted on its own, stably.
+ * seg_offsets is a device array of nseg + 1 non-decreasing values <= n;
+ * empty segments are allowed and elements outside
+ * [seg_offsets[0], seg_offsets[nseg]) are untouched.  The whole batch runs
+ * as one persistent kernel over a device work queue.  A violation of the
+ * offsets contract is reported as ZSORT_ERR_BAD_OFFSETS by
+ * zsort_sync_status() and leaves keys/vals untouched. */
+int zsort_segmented(uint64_t *keys, uint32_t *vals, uint64_t n, const uint64_t *seg_offsets,
+                    uint64_t nseg, zsort_stream_t stream);
+int zsort_segmented_ex(uint64_t *keys, uint32_t *vals, uint64_t n, const uint64_t *seg_offsets,
+                       uint64_t nseg, const zsort_opts *opts, zsort_stream_t stream);
+
+/* Sizes the (device, stream) workspace for calls of up to n elements and
+ * nseg segments, so that those calls allocate nothing. */
+int zsort_reserve(uint64_t n, uint64_t nseg, zsort_stream_t stream);
+
+/* Frees every workspace of the current device.  No call may be in flight. */
+int zsort_release(void);
+
+/* Waits for `stream`, then returns the device status word of its workspace
+ * (ZSORT_OK or a negative code) and clears it. */
+int zsort_sync_status(zsort_stream_t stream);
+
+/* Waits for `stream` and copies the counters of its last call to *out. */
+int zsort_last_stats(zsort_stream_t stream, zsort_stats *out);
+
+/* Human-readable text of a status code (static storage). */
+const char *zsort_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ZSORT_H */

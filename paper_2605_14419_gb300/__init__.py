@@ -1,0 +1,218 @@
+"""GB300-native zSort: a stable distribution sort of (uint64 key, uint32 payload)
+pairs after "zSort: Stable Distribution Sort using Z-Score Partitioning"
+(arXiv 2605.14419).
+
+This module is a thin ctypes binding of the C ABI in ``include/zsort.h``:
+it only marshals arguments.  Every step of the sort runs in the CUDA library
+``libzsort.so`` (built in-tree by ``paper_2605_14419_gb300.build``); there is
+no CPU path.  PyTorch supplies device memory and streams only.
+
+Tensors: keys are 8-byte CUDA tensors (torch.int64/uint64/float64 storage,
+reinterpreted by ``key_type``), payloads 4-byte CUDA tensors (torch.int32 or
+uint32 storage), both contiguous, sorted in place.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libzsort.so")
+_HEADER = os.path.join(os.path.dirname(_HERE), "include", "zsort.h")
+_lib = None
+
+OK = 0
+ERR_INVALID, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_BAD_OFFSETS, ERR_CAPACITY, ERR_INTERNAL = (
+    -1, -2, -3, -4, -5, -6, -7)
+MAP_ZSCORE, MAP_LEARNED = 0, 1
+KEY_TYPES = {"u64": 0, "i64": 1, "f64": 2}
+MAX_N = 1 << 30
+
+
+class ZsortError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {strerror(code)} ({code})")
+
+
+class Opts(ctypes.Structure):
+    """``zsort_opts`` (field meanings in include/zsort.h)."""
+
+    _fields_ = [
+        ("struct_size", ctypes.c_uint32),
+        ("mapper", ctypes.c_uint32),
+        ("kmax", ctypes.c_uint32),
+        ("leaf_target", ctypes.c_uint32),
+        ("large_min", ctypes.c_uint32),
+        ("learn_min", ctypes.c_uint32),
+        ("sample", ctypes.c_uint32),
+        ("fallback_ratio", ctypes.c_float),
+        ("seed", ctypes.c_uint64),
+        ("guard_level", ctypes.c_uint32),
+        ("ctas_per_sm", ctypes.c_uint32),
+        ("wait_limit_ms", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32),
+    ]
+
+
+class Stats(ctypes.Structure):
+    """``zsort_stats``: counters of the last call on a stream's workspace."""
+
+    _fields_ = [
+        ("n", ctypes.c_uint64),
+        ("partitions_large", ctypes.c_uint64),
+        ("partitions_small", ctypes.c_uint64),
+        ("leaves", ctypes.c_uint64),
+        ("leaf_fallbacks", ctypes.c_uint64),
+        ("copies", ctypes.c_uint64),
+        ("learned_accepted", ctypes.c_uint64),
+        ("learned_rejected", ctypes.c_uint64),
+        ("guard_levels", ctypes.c_uint64),
+        ("max_level", ctypes.c_uint64),
+        ("bytes_algorithmic", ctypes.c_uint64),
+        ("tasks", ctypes.c_uint64),
+        ("persistent_ctas", ctypes.c_uint64),
+        ("top_mean_d", ctypes.c_double),
+        ("top_sd", ctypes.c_double),
+        ("top_min", ctypes.c_uint64),
+        ("top_max", ctypes.c_uint64),
+        ("top_k", ctypes.c_uint32),
+        ("top_map", ctypes.c_uint32),
+    ]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/zsort.h."""
+    with open(_HEADER) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(zsort_\w+)\s*\(", text, re.M)))
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def load():
+    """Loads libzsort.so; raises if it was not built (there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise RuntimeError(f"zsort CUDA library missing: {_LIB_PATH}; build it with "
+                           "`python -m paper_2605_14419_gb300.build`")
+    lib = ctypes.CDLL(_LIB_PATH)
+    vp, u32, u64, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+    sig = {
+        "zsort_default_opts": (None, [ctypes.POINTER(Opts)]),
+        "zsort_pairs": (i32, [vp, vp, u64, vp]),
+        "zsort_pairs_i64": (i32, [vp, vp, u64, vp]),
+        "zsort_pairs_f64": (i32, [vp, vp, u64, vp]),
+        "zsort_pairs_ex": (i32, [vp, u32, vp, u64, ctypes.POINTER(Opts), vp]),
+        "zsort_segmented": (i32, [vp, vp, u64, vp, u64, vp]),
+        "zsort_segmented_ex": (i32, [vp, vp, u64, vp, u64, ctypes.POINTER(Opts), vp]),
+        "zsort_reserve": (i32, [u64, u64, vp]),
+        "zsort_release": (i32, []),
+        "zsort_sync_status": (i32, [vp]),
+        "zsort_last_stats": (i32, [vp, ctypes.POINTER(Stats)]),
+        "zsort_strerror": (ctypes.c_char_p, [i32]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def strerror(code: int) -> str:
+    try:
+        return load().zsort_strerror(code).decode()
+    except RuntimeError:
+        return f"status {code}"
+
+
+def default_opts(**overrides) -> Opts:
+    o = Opts()
+    load().zsort_default_opts(ctypes.byref(o))
+    for k, v in overrides.items():
+        if not hasattr(o, k):
+            raise AttributeError(f"zsort_opts has no field {k}")
+        setattr(o, k, v)
+    return o
+
+
+def _stream_handle(stream):
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _check_tensor(t, elem: int, what: str):
+    if not t.is_cuda or not t.is_contiguous() or t.element_size() != elem or t.dim() != 1:
+        raise ValueError(f"{what}: need a contiguous 1-D CUDA tensor of {elem}-byte elements")
+
+
+def _raise(rc: int, where: str):
+    if rc != OK:
+        raise ZsortError(rc, where)
+
+
+def sort_pairs(keys, vals, key_type: str = "u64", opts: Opts | None = None, stream=None,
+               check: bool = True):
+    """Sorts (keys, vals) in place, stably by key.  With check=True the stream
+    is synchronised and the device status raised as ZsortError."""
+    _check_tensor(keys, 8, "keys")
+    _check_tensor(vals, 4, "vals")
+    if keys.numel() != vals.numel():
+        raise ValueError("keys and vals differ in length")
+    lib = load()
+    st = _stream_handle(stream)
+    rc = lib.zsort_pairs_ex(ctypes.c_void_p(keys.data_ptr()), KEY_TYPES[key_type],
+                            ctypes.c_void_p(vals.data_ptr()), keys.numel(),
+                            ctypes.byref(opts) if opts is not None else None, st)
+    _raise(rc, "zsort_pairs_ex")
+    if check:
+        _raise(lib.zsort_sync_status(st), "zsort (device)")
+    return keys, vals
+
+
+def sort_segmented(keys, vals, offsets, opts: Opts | None = None, stream=None, check: bool = True):
+    """Sorts each segment [offsets[i], offsets[i+1]) of (keys, vals) in place.
+    offsets: CUDA int64/uint64 tensor of nseg + 1 entries."""
+    _check_tensor(keys, 8, "keys")
+    _check_tensor(vals, 4, "vals")
+    _check_tensor(offsets, 8, "offsets")
+    lib = load()
+    st = _stream_handle(stream)
+    rc = lib.zsort_segmented_ex(ctypes.c_void_p(keys.data_ptr()), ctypes.c_void_p(vals.data_ptr()),
+                                keys.numel(), ctypes.c_void_p(offsets.data_ptr()),
+                                max(offsets.numel() - 1, 0),
+                                ctypes.byref(opts) if opts is not None else None, st)
+    _raise(rc, "zsort_segmented_ex")
+    if check:
+        _raise(lib.zsort_sync_status(st), "zsort_segmented (device)")
+    return keys, vals
+
+
+def reserve(n: int, nseg: int = 1, stream=None):
+    _raise(load().zsort_reserve(n, nseg, _stream_handle(stream)), "zsort_reserve")
+
+
+def release():
+    _raise(load().zsort_release(), "zsort_release")
+
+
+def sync_status(stream=None) -> int:
+    return load().zsort_sync_status(_stream_handle(stream))
+
+
+def last_stats(stream=None) -> dict:
+    s = Stats()
+    _raise(load().zsort_last_stats(_stream_handle(stream), ctypes.byref(s)), "zsort_last_stats")
+    return s.as_dict()

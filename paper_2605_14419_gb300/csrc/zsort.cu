@@ -1,0 +1,572 @@
+// zsort.cu -- kernels and C ABI of the GB300 zSort (see include/zsort.h).
+//
+// One call = four stream-ordered operations: clear the control block,
+// classify the (segment) inputs, publish the first queue entries, then ONE
+// persistent kernel (one or two CTAs per SM) that pulls tasks from a device
+// work queue until every (sub)array is sorted.  Nothing on the path runs on
+// the host or falls back to it; the host only sizes the workspace and
+// launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "../../include/zsort.h"
+#include "zsort_tasks.cuh"
+
+using namespace zs;
+
+// ---------------------------------------------------------------- kernels
+__global__ void __launch_bounds__(BLOCK, 2) k_persistent(Params P)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    SmemTile &s = *reinterpret_cast<SmemTile *>(smraw);
+    for (;;) {
+        if (threadIdx.x == 0) dequeue(P, s.task);
+        __syncthreads();
+        const uint32_t type = s.task[0], arg = s.task[1], tile = s.task[2];
+        const uint32_t e = s.task[3], ntiles = s.task[4];
+        __syncthreads();
+        if (type == T_NONE) return;
+        switch (type) {
+        case T_LSTATS: task_lstats(P, arg, tile, s); break;
+        case T_LTRAIN: task_ltrain(P, arg, s); break;
+        case T_LHIST: task_lhist(P, arg, tile, s); break;
+        case T_LSCATTER: task_lscatter(P, arg, tile, s); break;
+        case T_MPART: task_mpart(P, load_item(P, arg + tile), s); break;
+        case T_FINISH: task_finish(P, load_item(P, arg + tile), s); break;
+        case T_COPY: task_copy(P, arg, tile); break;
+        default: set_error(P, ST_INTERNAL); break;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            uint32_t old = atomicAdd(&P.tdone[e], 1u);
+            s.flag2 = (old + 1 == ntiles) ? 1u : 0u;
+            atomicAdd(&P.ctl->progress, 1ull);
+            atomicAdd(&P.ctl->tasks, 1ull);
+        }
+        __syncthreads();
+        if (s.flag2) {
+            __threadfence();
+            switch (type) {
+            case T_LSTATS: lstats_done(P, arg, s); break;
+            case T_LHIST: lhist_done(P, arg, s); break;
+            case T_LSCATTER: lscatter_done(P, arg, s); break;
+            default: break;  // LTRAIN publishes its successor itself
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                atomicSub(&P.ctl->pending, 1u);
+            }
+        }
+    }
+}
+
+// Classifies each input segment: leaf (<= LEAF_CAP), medium (<= large_min),
+// or large (own descriptor and look-back rows).  off == nullptr means one
+// segment [0, n).  Leaves are staged in items[0, nseg), mediums in
+// items[nseg, 2 nseg).
+__global__ void k_init_segments(Params P, const uint64_t *off, unsigned long long nseg)
+{
+    const unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nseg) return;
+    const unsigned long long a = off ? off[i] : 0ull, b = off ? off[i + 1] : P.n;
+    if (a > b || b > P.n) {
+        set_error(P, ST_BAD_OFFSETS);
+        return;
+    }
+    const unsigned long long len = b - a;
+    if (len <= 1) return;
+    Ctl *C = P.ctl;
+    Item it;
+    it.off = a;
+    it.len = (uint32_t)len;
+    it.buf = 0;
+    it.level = 0;
+    if (len <= (unsigned long long)LEAF_CAP) {
+        uint32_t j = atomicAdd(&C->init_leaf, 1u);
+        P.items[j] = it;
+        return;
+    }
+    if (len > P.large_min) {
+        const uint32_t kk = choose_k(P, (uint32_t)len);
+        const uint32_t tiles = (uint32_t)((len + TILE - 1) / TILE);
+        const unsigned long long need = (unsigned long long)tiles * kk;
+        const uint32_t sid = atomicAdd(&C->seg_alloc, 1u);
+        unsigned long long sb = ~0ull;
+        if (sid < P.segcap) sb = atomicAdd(&C->status_alloc, need);
+        if (sid < P.segcap && sb + need <= P.statuscap) {
+            Seg *S = &P.segs[sid];
+            S->off = a;
+            S->mn = ~0ull;
+            S->mx = 0ull;
+            S->s1[0] = S->s1[1] = 0ull;
+            S->s2[0] = S->s2[1] = S->s2[2] = 0ull;
+            S->status_base = sb;
+            S->len = (uint32_t)len;
+            S->k = kk;
+            S->tiles = tiles;
+            S->level = 0;
+            S->buf = 0;
+            S->kind = MAP_Z;
+            S->train_slot = INVALID;
+            for (uint32_t q = 0; q < kk; q++) P.counts[(size_t)sid * NB_MAX + q] = 0;
+            return;
+        }
+        if (sid < P.segcap) P.segs[sid].len = 0;  // no room: partitioned by one CTA
+    }
+    uint32_t j = atomicAdd(&C->init_med, 1u);
+    P.items[nseg + j] = it;
+}
+
+// Publishes the first entries (after k_init_segments, same stream).
+__global__ void k_init_publish(Params P, unsigned long long nseg)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    Ctl *C = P.ctl;
+    if (C->error) {
+        C->pending = 0;
+        return;
+    }
+    const uint32_t nl = C->init_leaf, nm = C->init_med;
+    const uint32_t ns = min(C->seg_alloc, P.segcap);
+    uint32_t e = 0;
+    if (nl) q_write(P, e++, T_FINISH, 0, nl);
+    if (nm) q_write(P, e++, T_MPART, (uint32_t)nseg, nm);
+    for (uint32_t sid = 0; sid < ns; sid++) {
+        if (P.segs[sid].len == 0) continue;
+        if (e >= P.qcap) {
+            C->error = (unsigned int)ST_CAPACITY;
+            C->pending = 0;
+            return;
+        }
+        q_write(P, e++, T_LSTATS, sid, P.segs[sid].tiles);
+    }
+    C->q_alloc = e;
+    C->pending = e;
+    C->item_alloc = (uint32_t)(2 * nseg);
+    for (uint32_t i = 0; i < e; i++) P.ready[i] = P.epoch;
+}
+
+// Order-preserving encodings to uint64 and back (in place).
+__global__ void k_encode(uint64_t *keys, unsigned long long n, uint32_t type, int inverse)
+{
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        uint64_t x = keys[i];
+        if (type == ZSORT_KEY_I64) {
+            x ^= 0x8000000000000000ull;  // two's complement order -> unsigned order
+        } else if (!inverse) {       // IEEE-754 totalOrder
+            x = (x >> 63) ? ~x : (x | 0x8000000000000000ull);
+        } else {
+            x = (x >> 63) ? (x & 0x7fffffffffffffffull) : ~x;
+        }
+        keys[i] = x;
+    }
+}
+
+// ---------------------------------------------------------------- host side
+namespace {
+
+struct Workspace {
+    int device = -1;
+    cudaStream_t stream = nullptr;
+    unsigned long long n_cap = 0, nseg_cap = 0;
+    unsigned long long large_min = 0;
+    void *block = nullptr;
+    size_t bytes = 0;
+    Params P{};
+    uint32_t epoch = 0;
+    int sms = 0;
+    int occ = 0;
+};
+
+std::mutex g_mu;
+std::vector<Workspace *> g_ws;
+bool g_attr_set[64] = {false};
+const size_t SMEM_BYTES = sizeof(SmemTile);
+
+unsigned long long div_up(unsigned long long a, unsigned long long b) { return (a + b - 1) / b; }
+
+size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Capacity plan for calls of up to n elements and nseg segments.
+struct Plan {
+    unsigned long long qcap, segcap, itemcap, statuscap, traincap;
+    size_t off_skeys, off_svals, off_ctl, off_entries, off_ready, off_tnext, off_tdone, off_segs,
+        off_items, off_counts, off_bstart, off_status, off_pwl, off_train, total;
+};
+
+Plan make_plan(unsigned long long n, unsigned long long nseg, unsigned long long large_min)
+{
+    Plan p{};
+    const unsigned long long tiles = div_up(n, TILE);
+    p.qcap = n / 128 + 4 * nseg + 4096;
+    p.segcap = 3 * (n / (large_min + 1)) + 64;
+    p.itemcap = 2 * nseg + n / 32 + 4096;
+    p.statuscap = 2 * (tiles + 64) * (unsigned long long)NB_MAX;
+    p.traincap = std::min<unsigned long long>(p.segcap, 32);
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t r = o;
+        o = align_up(o + bytes);
+        return r;
+    };
+    p.off_skeys = take(n * 8);
+    p.off_svals = take(n * 4);
+    p.off_ctl = take(sizeof(Ctl));
+    p.off_entries = take(p.qcap * sizeof(Entry));
+    p.off_ready = take(p.qcap * 4);
+    p.off_tnext = take(p.qcap * 4);
+    p.off_tdone = take(p.qcap * 4);
+    p.off_segs = take(p.segcap * sizeof(Seg));
+    p.off_items = take(p.itemcap * sizeof(Item));
+    p.off_counts = take(p.segcap * NB_MAX * 4);
+    p.off_bstart = take(p.segcap * NB_MAX * 4);
+    p.off_status = take(p.statuscap * 4);
+    p.off_pwl = take(p.segcap * (PWL_P + 1) * 4);
+    p.off_train = take(p.traincap * 2 * SAMPLE_MAX * 4);
+    p.total = o;
+    return p;
+}
+
+int cuda_err(cudaError_t e)
+{
+    if (e == cudaSuccess) return ZSORT_OK;
+    if (e == cudaErrorMemoryAllocation) return ZSORT_ERR_NOMEM;
+    return ZSORT_ERR_CUDA;
+}
+
+// Finds or (re)allocates the workspace of (current device, stream).
+int get_workspace(cudaStream_t stream, unsigned long long n, unsigned long long nseg,
+                  unsigned long long large_min, Workspace **out)
+{
+    int dev = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce != cudaSuccess) return cuda_err(ce);
+    Workspace *ws = nullptr;
+    for (Workspace *w : g_ws)
+        if (w->device == dev && w->stream == stream) ws = w;
+    if (!ws) {
+        ws = new Workspace();
+        ws->device = dev;
+        ws->stream = stream;
+        g_ws.push_back(ws);
+    }
+    if (!ws->block || ws->n_cap < n || ws->nseg_cap < nseg || ws->large_min != large_min) {
+        unsigned long long ncap = std::max<unsigned long long>(n, ws->n_cap);
+        unsigned long long scap = std::max<unsigned long long>(nseg, ws->nseg_cap);
+        ncap = std::max<unsigned long long>(ncap, 1);
+        scap = std::max<unsigned long long>(scap, 1);
+        Plan p = make_plan(ncap, scap, large_min);
+        if (ws->block) {
+            ce = cudaStreamSynchronize(stream);  // the old block may still be in use
+            if (ce != cudaSuccess) return cuda_err(ce);
+            cudaFree(ws->block);
+            ws->block = nullptr;
+        }
+        void *blk = nullptr;
+        ce = cudaMalloc(&blk, p.total);
+        if (ce != cudaSuccess) {
+            cudaGetLastError();
+            return ZSORT_ERR_NOMEM;
+        }
+        ce = cudaMemset(blk, 0, p.total);  // zero ready flags (epoch 0 never used)
+        if (ce != cudaSuccess) return cuda_err(ce);
+        ws->block = blk;
+        ws->bytes = p.total;
+        ws->n_cap = ncap;
+        ws->nseg_cap = scap;
+        ws->large_min = large_min;
+        char *b = static_cast<char *>(blk);
+        Params &P = ws->P;
+        P = Params{};
+        P.skeys = reinterpret_cast<uint64_t *>(b + p.off_skeys);
+        P.svals = reinterpret_cast<uint32_t *>(b + p.off_svals);
+        P.ctl = reinterpret_cast<Ctl *>(b + p.off_ctl);
+        P.entries = reinterpret_cast<Entry *>(b + p.off_entries);
+        P.ready = reinterpret_cast<uint32_t *>(b + p.off_ready);
+        P.tnext = reinterpret_cast<uint32_t *>(b + p.off_tnext);
+        P.tdone = reinterpret_cast<uint32_t *>(b + p.off_tdone);
+        P.qcap = (uint32_t)p.qcap;
+        P.segs = reinterpret_cast<Seg *>(b + p.off_segs);
+        P.segcap = (uint32_t)p.segcap;
+        P.items = reinterpret_cast<Item *>(b + p.off_items);
+        P.itemcap = (uint32_t)p.itemcap;
+        P.counts = reinterpret_cast<uint32_t *>(b + p.off_counts);
+        P.bstart = reinterpret_cast<uint32_t *>(b + p.off_bstart);
+        P.status = reinterpret_cast<uint32_t *>(b + p.off_status);
+        P.statuscap = p.statuscap;
+        P.pwl = reinterpret_cast<float *>(b + p.off_pwl);
+        P.trainbuf = reinterpret_cast<uint32_t *>(b + p.off_train);
+        P.traincap = (uint32_t)p.traincap;
+        ws->epoch = 0;
+    }
+    if (!ws->sms) {
+        ce = cudaDeviceGetAttribute(&ws->sms, cudaDevAttrMultiProcessorCount, dev);
+        if (ce != cudaSuccess) return cuda_err(ce);
+        if (dev < 64 && !g_attr_set[dev]) {
+            ce = cudaFuncSetAttribute(k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)SMEM_BYTES);
+            if (ce != cudaSuccess) return cuda_err(ce);
+            g_attr_set[dev] = true;
+        }
+        ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ws->occ, k_persistent, BLOCK, SMEM_BYTES);
+        if (ce != cudaSuccess) return cuda_err(ce);
+        if (ws->occ < 1) return ZSORT_ERR_CUDA;
+    }
+    *out = ws;
+    return ZSORT_OK;
+}
+
+bool opts_valid(const zsort_opts &o)
+{
+    if (o.struct_size != sizeof(zsort_opts)) return false;
+    if (o.mapper > 1) return false;
+    if (o.kmax < MIN_K || o.kmax > NB_MAX || (o.kmax & (o.kmax - 1))) return false;
+    if (o.leaf_target < 16 || o.leaf_target > (1u << 24)) return false;
+    if (o.large_min < (uint32_t)LEAF_CAP || o.large_min >= (1u << 30)) return false;
+    if (o.sample < (uint32_t)PWL_P || o.sample > (uint32_t)SAMPLE_MAX) return false;
+    if (o.learn_min < o.sample) return false;
+    if (!(o.fallback_ratio > 0.0f)) return false;
+    if (o.guard_level < 1) return false;
+    return true;
+}
+
+// Enqueues one sort (single array when off == nullptr).
+int launch(uint64_t *keys, uint32_t *vals, unsigned long long n, const uint64_t *off,
+           unsigned long long nseg, const zsort_opts &o, cudaStream_t stream)
+{
+    std::lock_guard<std::mutex> lock(g_mu);
+    Workspace *ws = nullptr;
+    int rc = get_workspace(stream, n, nseg, o.large_min, &ws);
+    if (rc != ZSORT_OK) return rc;
+    Params P = ws->P;
+    P.ukeys = keys;
+    P.uvals = vals;
+    P.n = n;
+    P.epoch = ++ws->epoch;
+    if (P.epoch == 0) P.epoch = ws->epoch = 1;
+    P.kmax = o.kmax;
+    P.leaf_target = o.leaf_target;
+    P.large_min = o.large_min;
+    P.learn_min = o.learn_min;
+    P.sample = o.sample;
+    P.mapper = o.mapper;
+    P.guard_level = o.guard_level;
+    P.fallback_ratio = o.fallback_ratio;
+    P.seed = o.seed;
+    P.wait_ns = (unsigned long long)o.wait_limit_ms * 1000000ull;
+    cudaError_t ce = cudaMemsetAsync(P.ctl, 0, sizeof(Ctl), stream);
+    if (ce != cudaSuccess) return cuda_err(ce);
+    const unsigned int gi = (unsigned int)div_up(nseg, 256);
+    k_init_segments<<<gi, 256, 0, stream>>>(P, off, nseg);
+    k_init_publish<<<1, 32, 0, stream>>>(P, nseg);
+    int per_sm = o.ctas_per_sm ? (int)std::min<uint32_t>(o.ctas_per_sm, (uint32_t)ws->occ) : ws->occ;
+    k_persistent<<<ws->sms * per_sm, BLOCK, SMEM_BYTES, stream>>>(P);
+    ce = cudaGetLastError();
+    return cuda_err(ce);
+}
+
+int encode(void *keys, unsigned long long n, uint32_t type, int inverse, cudaStream_t stream)
+{
+    if (type == ZSORT_KEY_U64 || n == 0) return ZSORT_OK;
+    unsigned int grid = (unsigned int)std::min<unsigned long long>(div_up(n, 256), 4096);
+    k_encode<<<grid, 256, 0, stream>>>(static_cast<uint64_t *>(keys), n, type, inverse);
+    return cuda_err(cudaGetLastError());
+}
+
+Workspace *find_ws(cudaStream_t stream)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    for (Workspace *w : g_ws)
+        if (w->device == dev && w->stream == stream) return w;
+    return nullptr;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- C ABI
+extern "C" {
+
+void zsort_default_opts(zsort_opts *o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->struct_size = sizeof(zsort_opts);
+    o->mapper = ZSORT_MAP_ZSCORE;
+    o->kmax = 1024;
+    o->leaf_target = 2048;
+    o->large_min = 65536;
+    o->learn_min = 1u << 20;
+    o->sample = 65536;
+    o->fallback_ratio = 4.0f;
+    o->seed = 0x5eed2605ull;
+    o->guard_level = 8;
+    o->ctas_per_sm = 0;
+    o->wait_limit_ms = 2000;
+}
+
+int zsort_pairs_ex(void *keys, uint32_t key_type, uint32_t *vals, uint64_t n, const zsort_opts *opts,
+                   zsort_stream_t stream)
+{
+    zsort_opts o;
+    if (opts)
+        o = *opts;
+    else
+        zsort_default_opts(&o);
+    if (!opts_valid(o)) return ZSORT_ERR_INVALID;
+    if (key_type > ZSORT_KEY_F64 || n > ZSORT_MAX_N) return ZSORT_ERR_INVALID;
+    if (n <= 1) return ZSORT_OK;
+    if (!keys || !vals) return ZSORT_ERR_INVALID;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int rc = encode(keys, n, key_type, 0, st);
+    if (rc != ZSORT_OK) return rc;
+    rc = launch(static_cast<uint64_t *>(keys), vals, n, nullptr, 1, o, st);
+    if (rc != ZSORT_OK) return rc;
+    return encode(keys, n, key_type, 1, st);
+}
+
+int zsort_pairs(uint64_t *keys, uint32_t *vals, uint64_t n, zsort_stream_t stream)
+{
+    return zsort_pairs_ex(keys, ZSORT_KEY_U64, vals, n, nullptr, stream);
+}
+
+int zsort_pairs_i64(int64_t *keys, uint32_t *vals, uint64_t n, zsort_stream_t stream)
+{
+    return zsort_pairs_ex(keys, ZSORT_KEY_I64, vals, n, nullptr, stream);
+}
+
+int zsort_pairs_f64(double *keys, uint32_t *vals, uint64_t n, zsort_stream_t stream)
+{
+    return zsort_pairs_ex(keys, ZSORT_KEY_F64, vals, n, nullptr, stream);
+}
+
+int zsort_segmented_ex(uint64_t *keys, uint32_t *vals, uint64_t n, const uint64_t *seg_offsets,
+                       uint64_t nseg, const zsort_opts *opts, zsort_stream_t stream)
+{
+    zsort_opts o;
+    if (opts)
+        o = *opts;
+    else
+        zsort_default_opts(&o);
+    if (!opts_valid(o)) return ZSORT_ERR_INVALID;
+    if (n > ZSORT_MAX_N || nseg > (1ull << 31)) return ZSORT_ERR_INVALID;
+    if (nseg == 0) return ZSORT_OK;
+    if (!seg_offsets || (n > 0 && (!keys || !vals))) return ZSORT_ERR_INVALID;
+    return launch(keys, vals, n, seg_offsets, nseg, o, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int zsort_segmented(uint64_t *keys, uint32_t *vals, uint64_t n, const uint64_t *seg_offsets, uint64_t nseg,
+                    zsort_stream_t stream)
+{
+    return zsort_segmented_ex(keys, vals, n, seg_offsets, nseg, nullptr, stream);
+}
+
+int zsort_reserve(uint64_t n, uint64_t nseg, zsort_stream_t stream)
+{
+    if (n > ZSORT_MAX_N) return ZSORT_ERR_INVALID;
+    zsort_opts o;
+    zsort_default_opts(&o);
+    std::lock_guard<std::mutex> lock(g_mu);
+    Workspace *ws = nullptr;
+    return get_workspace(reinterpret_cast<cudaStream_t>(stream), n, std::max<uint64_t>(nseg, 1),
+                         o.large_min, &ws);
+}
+
+int zsort_release(void)
+{
+    std::lock_guard<std::mutex> lock(g_mu);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return ZSORT_ERR_CUDA;
+    int rc = ZSORT_OK;
+    std::vector<Workspace *> keep;
+    for (Workspace *w : g_ws) {
+        if (w->device != dev) {
+            keep.push_back(w);
+            continue;
+        }
+        if (w->block && cudaFree(w->block) != cudaSuccess) rc = ZSORT_ERR_CUDA;
+        delete w;
+    }
+    g_ws.swap(keep);
+    return rc;
+}
+
+int zsort_sync_status(zsort_stream_t stream)
+{
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t ce = cudaStreamSynchronize(st);
+    if (ce != cudaSuccess) return cuda_err(ce);
+    std::lock_guard<std::mutex> lock(g_mu);
+    Workspace *ws = find_ws(st);
+    if (!ws || !ws->block) return ZSORT_OK;
+    unsigned int err = 0;
+    ce = cudaMemcpy(&err, &ws->P.ctl->error, sizeof(err), cudaMemcpyDeviceToHost);
+    if (ce != cudaSuccess) return cuda_err(ce);
+    if (err) {
+        unsigned int zero = 0;
+        cudaMemcpy(&ws->P.ctl->error, &zero, sizeof(zero), cudaMemcpyHostToDevice);
+    }
+    return (int)err;
+}
+
+int zsort_last_stats(zsort_stream_t stream, zsort_stats *out)
+{
+    if (!out) return ZSORT_ERR_INVALID;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t ce = cudaStreamSynchronize(st);
+    if (ce != cudaSuccess) return cuda_err(ce);
+    std::lock_guard<std::mutex> lock(g_mu);
+    Workspace *ws = find_ws(st);
+    std::memset(out, 0, sizeof(*out));
+    if (!ws || !ws->block) return ZSORT_OK;
+    Ctl c;
+    ce = cudaMemcpy(&c, ws->P.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost);
+    if (ce != cudaSuccess) return cuda_err(ce);
+    out->n = ws->P.n;
+    out->partitions_large = c.n_large;
+    out->partitions_small = c.n_small;
+    out->leaves = c.n_leaves;
+    out->leaf_fallbacks = c.n_leaf_fb;
+    out->copies = c.n_copies;
+    out->learned_accepted = c.n_learn_ok;
+    out->learned_rejected = c.n_learn_rej;
+    out->guard_levels = c.n_guard;
+    out->max_level = c.max_level;
+    out->bytes_algorithmic = c.bytes;
+    out->tasks = c.tasks;
+    out->persistent_ctas = (uint64_t)ws->sms * ws->occ;
+    out->top_mean_d = c.top_mean_d;
+    out->top_sd = c.top_sd;
+    out->top_min = c.top_min;
+    out->top_max = c.top_max;
+    out->top_k = c.top_k;
+    out->top_map = c.top_map;
+    return ZSORT_OK;
+}
+
+const char *zsort_strerror(int code)
+{
+    switch (code) {
+    case ZSORT_OK: return "ok";
+    case ZSORT_ERR_INVALID: return "invalid argument";
+    case ZSORT_ERR_NOMEM: return "device allocation failed";
+    case ZSORT_ERR_CUDA: return "CUDA runtime error";
+    case ZSORT_ERR_TIMEOUT: return "bounded device wait expired";
+    case ZSORT_ERR_BAD_OFFSETS: return "segment offsets decrease or exceed n";
+    case ZSORT_ERR_CAPACITY: return "internal device queue overflowed";
+    case ZSORT_ERR_INTERNAL: return "device consistency check failed";
+    default: return "unknown status";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,529 @@
+// zsort_device.cuh -- device-side building blocks of the GB300 zSort.
+//
+// Data layout in HBM (all arrays structure-of-arrays, 64-bit keys, 32-bit
+// payloads):  the caller's keys/vals, a scratch pair of the same length
+// (scratch[i] mirrors user[i]; a bucket keeps its index range in both), and
+// the bookkeeping pools of the persistent executor (queue entries, large
+// segment descriptors, work items, bucket counts, look-back status rows,
+// learned-map tables and training buffers).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace zs {
+
+// ---------------------------------------------------------------- constants
+constexpr int BLOCK = 256;                // threads per CTA
+constexpr int WARPS = BLOCK / 32;
+constexpr int IPT = 16;                   // items per thread per tile
+constexpr int TILE = BLOCK * IPT;         // 4096 pairs per tile
+constexpr int WARP_SPAN = 32 * IPT;       // contiguous elements per warp
+constexpr int NB_MAX = 1024;              // buckets per partition pass
+constexpr int LEAF_CAP = TILE;            // a bucket (group) this small is finished in smem
+constexpr int RANK_SMALL = BLOCK;         // leaves this small are ranked by counting
+constexpr int PWL_P = 256;                // pieces of the learned map
+constexpr int SAMPLE_MAX = 65536;         // largest training sample
+constexpr int MIN_K = 16;                 // fewest buckets of a partition pass
+constexpr int MAX_LEVEL = 48;             // hard bound on the partition depth
+constexpr uint32_t INVALID = 0xFFFFFFFFu;
+constexpr uint32_t FLAG_A = 1u << 30;     // look-back: tile aggregate only
+constexpr uint32_t FLAG_P = 2u << 30;     // look-back: inclusive prefix
+constexpr uint32_t VAL_MASK = (1u << 30) - 1;
+
+// Status codes (mirror zsort.h).
+constexpr int ST_TIMEOUT = -4;
+constexpr int ST_BAD_OFFSETS = -5;
+constexpr int ST_CAPACITY = -6;
+constexpr int ST_INTERNAL = -7;
+
+enum MapKind : uint32_t { MAP_Z = 0, MAP_PWL = 1, MAP_RANGE = 2 };
+enum TaskType : uint32_t {
+    T_NONE = 0,
+    T_LSTATS = 1,    // large segment: statistics tile
+    T_LTRAIN = 2,    // large segment: learned-map training (one CTA)
+    T_LHIST = 3,     // large segment: histogram tile
+    T_LSCATTER = 4,  // large segment: look-back stable scatter tile
+    T_MPART = 5,     // medium segment: whole partition pass by one CTA
+    T_FINISH = 6,    // leaf (group of small buckets): shared-memory sort
+    T_COPY = 7       // all-equal large segment living in scratch: copy back
+};
+
+// ---------------------------------------------------------------- records
+// A large segment: partitioned by many CTAs, phase by phase.
+struct Seg {
+    unsigned long long off;      // first element (absolute index)
+    unsigned long long mn, mx;   // exact min / max (atomics)
+    unsigned long long s1[2];    // exact sum of keys, 128-bit (atomics)
+    unsigned long long s2[3];    // exact sum of squared keys, 192-bit
+    unsigned long long status_base;  // first look-back word
+    double mean_d, sd;           // mean of key - min, population sd
+    float zc;                    // z-score map multiplier: (k/4) / sd
+    float escale;                // learned map: 2^-bitlen(max - min)
+    uint32_t len, k, tiles, level, buf;
+    uint32_t kind;               // MapKind
+    uint32_t rshift, rmult;      // range map
+    uint32_t train_slot;         // learned map training buffer, INVALID if none
+    uint32_t pad;
+};
+
+// A leaf group or a medium segment.
+struct Item {
+    unsigned long long off;
+    uint32_t len;
+    uint16_t buf;
+    uint16_t level;
+};
+
+struct Entry {
+    uint32_t type, arg, ntiles, pad;
+};
+
+struct Ctl {
+    unsigned int q_head, q_alloc, pending, error;
+    unsigned int seg_alloc, item_alloc, train_alloc, init_leaf;
+    unsigned int init_med, pad0, pad1, pad2;
+    unsigned long long status_alloc;
+    unsigned long long progress;
+    // counters reported through zsort_stats
+    unsigned long long n_large, n_small, n_leaves, n_leaf_fb, n_copies;
+    unsigned long long n_learn_ok, n_learn_rej, n_guard, max_level, bytes, tasks;
+    double top_mean_d, top_sd;
+    unsigned long long top_min, top_max;
+    unsigned int top_k, top_map;
+};
+
+struct Params {
+    uint64_t *ukeys;
+    uint32_t *uvals;
+    uint64_t *skeys;
+    uint32_t *svals;
+    unsigned long long n;
+    Ctl *ctl;
+    Entry *entries;
+    uint32_t *ready, *tnext, *tdone;
+    uint32_t qcap, epoch;
+    Seg *segs;
+    uint32_t segcap;
+    Item *items;
+    uint32_t itemcap;
+    uint32_t *counts;   // segcap * NB_MAX
+    uint32_t *bstart;   // segcap * NB_MAX
+    uint32_t *status;
+    unsigned long long statuscap;
+    float *pwl;         // segcap * (PWL_P + 1)
+    uint32_t *trainbuf; // traincap * 2 * SAMPLE_MAX
+    uint32_t traincap;
+    // options
+    uint32_t kmax, leaf_target, large_min, learn_min, sample, mapper, guard_level;
+    float fallback_ratio;
+    unsigned long long seed;
+    unsigned long long wait_ns;
+};
+
+// ---------------------------------------------------------------- memory ops
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed(uint32_t *p, uint32_t v)
+{
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_release(uint32_t *p, uint32_t v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long globaltimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void set_error(const Params &P, int code)
+{
+    atomicCAS(&P.ctl->error, 0u, (unsigned int)code);
+}
+__device__ __forceinline__ bool has_error(const Params &P)
+{
+    return ld_relaxed(&P.ctl->error) != 0;
+}
+
+__device__ __forceinline__ uint32_t bitlen64(unsigned long long x)
+{
+    return x ? 64u - (uint32_t)__clzll((long long)x) : 0u;
+}
+__device__ __forceinline__ uint32_t pow2ceil32(uint32_t x)
+{
+    return x <= 1 ? 1u : 1u << (32 - __clz((int)(x - 1)));
+}
+
+// ------------------------------------------------------- exact moments
+// Exact running sums of a set of keys: count is implicit, S1 = sum x
+// (128-bit), S2 = sum x^2 (192-bit), exact min / max.  Integer sums are
+// associative, so the result does not depend on the reduction order.
+struct Acc {
+    unsigned long long mn, mx;
+    unsigned __int128 s1;
+    unsigned __int128 s2lo;
+    unsigned long long s2hi;
+};
+
+__device__ __forceinline__ void acc_init(Acc &a)
+{
+    a.mn = ~0ull;
+    a.mx = 0ull;
+    a.s1 = 0;
+    a.s2lo = 0;
+    a.s2hi = 0;
+}
+__device__ __forceinline__ void acc_key(Acc &a, unsigned long long x)
+{
+    a.mn = x < a.mn ? x : a.mn;
+    a.mx = x > a.mx ? x : a.mx;
+    a.s1 += x;
+    unsigned __int128 sq = (unsigned __int128)x * x;
+    unsigned __int128 t = a.s2lo + sq;
+    a.s2hi += (t < sq) ? 1ull : 0ull;
+    a.s2lo = t;
+}
+__device__ __forceinline__ void acc_merge(Acc &a, const Acc &b)
+{
+    a.mn = b.mn < a.mn ? b.mn : a.mn;
+    a.mx = b.mx > a.mx ? b.mx : a.mx;
+    a.s1 += b.s1;
+    unsigned __int128 t = a.s2lo + b.s2lo;
+    a.s2hi += b.s2hi + ((t < b.s2lo) ? 1ull : 0ull);
+    a.s2lo = t;
+}
+__device__ __forceinline__ unsigned long long shfl_down64(unsigned long long v, int o)
+{
+    return __shfl_down_sync(0xffffffffu, v, o);
+}
+__device__ __forceinline__ unsigned __int128 shfl_down128(unsigned __int128 v, int o)
+{
+    unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)(v >> 64);
+    lo = __shfl_down_sync(0xffffffffu, lo, o);
+    hi = __shfl_down_sync(0xffffffffu, hi, o);
+    return ((unsigned __int128)hi << 64) | lo;
+}
+
+// Block reduction; the result is valid in thread 0.  `sh` holds WARPS Accs.
+__device__ void acc_block_reduce(Acc &a, Acc *sh)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        Acc b;
+        b.mn = shfl_down64(a.mn, o);
+        b.mx = shfl_down64(a.mx, o);
+        b.s1 = shfl_down128(a.s1, o);
+        b.s2lo = shfl_down128(a.s2lo, o);
+        b.s2hi = shfl_down64(a.s2hi, o);
+        acc_merge(a, b);
+    }
+    if (lane == 0) sh[warp] = a;
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int w = 1; w < WARPS; w++) acc_merge(a, sh[w]);
+    __syncthreads();
+}
+
+// Exact multiword atomic accumulation: each limb is added atomically and
+// the carry out of a limb is added to the next one, so the final value is
+// the exact sum whatever the order of the contributions.
+__device__ void atomic_add_wide(unsigned long long *w, const unsigned long long *v, int nw)
+{
+    unsigned long long carry = 0;
+    for (int i = 0; i < nw; i++) {
+        unsigned long long add = v[i] + carry;
+        unsigned long long c = (add < v[i]) ? 1ull : 0ull;
+        if (add) {
+            unsigned long long old = atomicAdd(&w[i], add);
+            c += (old + add < old) ? 1ull : 0ull;
+        }
+        carry = c;
+    }
+}
+
+// Rounds a 256-bit unsigned integer (4 limbs, little endian) to double.
+__device__ double u256_to_double(const unsigned long long *x)
+{
+    int top = 3;
+    while (top > 0 && x[top] == 0) top--;
+    if (top == 0) return __ull2double_rn(x[0]);
+    int lz = __clzll((long long)x[top]);
+    unsigned long long hi = x[top], lo = x[top - 1];
+    unsigned long long m = lz ? (hi << lz) | (lo >> (64 - lz)) : hi;
+    unsigned long long rest = lz ? (lo << lz) : lo;
+    for (int i = top - 2; i >= 0; i--) rest |= x[i];
+    m |= rest ? 1ull : 0ull;  // sticky bit: 64 > 53 + 2 bits keeps the rounding exact
+    return ldexp(__ull2double_rn(m), 64 * top - lz);
+}
+
+// mean of (key - min) and population variance from exact sums (Alg. 1's
+// statistics, evaluated exactly and rounded once to double).
+__device__ void moments_from_sums(unsigned long long n, unsigned long long mn,
+                                  const unsigned long long s1w[2], const unsigned long long s2w[3],
+                                  double *mean_d, double *var)
+{
+    unsigned __int128 s1 = ((unsigned __int128)s1w[1] << 64) | s1w[0];
+    unsigned __int128 sum_d = s1 - (unsigned __int128)n * mn;  // exact, >= 0
+    unsigned long long sd4[4] = {(unsigned long long)sum_d, (unsigned long long)(sum_d >> 64), 0, 0};
+    *mean_d = u256_to_double(sd4) / (double)n;
+    // n * S2 (S2 < 2^192, n < 2^32)
+    unsigned long long a[4];
+    unsigned __int128 c = 0;
+    for (int i = 0; i < 3; i++) {
+        c += (unsigned __int128)s2w[i] * n;
+        a[i] = (unsigned long long)c;
+        c >>= 64;
+    }
+    a[3] = (unsigned long long)c;
+    // S1^2 (S1 < 2^128)
+    unsigned long long p[4] = {0, 0, 0, 0};
+    unsigned long long s1l[2] = {s1w[0], s1w[1]};
+    for (int i = 0; i < 2; i++) {
+        unsigned __int128 cc = 0;
+        for (int j = 0; j < 2; j++) {
+            cc += (unsigned __int128)s1l[i] * s1l[j] + p[i + j];
+            p[i + j] = (unsigned long long)cc;
+            cc >>= 64;
+        }
+        int q = i + 2;
+        while (cc && q < 4) {
+            cc += p[q];
+            p[q] = (unsigned long long)cc;
+            cc >>= 64;
+            q++;
+        }
+    }
+    // n * S2 - S1^2 >= 0 (Cauchy-Schwarz)
+    unsigned long long r[4];
+    unsigned long long borrow = 0;
+    for (int i = 0; i < 4; i++) {
+        unsigned long long t = a[i] - p[i];
+        unsigned long long b1 = a[i] < p[i];
+        unsigned long long t2 = t - borrow;
+        unsigned long long b2 = t < borrow;
+        r[i] = t2;
+        borrow = b1 | b2;
+    }
+    double dn = (double)n;
+    *var = borrow ? 0.0 : u256_to_double(r) / (dn * dn);
+}
+
+// ------------------------------------------------------------ bucket maps
+// One definition serves the histogram and the scatter, so both passes
+// compute bit-identical buckets.  Every map is monotone non-decreasing in
+// the key, which is all the sort's exactness needs.
+struct MapSm {
+    unsigned long long mn;
+    uint32_t kind, k, K, rshift, rmult;
+    float zc, escale;
+    float q[PWL_P + 1];
+};
+
+__device__ __forceinline__ uint32_t map_key(const MapSm &m, unsigned long long key)
+{
+    unsigned long long d = key - m.mn;
+    if (m.kind == MAP_Z) {
+        // Eq. 1 with |z_min| = (mean - min)/sd: h = (key - min) * (k/4) / sd.
+        float f = __fmul_rn(__ull2float_rn(d), m.zc);
+        uint32_t b = __float2uint_rz(f);
+        return b < m.k ? b : m.k - 1;
+    }
+    if (m.kind == MAP_RANGE) {
+        if (m.rmult == 0) return (uint32_t)d;  // range < k: counting map
+        return __umulhi((uint32_t)(d >> m.rshift), m.rmult);
+    }
+    // learned piecewise-linear CDF over u = fl32(d) * 2^-E
+    float u = __fmul_rn(__ull2float_rn(d), m.escale);
+    int s = 0;
+#pragma unroll
+    for (int st = PWL_P / 2; st; st >>= 1)
+        if (m.q[s + st] <= u) s += st;
+    float lo = m.q[s], hi = m.q[s + 1];
+    float frac = 0.0f;
+    if (hi > lo) frac = __fdiv_rn(__fsub_rn(u, lo), __fsub_rn(hi, lo));
+    frac = fminf(fmaxf(frac, 0.0f), 0x1.fffffep-1f);
+    uint32_t w = __float2uint_rz(__fmul_rn(frac, (float)m.K));
+    w = w < m.K ? w : m.K - 1;
+    return (uint32_t)s * m.K + w;
+}
+
+// Range map parameters: floor-like (d >> shift) * mult / 2^32, monotone,
+// bucket(0) = 0, bucket(range) >= 1 for k >= 16, never above k - 1.
+__device__ __forceinline__ void range_params(unsigned long long range, uint32_t k, uint32_t *rshift,
+                                             uint32_t *rmult)
+{
+    if (range < k) {
+        *rshift = 0;
+        *rmult = 0;
+        return;
+    }
+    uint32_t e = bitlen64(range);
+    uint32_t sh = e > 32 ? e - 32 : 0;
+    unsigned long long rr = range >> sh;
+    *rshift = sh;
+    *rmult = (uint32_t)((((unsigned long long)k) << 32) / (rr + 1));
+}
+
+// --------------------------------------------------------------- smem
+struct SmemTile {
+    unsigned long long key[TILE];    // 32 KB
+    uint32_t val[TILE];              // 16 KB
+    uint16_t bkt[TILE];              // 8 KB (bucket, or index in the bitonic fallback)
+    uint16_t wcnt[WARPS * NB_MAX];   // 16 KB: per-warp counts, then warp prefixes
+    uint32_t tcount[NB_MAX];         // tile count per bucket
+    uint32_t tstart[NB_MAX];         // tile-local exclusive start per bucket
+    uint32_t gdelta[NB_MAX];         // global position - tile position (mod 2^32)
+    uint32_t hist[NB_MAX];           // histogram (single-CTA passes)
+    uint32_t cursor[NB_MAX];         // running bucket cursor (single-CTA passes)
+    uint32_t bs[NB_MAX];             // bucket starts (single-CTA passes)
+    uint32_t wsum[WARPS + 1];
+    Acc acc[WARPS];
+    MapSm map;
+    uint32_t task[6];
+    uint32_t flag, flag2, n_leaf, n_med, n_large, n_large_ok, item_base, e_base;
+    unsigned long long red64[WARPS * 2];
+};
+
+// Lists built when a partition's children are classified; alias the tile.
+struct ChildList {
+    uint32_t leaf_off[NB_MAX], leaf_len[NB_MAX];
+    uint32_t med_off[NB_MAX], med_len[NB_MAX];
+    uint32_t lg_off[NB_MAX], lg_len[NB_MAX], lg_sid[NB_MAX];
+};
+static_assert(sizeof(ChildList) <= sizeof(unsigned long long) * TILE, "child lists alias keys");
+
+// ------------------------------------------------------------ block scan
+// Exclusive scan of in[0..nb) into out (may alias); returns the total.
+__device__ uint32_t block_exclusive_scan(const uint32_t *in, uint32_t *out, uint32_t nb, uint32_t *wsum)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t per = (nb + BLOCK - 1) / BLOCK;  // <= 4
+    const uint32_t base = threadIdx.x * per;
+    uint32_t loc[4];
+    uint32_t sum = 0;
+#pragma unroll
+    for (uint32_t j = 0; j < 4; j++) {
+        if (j < per) {
+            uint32_t idx = base + j;
+            uint32_t v = idx < nb ? in[idx] : 0u;
+            loc[j] = sum;
+            sum += v;
+        }
+    }
+    uint32_t x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < WARPS ? wsum[lane] : 0u;
+        uint32_t incl = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane < WARPS) wsum[lane] = incl - w;
+        if (lane == WARPS - 1) wsum[WARPS] = incl;  // the total
+    }
+    __syncthreads();
+    uint32_t excl = wsum[warp] + x - sum;
+#pragma unroll
+    for (uint32_t j = 0; j < 4; j++) {
+        if (j < per) {
+            uint32_t idx = base + j;
+            if (idx < nb) out[idx] = excl + loc[j];
+        }
+    }
+    uint32_t total = wsum[WARPS];
+    __syncthreads();
+    return total;
+}
+
+// ------------------------------------------------------------ tile ranking
+// Stable multisplit of one tile.  Element (warp w, slot i, lane l) is the
+// tile's element w*WARP_SPAN + i*32 + l, so (w, i, l) order is input order.
+// In each slot the warp's lanes with equal buckets are found with
+// __match_any_sync; their rank is the count of earlier equal lanes plus the
+// warp's running count for that bucket.  Warp prefixes per bucket and a
+// block scan over buckets then give each element its position in the tile
+// ordered by (bucket, input position).  Buckets INVALID are skipped.
+__device__ void tile_rank(const uint32_t (&b)[IPT], uint32_t (&pos)[IPT], uint32_t nb, SmemTile &s)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint32_t i = threadIdx.x; i < (uint32_t)WARPS * nb; i += BLOCK) s.wcnt[i] = 0;
+    __syncthreads();
+    const uint32_t lt = (1u << lane) - 1u;
+    uint16_t *wc = s.wcnt + warp * nb;
+#pragma unroll
+    for (int i = 0; i < IPT; i++) {
+        uint32_t peers = __match_any_sync(0xffffffffu, b[i]);
+        int leader = __ffs(peers) - 1;
+        uint32_t before = 0;
+        if (lane == leader && b[i] != INVALID) {
+            before = wc[b[i]];
+            wc[b[i]] = (uint16_t)(before + __popc(peers));
+        }
+        before = __shfl_sync(0xffffffffu, before, leader);
+        pos[i] = before + __popc(peers & lt);
+    }
+    __syncthreads();
+    for (uint32_t q = threadIdx.x; q < nb; q += BLOCK) {
+        uint32_t run = 0;
+#pragma unroll
+        for (int w = 0; w < WARPS; w++) {
+            uint32_t c = s.wcnt[w * nb + q];
+            s.wcnt[w * nb + q] = (uint16_t)run;
+            run += c;
+        }
+        s.tcount[q] = run;
+    }
+    __syncthreads();
+    block_exclusive_scan(s.tcount, s.tstart, nb, s.wsum);
+#pragma unroll
+    for (int i = 0; i < IPT; i++)
+        if (b[i] != INVALID) pos[i] += s.tstart[b[i]] + s.wcnt[warp * nb + b[i]];
+}
+
+// ------------------------------------------------------------ sampling
+// SplitMix64 (Steele, Lea, Flood, OOPSLA 2014) output for state x + 1 step.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x)
+{
+    unsigned long long z = x + 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+// Position of sample i of m drawn from [0, len): one per stratum.
+__device__ __forceinline__ unsigned long long sample_pos(unsigned long long seed, unsigned long long len,
+                                                         unsigned long long m, unsigned long long i)
+{
+    unsigned long long lo = (i * len) / m;
+    unsigned long long hi = ((i + 1) * len) / m;
+    unsigned long long w = hi - lo;
+    return lo + (w ? splitmix64(seed + i) % w : 0ull);
+}
+
+}  // namespace zs

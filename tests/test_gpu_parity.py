@@ -1,0 +1,181 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+The result of a stable sort is unique, so the bar is bit-exact keys and
+payloads.  At sizes the oracle finishes in seconds the two are compared
+element by element; at the full 2^28 size the output is checked by
+properties that pin it completely (keys non-decreasing, payload i is the
+input position of output key i, and ties keep ascending positions).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2605_14419_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - CPU machine
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2605_14419_gb300 as z  # noqa: E402
+from paper_2605_14419_gb300 import build as zbuild  # noqa: E402
+
+zbuild.build()
+DEV = torch.device("cuda:0")
+
+
+def to_dev(keys, vals):
+    k = torch.from_numpy(np.ascontiguousarray(keys).view(np.int64)).to(DEV)
+    v = torch.from_numpy(np.ascontiguousarray(vals).view(np.int32)).to(DEV)
+    return k, v
+
+
+def gpu_sort(keys, vals, opts=None, key_type="u64"):
+    k, v = to_dev(keys, vals)
+    z.sort_pairs(k, v, key_type=key_type, opts=opts)
+    return k.cpu().numpy().view(keys.dtype), v.cpu().numpy().view(np.uint32)
+
+
+def assert_same_as_oracle(keys, vals=None, opts=None):
+    vals = inputs.index_payload(keys.size) if vals is None else vals
+    gk, gv = gpu_sort(keys, vals, opts)
+    ok, ov = oracle.zsort_pairs(keys, vals)
+    assert np.array_equal(gk, ok), "keys differ"
+    assert np.array_equal(gv, ov), "payloads differ"
+
+
+FAMILIES = list(inputs.FAMILIES)
+SIZES = [2, 3, 31, 255, 256, 257, 1000, 4095, 4096, 4097, 8193, 65535, 65536, 65537, 200_003]
+
+
+@pytest.mark.parametrize("n", SIZES)
+@pytest.mark.parametrize("family", FAMILIES)
+def test_parity_sizes(family, n):
+    assert_same_as_oracle(inputs.FAMILIES[family](n, seed=n + 1))
+
+
+def test_config1_uniform_65536_seed0():
+    assert_same_as_oracle(inputs.uniform(65_536, 0))
+
+
+@pytest.mark.parametrize("family", FAMILIES)
+def test_config2_paper_scale_1e7(family):
+    assert_same_as_oracle(inputs.FAMILIES[family](10_000_000, seed=2))
+
+
+@pytest.mark.parametrize("gen", [inputs.lognormal, inputs.gaussian_mixture, inputs.dense_interval_u64])
+@pytest.mark.parametrize("mapper", [z.MAP_ZSCORE, z.MAP_LEARNED])
+def test_skewed_both_mappers(gen, mapper):
+    keys = gen(3_000_000, seed=4)
+    assert_same_as_oracle(keys, opts=z.default_opts(mapper=mapper))
+
+
+def test_edge_cases():
+    # empty, single, all equal, two values, extremes, random payload
+    for keys in (np.zeros(0, np.uint64), np.array([5], np.uint64), np.full(100_000, 7, np.uint64),
+                 np.array([2 ** 64 - 1, 0] * 50_000, np.uint64),
+                 np.array([2 ** 63 + 1, 2 ** 63] * 40_000, np.uint64)):
+        vals = inputs.index_payload(keys.size)
+        if keys.size <= 1:
+            k, v = to_dev(keys, vals) if keys.size else (torch.zeros(0, dtype=torch.int64, device=DEV),
+                                                          torch.zeros(0, dtype=torch.int32, device=DEV))
+            z.sort_pairs(k, v)
+            assert np.array_equal(k.cpu().numpy().view(np.uint64), keys)
+            continue
+        assert_same_as_oracle(keys)
+    rng = np.random.default_rng(3)
+    keys = rng.integers(0, 1000, 300_000).astype(np.uint64)
+    vals = rng.integers(0, 2 ** 32, 300_000, dtype=np.uint64).astype(np.uint32)
+    assert_same_as_oracle(keys, vals)
+
+
+def test_small_kmax_forces_deep_recursion():
+    keys = inputs.uniform(2_000_000, 5)
+    assert_same_as_oracle(keys, opts=z.default_opts(kmax=16, leaf_target=64, large_min=8192))
+
+
+def test_guard_level_range_map():
+    keys = inputs.lognormal(1_000_000, 6)
+    assert_same_as_oracle(keys, opts=z.default_opts(guard_level=1))
+
+
+def test_int64_and_float64_keys():
+    x = inputs.dense_interval_i64(500_000, 7)
+    vals = inputs.index_payload(x.size)
+    gk, gv = gpu_sort(x.astype(np.int64), vals, key_type="i64")
+    u = oracle.key_from_i64(x)
+    ok, ov = oracle.zsort_pairs(u, vals)
+    assert np.array_equal(gv, ov) and np.array_equal(gk, oracle.key_to_i64(ok))
+    f = inputs.normal_f64_specials(500_000, 8)
+    gk, gv = gpu_sort(f, vals, key_type="f64")
+    u = oracle.key_from_f64(f)
+    ok, ov = oracle.zsort_pairs(u, vals)
+    assert np.array_equal(gv, ov)
+    assert np.array_equal(gk.view(np.uint64), oracle.key_to_f64(ok).view(np.uint64))
+
+
+def test_segmented_matches_oracle():
+    keys, vals, off, _ = inputs.segmented(300, 9, lo=1, hi=300_000)
+    k, v = to_dev(keys, vals)
+    offs = torch.from_numpy(off.view(np.int64)).to(DEV)
+    z.sort_segmented(k, v, offs)
+    ok, ov = oracle.zsort_segmented(keys, vals, off)
+    assert np.array_equal(k.cpu().numpy().view(np.uint64), ok)
+    assert np.array_equal(v.cpu().numpy().view(np.uint32), ov)
+
+
+def test_segmented_empty_and_untouched_edges():
+    keys = inputs.uniform(10_000, 10)
+    vals = inputs.index_payload(keys.size)
+    off = np.array([100, 100, 5000, 5000, 9000], dtype=np.uint64)  # empty segments; outside untouched
+    k, v = to_dev(keys, vals)
+    z.sort_segmented(k, v, torch.from_numpy(off.view(np.int64)).to(DEV))
+    gk = k.cpu().numpy().view(np.uint64)
+    assert np.array_equal(gk[:100], keys[:100]) and np.array_equal(gk[9000:], keys[9000:])
+    ok, ov = oracle.zsort_segmented(keys, vals, off)
+    assert np.array_equal(gk, ok)
+
+
+def test_bad_offsets_reported_and_data_untouched_then_recovers():
+    keys = inputs.uniform(10_000, 11)
+    vals = inputs.index_payload(keys.size)
+    k, v = to_dev(keys, vals)
+    bad = torch.tensor([0, 6000, 5000, 10_000], dtype=torch.int64, device=DEV)
+    with pytest.raises(z.ZsortError) as ei:
+        z.sort_segmented(k, v, bad)
+    assert ei.value.code == z.ERR_BAD_OFFSETS
+    assert np.array_equal(k.cpu().numpy().view(np.uint64), keys)
+    past_end = torch.tensor([0, 10_001], dtype=torch.int64, device=DEV)
+    with pytest.raises(z.ZsortError):
+        z.sort_segmented(k, v, past_end)
+    assert_same_as_oracle(keys)  # the next call works
+
+
+def _check_full_properties(k_in, k_out, v_out):
+    """Sorted, stable, and payload = input position of the output key."""
+    pos = v_out.to(torch.int64) & 0xFFFFFFFF
+    # payload is a permutation and points at the same key in the input
+    assert bool(torch.equal(k_in[pos], k_out))
+    seen = torch.zeros(k_in.numel(), dtype=torch.int32, device=DEV)
+    seen.index_add_(0, pos, torch.ones_like(pos, dtype=torch.int32))
+    assert bool((seen == 1).all())
+    # order: compare as unsigned by flipping the sign bit
+    s = k_out ^ torch.tensor(-(2 ** 63), dtype=torch.int64, device=DEV)
+    assert bool((s[1:] >= s[:-1]).all())
+    eq = s[1:] == s[:-1]
+    assert bool((pos[1:][eq] > pos[:-1][eq]).all())
+
+
+@pytest.mark.parametrize("gen", [inputs.lognormal, inputs.gaussian_mixture])
+@pytest.mark.parametrize("mapper", [z.MAP_ZSCORE, z.MAP_LEARNED])
+def test_full_size_2p28_properties(gen, mapper):
+    n = 1 << 28
+    keys = gen(n, seed=3)
+    k_in = torch.from_numpy(keys.view(np.int64)).to(DEV)
+    k = k_in.clone()
+    v = torch.arange(n, dtype=torch.int32, device=DEV)
+    z.sort_pairs(k, v, opts=z.default_opts(mapper=mapper))
+    _check_full_properties(k_in, k, v)
+    del k_in, k, v
+    torch.cuda.empty_cache()
