@@ -117,6 +117,15 @@ typedef struct {
     uint64_t top_min, top_max;  /* top level: exact min and max                 */
     uint32_t top_k;             /* top level: buckets                           */
     uint32_t top_map;           /* top level: map used (ZSORT_MAP_*, 2 = range) */
+    /* device time of the persistent kernel's tasks, summed over CTAs (ns);
+       index = task type: 1 statistics tile, 2 learned-map training, 3
+       histogram tile, 4 look-back scatter tile, 5 single-CTA partition,
+       6 shared-memory finish, 7 copy */
+    uint64_t task_ns[8];
+    uint64_t task_count[8];
+    uint64_t handler_ns;        /* tasks whose phase-completion work ran (incl.)  */
+    uint64_t idle_ns;           /* time CTAs spent waiting for work               */
+    uint64_t busy_window_ns;    /* first task start to last task end              */
 } zsort_stats;
 
 /* Fills *o with the defaults (z-score map, kmax 1024, ...). */

@@ -453,9 +453,12 @@ void oracle_pwl_train(const uint64_t *sample, uint64_t m, uint64_t mn,
 }
 
 /* Inference: piece s = #{ 0 < j < P : q[j] <= u }; within it the linear
- * interpolation frac = (u - q[s]) / (q[s+1] - q[s]) (0 for an empty piece),
- * clipped to [0, 1 - 2^-24]; bucket = s*K + min(K-1, floor(frac * K)),
- * K = k / P.  All arithmetic is IEEE binary32 with round-to-nearest. */
+ * interpolation frac = (u - q[s]) * r[s] with the reciprocal width
+ * r[s] = 1 / (q[s+1] - q[s]) (0 for an empty piece), clipped to
+ * [0, 1 - 2^-24]; bucket = s*K + min(K-1, floor(frac * K)), K = k / P.
+ * All arithmetic is IEEE binary32 with round-to-nearest; frac is monotone
+ * in u inside a piece and every piece owns its own K buckets, so the map is
+ * monotone non-decreasing. */
 uint32_t oracle_pwl_bucket(uint64_t key, uint64_t mn, uint64_t mx,
                            const float *q, uint32_t P, uint32_t k)
 {
@@ -467,9 +470,10 @@ uint32_t oracle_pwl_bucket(uint64_t key, uint64_t mn, uint64_t mx,
     volatile float lo = q[s], hi = q[s + 1];
     float frac = 0.0f;
     if (hi > lo) {
-        volatile float num = u - lo;
         volatile float den = hi - lo;
-        frac = num / den;
+        volatile float r = 1.0f / den;
+        volatile float num = u - lo;
+        frac = num * r;
     }
     if (frac < 0.0f) frac = 0.0f;
     if (frac > 0.99999994f) frac = 0.99999994f; /* 1 - 2^-24 */

@@ -79,10 +79,19 @@ class Stats(ctypes.Structure):
         ("top_max", ctypes.c_uint64),
         ("top_k", ctypes.c_uint32),
         ("top_map", ctypes.c_uint32),
+        ("task_ns", ctypes.c_uint64 * 8),
+        ("task_count", ctypes.c_uint64 * 8),
+        ("handler_ns", ctypes.c_uint64),
+        ("idle_ns", ctypes.c_uint64),
+        ("busy_window_ns", ctypes.c_uint64),
     ]
 
     def as_dict(self) -> dict:
-        return {name: getattr(self, name) for name, _ in self._fields_}
+        out = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            out[name] = list(v) if isinstance(v, ctypes.Array) else v
+        return out
 
 
 def header_functions() -> list[str]:

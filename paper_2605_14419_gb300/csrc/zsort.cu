@@ -24,32 +24,56 @@ using namespace zs;
 // ---------------------------------------------------------------- kernels
 __global__ void __launch_bounds__(BLOCK, 2) k_persistent(Params P)
 {
-    extern __shared__ __align__(16) unsigned char smraw[];
+    extern __shared__ __align__(128) unsigned char smraw[];
     SmemTile &s = *reinterpret_cast<SmemTile *>(smraw);
+    if (threadIdx.x == 0) {
+        mbar_init(&s.bar[0]);
+        mbar_init(&s.bar[1]);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    Pipe pp;
+    pp.uses[0] = pp.uses[1] = 0;
+    QCache qc;
+    qc.e = INVALID;
+    unsigned long long t_idle0 = 0, t_task0 = 0;
     for (;;) {
-        if (threadIdx.x == 0) dequeue(P, s.task);
-        __syncthreads();
-        const uint32_t type = s.task[0], arg = s.task[1], tile = s.task[2];
-        const uint32_t e = s.task[3], ntiles = s.task[4];
-        __syncthreads();
-        if (type == T_NONE) return;
-        switch (type) {
-        case T_LSTATS: task_lstats(P, arg, tile, s); break;
-        case T_LTRAIN: task_ltrain(P, arg, s); break;
-        case T_LHIST: task_lhist(P, arg, tile, s); break;
-        case T_LSCATTER: task_lscatter(P, arg, tile, s); break;
-        case T_MPART: task_mpart(P, load_item(P, arg + tile), s); break;
-        case T_FINISH: task_finish(P, load_item(P, arg + tile), s); break;
-        case T_COPY: task_copy(P, arg, tile); break;
-        default: set_error(P, ST_INTERNAL); break;
+        if (threadIdx.x == 0) {
+            t_idle0 = globaltimer();
+            dequeue(P, s.task, qc);
+            t_task0 = globaltimer();
+            atomicAdd(&P.ctl->idle_ns, t_task0 - t_idle0);
+            if (s.task[0] != T_NONE) atomicMin(&P.ctl->t_first, t_task0);
         }
         __syncthreads();
+        const uint32_t type = s.task[0], arg = s.task[1], tile0 = s.task[2];
+        const uint32_t e = s.task[3], ntiles = s.task[4], count = s.task[5];
+        __syncthreads();
+        if (type == T_NONE) return;
+        for (uint32_t j = 0; j < count; j++) {
+            const uint32_t tile = tile0 + j;
+            switch (type) {
+            case T_LSTATS: task_lstats(P, arg, tile, s, pp); break;
+            case T_LTRAIN: task_ltrain(P, arg, s); break;
+            case T_LHIST: task_lhist(P, arg, tile, s, pp); break;
+            case T_LSCATTER: task_lscatter(P, arg, tile, s, pp); break;
+            case T_MPART: task_mpart(P, load_item(P, arg + tile), s, pp); break;
+            case T_FINISH: task_finish(P, load_item(P, arg + tile), s, pp); break;
+            case T_COPY: task_copy(P, arg, tile); break;
+            default: set_error(P, ST_INTERNAL); break;
+            }
+            fence_proxy_async();  // order this task's smem writes before later bulk copies
+            __syncthreads();
+        }
         if (threadIdx.x == 0) {
+            unsigned long long t1 = globaltimer();
+            atomicAdd(&P.ctl->task_ns[type & 7], t1 - t_task0);
+            atomicAdd(&P.ctl->task_cnt[type & 7], (unsigned long long)count);
             __threadfence();
-            uint32_t old = atomicAdd(&P.tdone[e], 1u);
-            s.flag2 = (old + 1 == ntiles) ? 1u : 0u;
+            uint32_t old = atomicAdd(&P.tdone[e], count);
+            s.flag2 = (old + count == ntiles) ? 1u : 0u;
             atomicAdd(&P.ctl->progress, 1ull);
-            atomicAdd(&P.ctl->tasks, 1ull);
+            atomicAdd(&P.ctl->tasks, (unsigned long long)count);
         }
         __syncthreads();
         if (s.flag2) {
@@ -65,6 +89,11 @@ __global__ void __launch_bounds__(BLOCK, 2) k_persistent(Params P)
                 __threadfence();
                 atomicSub(&P.ctl->pending, 1u);
             }
+        }
+        if (threadIdx.x == 0) {
+            unsigned long long t2 = globaltimer();
+            if (s.flag2) atomicAdd(&P.ctl->handler_ns, t2 - t_task0);
+            atomicMax(&P.ctl->t_last, t2);
         }
     }
 }
@@ -98,7 +127,9 @@ __global__ void k_init_segments(Params P, const uint64_t *off, unsigned long lon
     if (len > P.large_min) {
         const uint32_t kk = choose_k(P, (uint32_t)len);
         const uint32_t tiles = (uint32_t)((len + TILE - 1) / TILE);
-        const unsigned long long need = (unsigned long long)tiles * kk;
+        const uint32_t ct = choose_chunk_tiles(P, tiles);
+        const uint32_t chunks = (tiles + ct - 1) / ct;
+        const unsigned long long need = 2ull * chunks * kk;
         const uint32_t sid = atomicAdd(&C->seg_alloc, 1u);
         unsigned long long sb = ~0ull;
         if (sid < P.segcap) sb = atomicAdd(&C->status_alloc, need);
@@ -113,6 +144,8 @@ __global__ void k_init_segments(Params P, const uint64_t *off, unsigned long lon
             S->len = (uint32_t)len;
             S->k = kk;
             S->tiles = tiles;
+            S->chunk_tiles = ct;
+            S->chunks = chunks;
             S->level = 0;
             S->buf = 0;
             S->kind = MAP_Z;
@@ -147,8 +180,9 @@ __global__ void k_init_publish(Params P, unsigned long long nseg)
             C->pending = 0;
             return;
         }
-        q_write(P, e++, T_LSTATS, sid, P.segs[sid].tiles);
+        q_write(P, e++, T_LSTATS, sid, P.segs[sid].chunks);
     }
+    C->t_first = ~0ull;
     C->q_alloc = e;
     C->pending = e;
     C->item_alloc = (uint32_t)(2 * nseg);
@@ -207,11 +241,10 @@ struct Plan {
 Plan make_plan(unsigned long long n, unsigned long long nseg, unsigned long long large_min)
 {
     Plan p{};
-    const unsigned long long tiles = div_up(n, TILE);
     p.qcap = n / 128 + 4 * nseg + 4096;
     p.segcap = 3 * (n / (large_min + 1)) + 64;
     p.itemcap = 2 * nseg + n / 32 + 4096;
-    p.statuscap = 2 * (tiles + 64) * (unsigned long long)NB_MAX;
+    p.statuscap = (n / (2 * TILE) + 8192) * 256ull;
     p.traincap = std::min<unsigned long long>(p.segcap, 32);
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -231,7 +264,7 @@ Plan make_plan(unsigned long long n, unsigned long long nseg, unsigned long long
     p.off_counts = take(p.segcap * NB_MAX * 4);
     p.off_bstart = take(p.segcap * NB_MAX * 4);
     p.off_status = take(p.statuscap * 4);
-    p.off_pwl = take(p.segcap * (PWL_P + 1) * 4);
+    p.off_pwl = take(p.segcap * PWL_STRIDE * 4);
     p.off_train = take(p.traincap * 2 * SAMPLE_MAX * 4);
     p.total = o;
     return p;
@@ -364,13 +397,15 @@ int launch(uint64_t *keys, uint32_t *vals, unsigned long long n, const uint64_t 
     P.fallback_ratio = o.fallback_ratio;
     P.seed = o.seed;
     P.wait_ns = (unsigned long long)o.wait_limit_ms * 1000000ull;
+    P.user_aligned = ((reinterpret_cast<uintptr_t>(keys) | reinterpret_cast<uintptr_t>(vals)) & 15u) == 0;
+    int per_sm = o.ctas_per_sm ? (int)std::min<uint32_t>(o.ctas_per_sm, (uint32_t)ws->occ) : ws->occ;
+    P.nctas = (uint32_t)(ws->sms * per_sm);
     cudaError_t ce = cudaMemsetAsync(P.ctl, 0, sizeof(Ctl), stream);
     if (ce != cudaSuccess) return cuda_err(ce);
     const unsigned int gi = (unsigned int)div_up(nseg, 256);
     k_init_segments<<<gi, 256, 0, stream>>>(P, off, nseg);
     k_init_publish<<<1, 32, 0, stream>>>(P, nseg);
-    int per_sm = o.ctas_per_sm ? (int)std::min<uint32_t>(o.ctas_per_sm, (uint32_t)ws->occ) : ws->occ;
-    k_persistent<<<ws->sms * per_sm, BLOCK, SMEM_BYTES, stream>>>(P);
+    k_persistent<<<P.nctas, BLOCK, SMEM_BYTES, stream>>>(P);
     ce = cudaGetLastError();
     return cuda_err(ce);
 }
@@ -551,6 +586,13 @@ int zsort_last_stats(zsort_stream_t stream, zsort_stats *out)
     out->top_max = c.top_max;
     out->top_k = c.top_k;
     out->top_map = c.top_map;
+    for (int i = 0; i < 8; i++) {
+        out->task_ns[i] = c.task_ns[i];
+        out->task_count[i] = c.task_cnt[i];
+    }
+    out->handler_ns = c.handler_ns;
+    out->idle_ns = c.idle_ns;
+    out->busy_window_ns = (c.t_last > c.t_first && c.t_first != ~0ull) ? c.t_last - c.t_first : 0;
     return ZSORT_OK;
 }
 

@@ -15,18 +15,21 @@ namespace zs {
 // ---------------------------------------------------------------- constants
 constexpr int BLOCK = 256;                // threads per CTA
 constexpr int WARPS = BLOCK / 32;
-constexpr int IPT = 16;                   // items per thread per tile
-constexpr int TILE = BLOCK * IPT;         // 4096 pairs per tile
-constexpr int WARP_SPAN = 32 * IPT;       // contiguous elements per warp
+constexpr int IPT = 8;                    // items per thread of a streamed tile
+constexpr int TILE = BLOCK * IPT;         // 2048 pairs per streamed tile
+constexpr int WARP_SPAN = 32 * IPT;       // contiguous elements per warp and tile
+constexpr int LEAF_IPT = 16;              // items per thread of a leaf
+constexpr int LEAF_CAP = BLOCK * LEAF_IPT;  // 4096: a bucket (group) this small is finished in smem
+constexpr int LEAF_SPAN = 32 * LEAF_IPT;
+constexpr int PAD = 8;                    // smem slack for 16-byte aligned bulk copies
 constexpr int NB_MAX = 1024;              // buckets per partition pass
-constexpr int LEAF_CAP = TILE;            // a bucket (group) this small is finished in smem
 constexpr int RANK_SMALL = BLOCK;         // leaves this small are ranked by counting
 constexpr int PWL_P = 256;                // pieces of the learned map
 constexpr int SAMPLE_MAX = 65536;         // largest training sample
 constexpr int MIN_K = 16;                 // fewest buckets of a partition pass
 constexpr int MAX_LEVEL = 48;             // hard bound on the partition depth
 constexpr uint32_t INVALID = 0xFFFFFFFFu;
-constexpr uint32_t FLAG_A = 1u << 30;     // look-back: tile aggregate only
+constexpr uint32_t FLAG_A = 1u << 30;     // look-back: chunk aggregate only
 constexpr uint32_t FLAG_P = 2u << 30;     // look-back: inclusive prefix
 constexpr uint32_t VAL_MASK = (1u << 30) - 1;
 
@@ -57,13 +60,16 @@ struct Seg {
     unsigned long long s2[3];    // exact sum of squared keys, 192-bit
     unsigned long long status_base;  // first look-back word
     double mean_d, sd;           // mean of key - min, population sd
-    float zc;                    // z-score map multiplier: (k/4) / sd
+    float zc;                    // z-score map multiplier: (k/4) / sd * 2^zsh
     float escale;                // learned map: 2^-bitlen(max - min)
+    uint32_t zsh;                // z-score map: keys - min are shifted right by zsh
     uint32_t len, k, tiles, level, buf;
     uint32_t kind;               // MapKind
     uint32_t rshift, rmult;      // range map
     uint32_t train_slot;         // learned map training buffer, INVALID if none
-    uint32_t pad;
+    uint32_t chunk_tiles;        // tiles per chunk task
+    uint32_t chunks;             // chunk tasks per phase
+    uint32_t pad[3];
 };
 
 // A leaf group or a medium segment.
@@ -90,6 +96,9 @@ struct Ctl {
     double top_mean_d, top_sd;
     unsigned long long top_min, top_max;
     unsigned int top_k, top_map;
+    // device time per task type (ns, summed over CTAs), handler and idle time
+    unsigned long long task_ns[8], task_cnt[8], handler_ns, idle_ns;
+    unsigned long long t_first, t_last;
 };
 
 struct Params {
@@ -108,9 +117,11 @@ struct Params {
     uint32_t itemcap;
     uint32_t *counts;   // segcap * NB_MAX
     uint32_t *bstart;   // segcap * NB_MAX
-    uint32_t *status;
+    uint32_t *status;            // look-back words and chunk offsets: 2 * chunks * k per segment
     unsigned long long statuscap;
-    float *pwl;         // segcap * (PWL_P + 1)
+    uint32_t nctas;              // CTAs of the persistent launch
+    uint32_t user_aligned;       // caller's keys and vals 16-byte aligned: bulk copies allowed
+    float *pwl;         // segcap * PWL_STRIDE: breakpoints q[0..P], reciprocals r[0..P)
     uint32_t *trainbuf; // traincap * 2 * SAMPLE_MAX
     uint32_t traincap;
     // options
@@ -330,39 +341,66 @@ __device__ void moments_from_sums(unsigned long long n, unsigned long long mn,
 // One definition serves the histogram and the scatter, so both passes
 // compute bit-identical buckets.  Every map is monotone non-decreasing in
 // the key, which is all the sort's exactness needs.
+constexpr int PWL_BINS = 2048;  // learned map: bins of the normalised key's float bits
+constexpr int PWL_STRIDE = 2 * PWL_P + 1;
 struct MapSm {
     unsigned long long mn;
-    uint32_t kind, k, K, rshift, rmult;
+    uint32_t kind, k, K, rshift, rmult, zsh;
     float zc, escale;
-    float q[PWL_P + 1];
+    float q[PWL_P + 1];          // learned map: breakpoints
+    float r[PWL_P];              // learned map: 1 / (q[s+1] - q[s]), 0 for an empty piece
+    uint8_t seg0[PWL_BINS + 1];  // learned map: piece holding the lower edge of each bin
 };
+
+// fl32(d), round to nearest even, without the 64-bit conversion instruction:
+// the top 32 significant bits with the lost bits OR-ed into the lowest one
+// (a sticky bit below the guard bit keeps the rounding exact), converted,
+// then scaled back by a power of two (exact).
+__device__ __forceinline__ float u64_to_f32_rn(unsigned long long d)
+{
+    const uint32_t hi = (uint32_t)(d >> 32);
+    const uint32_t s = hi ? 32u - (uint32_t)__clz((int)hi) : 0u;
+    const unsigned long long lost = d & ((1ull << s) - 1ull);
+    const uint32_t m = (uint32_t)(d >> s) | (lost ? 1u : 0u);
+    return __fmul_rn(__uint2float_rn(m), __int_as_float((int)(127u + s) << 23));
+}
+
+// Learned map on the normalised key u = fl32(key - min) * 2^-E in [0, 1]:
+// piece s = the last breakpoint q[s] <= u (found from the bin table, then a
+// binary search inside the bin), linear interpolation inside the piece.
+__device__ __forceinline__ uint32_t pwl_bucket_u(const MapSm &m, float u)
+{
+    const uint32_t c = __float_as_uint(u) >> 19;  // u <= 1.0f: c <= 2032
+    uint32_t lo = m.seg0[c], hi = m.seg0[c + 1];
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (m.q[mid] <= u)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    float frac = __fmul_rn(__fsub_rn(u, m.q[lo]), m.r[lo]);
+    frac = fminf(fmaxf(frac, 0.0f), 0x1.fffffep-1f);
+    uint32_t w = __float2uint_rz(__fmul_rn(frac, (float)m.K));
+    w = w < m.K ? w : m.K - 1;
+    return lo * m.K + w;
+}
 
 __device__ __forceinline__ uint32_t map_key(const MapSm &m, unsigned long long key)
 {
-    unsigned long long d = key - m.mn;
+    const unsigned long long d = key - m.mn;
     if (m.kind == MAP_Z) {
-        // Eq. 1 with |z_min| = (mean - min)/sd: h = (key - min) * (k/4) / sd.
-        float f = __fmul_rn(__ull2float_rn(d), m.zc);
-        uint32_t b = __float2uint_rz(f);
+        // Eq. 1 with |z_min| = (mean - min)/sd: h = (key - min) * (k/4) / sd,
+        // on d >> zsh (a 32-bit value; zc carries the 2^zsh back).
+        const float f = __fmul_rn(__uint2float_rz((uint32_t)(d >> m.zsh)), m.zc);
+        const uint32_t b = __float2uint_rz(f);
         return b < m.k ? b : m.k - 1;
     }
     if (m.kind == MAP_RANGE) {
         if (m.rmult == 0) return (uint32_t)d;  // range < k: counting map
         return __umulhi((uint32_t)(d >> m.rshift), m.rmult);
     }
-    // learned piecewise-linear CDF over u = fl32(d) * 2^-E
-    float u = __fmul_rn(__ull2float_rn(d), m.escale);
-    int s = 0;
-#pragma unroll
-    for (int st = PWL_P / 2; st; st >>= 1)
-        if (m.q[s + st] <= u) s += st;
-    float lo = m.q[s], hi = m.q[s + 1];
-    float frac = 0.0f;
-    if (hi > lo) frac = __fdiv_rn(__fsub_rn(u, lo), __fsub_rn(hi, lo));
-    frac = fminf(fmaxf(frac, 0.0f), 0x1.fffffep-1f);
-    uint32_t w = __float2uint_rz(__fmul_rn(frac, (float)m.K));
-    w = w < m.K ? w : m.K - 1;
-    return (uint32_t)s * m.K + w;
+    return pwl_bucket_u(m, __fmul_rn(u64_to_f32_rn(d), m.escale));
 }
 
 // Range map parameters: floor-like (d >> shift) * mult / 2^32, monotone,
@@ -383,32 +421,45 @@ __device__ __forceinline__ void range_params(unsigned long long range, uint32_t 
 }
 
 // --------------------------------------------------------------- smem
-struct SmemTile {
-    unsigned long long key[TILE];    // 32 KB
-    uint32_t val[TILE];              // 16 KB
-    uint16_t bkt[TILE];              // 8 KB (bucket, or index in the bitonic fallback)
-    uint16_t wcnt[WARPS * NB_MAX];   // 16 KB: per-warp counts, then warp prefixes
-    uint32_t tcount[NB_MAX];         // tile count per bucket
-    uint32_t tstart[NB_MAX];         // tile-local exclusive start per bucket
-    uint32_t gdelta[NB_MAX];         // global position - tile position (mod 2^32)
-    uint32_t hist[NB_MAX];           // histogram (single-CTA passes)
-    uint32_t cursor[NB_MAX];         // running bucket cursor (single-CTA passes)
-    uint32_t bs[NB_MAX];             // bucket starts (single-CTA passes)
-    uint32_t wsum[WARPS + 1];
-    Acc acc[WARPS];
-    MapSm map;
-    uint32_t task[6];
-    uint32_t flag, flag2, n_leaf, n_med, n_large, n_large_ok, item_base, e_base;
-    unsigned long long red64[WARPS * 2];
-};
-
-// Lists built when a partition's children are classified; alias the tile.
+// Lists built when a partition's children are classified; alias the tiles.
 struct ChildList {
     uint32_t leaf_off[NB_MAX], leaf_len[NB_MAX];
     uint32_t med_off[NB_MAX], med_len[NB_MAX];
     uint32_t lg_off[NB_MAX], lg_len[NB_MAX], lg_sid[NB_MAX];
 };
-static_assert(sizeof(ChildList) <= sizeof(unsigned long long) * TILE, "child lists alias keys");
+
+struct TileBuf {
+    unsigned long long key[TILE + PAD];
+    uint32_t val[TILE + PAD];
+};
+struct LeafBuf {
+    unsigned long long key[LEAF_CAP + 2 * PAD];
+    uint32_t val[LEAF_CAP + 2 * PAD];
+};
+
+struct SmemTile {
+    union {
+        TileBuf buf[2];   // double-buffered streamed tiles (bulk-copy targets)
+        LeafBuf leaf;     // one leaf of up to LEAF_CAP pairs
+        ChildList children;
+    } u;
+    uint16_t bkt[LEAF_CAP];          // bucket of each staged element / bitonic index
+    uint16_t wcnt[WARPS * NB_MAX];   // per-warp counts, then warp prefixes
+    uint32_t tcount[NB_MAX];         // tile count per bucket
+    uint32_t tstart[NB_MAX];         // tile-local exclusive start per bucket
+    uint32_t gdelta[NB_MAX];         // global position - tile position (mod 2^32)
+    uint32_t hist[NB_MAX];           // histogram
+    uint32_t cursor[NB_MAX];         // running bucket cursor
+    uint32_t bs[NB_MAX];             // bucket starts
+    uint32_t wsum[WARPS + 1];
+    Acc acc[WARPS];
+    MapSm map;
+    unsigned long long bar[2];       // mbarriers of the two tile buffers
+    uint32_t task[8];
+    uint32_t flag, flag2, n_leaf, n_med, n_large, n_large_ok, item_base, e_base;
+    unsigned long long red64[WARPS * 2];
+};
+static_assert(sizeof(LeafBuf) <= sizeof(TileBuf) * 2, "leaf fits the tile buffers");
 
 // ------------------------------------------------------------ block scan
 // Exclusive scan of in[0..nb) into out (may alias); returns the total.
@@ -462,28 +513,43 @@ __device__ uint32_t block_exclusive_scan(const uint32_t *in, uint32_t *out, uint
 }
 
 // ------------------------------------------------------------ tile ranking
-// Stable multisplit of one tile.  Element (warp w, slot i, lane l) is the
-// tile's element w*WARP_SPAN + i*32 + l, so (w, i, l) order is input order.
-// In each slot the warp's lanes with equal buckets are found with
-// __match_any_sync; their rank is the count of earlier equal lanes plus the
-// warp's running count for that bucket.  Warp prefixes per bucket and a
-// block scan over buckets then give each element its position in the tile
-// ordered by (bucket, input position).  Buckets INVALID are skipped.
-__device__ void tile_rank(const uint32_t (&b)[IPT], uint32_t (&pos)[IPT], uint32_t nb, SmemTile &s)
+// Stable multisplit of one tile of N = BLOCK * NI elements.  Element (warp
+// w, slot i, lane l) is the tile's element w*32*NI + i*32 + l, so (w, i, l)
+// order is input order.  In each slot the warp's lanes with equal buckets are
+// found with __match_any_sync; their rank is the count of earlier equal lanes
+// plus the warp's running count for that bucket.  Warp prefixes per bucket
+// and a block scan over buckets then give each element its position in the
+// tile ordered by (bucket, input position).  Buckets INVALID are skipped.
+// On return s.tcount / s.tstart hold the per-bucket counts and starts.
+template <int NI, int NBITS>
+__device__ void tile_rank_bits(const uint32_t (&b)[NI], uint32_t (&pos)[NI], uint32_t nb, SmemTile &s)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (uint32_t i = threadIdx.x; i < (uint32_t)WARPS * nb; i += BLOCK) s.wcnt[i] = 0;
+    {
+        uint32_t *w32 = reinterpret_cast<uint32_t *>(s.wcnt);
+        for (uint32_t i = threadIdx.x; i < (uint32_t)WARPS * nb / 2; i += BLOCK) w32[i] = 0u;
+    }
     __syncthreads();
     const uint32_t lt = (1u << lane) - 1u;
     uint16_t *wc = s.wcnt + warp * nb;
 #pragma unroll
-    for (int i = 0; i < IPT; i++) {
-        uint32_t peers = __match_any_sync(0xffffffffu, b[i]);
-        int leader = __ffs(peers) - 1;
+    for (int i = 0; i < NI; i++) {
+        // lanes with an equal bucket: AND over the bucket's bits of the ballot
+        // of that bit (or of its complement), then separate INVALID lanes
+        const uint32_t bi = b[i];
+        uint32_t peers = __ballot_sync(0xffffffffu, bi == INVALID);
+        peers = bi == INVALID ? peers : ~peers;
+#pragma unroll
+        for (int bit = 0; bit < NBITS; bit++) {
+            const uint32_t f = (bi >> bit) & 1u;
+            const uint32_t bal = __ballot_sync(0xffffffffu, f);
+            peers &= f ? bal : ~bal;
+        }
+        const int leader = __ffs(peers) - 1;
         uint32_t before = 0;
-        if (lane == leader && b[i] != INVALID) {
-            before = wc[b[i]];
-            wc[b[i]] = (uint16_t)(before + __popc(peers));
+        if (lane == leader && bi != INVALID) {
+            before = wc[bi];
+            wc[bi] = (uint16_t)(before + __popc(peers));
         }
         before = __shfl_sync(0xffffffffu, before, leader);
         pos[i] = before + __popc(peers & lt);
@@ -502,8 +568,67 @@ __device__ void tile_rank(const uint32_t (&b)[IPT], uint32_t (&pos)[IPT], uint32
     __syncthreads();
     block_exclusive_scan(s.tcount, s.tstart, nb, s.wsum);
 #pragma unroll
-    for (int i = 0; i < IPT; i++)
+    for (int i = 0; i < NI; i++)
         if (b[i] != INVALID) pos[i] += s.tstart[b[i]] + s.wcnt[warp * nb + b[i]];
+}
+
+// Bucket ids below nb <= NB_MAX = 2^10: ten ballots identify equal buckets.
+template <int NI>
+__device__ __forceinline__ void tile_rank(const uint32_t (&b)[NI], uint32_t (&pos)[NI], uint32_t nb, SmemTile &s)
+{
+    tile_rank_bits<NI, 10>(b, pos, nb, s);
+}
+
+// ------------------------------------------------------------ bulk copies
+// Tiles are staged in shared memory by the Blackwell bulk-copy engine
+// (cp.async.bulk, completion counted on an mbarrier), double-buffered so
+// that the next tile streams in while the current one is processed.
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_arrive(unsigned long long *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, unsigned long long *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+// Waits for the given phase parity of an mbarrier; false after limit_ns.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity, unsigned long long limit_ns)
+{
+    const uint32_t a = smem_u32(bar);
+    unsigned long long t0 = 0;
+    for (uint32_t it = 0;; it++) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((it & 15u) == 15u) {
+            unsigned long long now = globaltimer();
+            if (t0 == 0)
+                t0 = now;
+            else if (now - t0 > limit_ns)
+                return false;
+        }
+    }
 }
 
 // ------------------------------------------------------------ sampling

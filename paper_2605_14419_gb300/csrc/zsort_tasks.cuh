@@ -3,12 +3,15 @@
 // Every (sub)array goes through the steps of Alg. 1: statistics (exact
 // min, max, mean and population sd), the bucket map (Eq. 1, or the learned
 // map, or the range map of the progress guard), a histogram, an exclusive
-// scan for the bucket starts, and a stable scatter; its buckets become the
+// scan for the bucket offsets, and a stable scatter; its buckets become the
 // next level's (sub)arrays, or leaves finished in shared memory.
-//   large (sub)arrays  -> one task per 4096-element tile and per phase, with
-//                         a decoupled look-back across tiles in the scatter
+//   large (sub)arrays  -> per phase, one task per chunk of consecutive tiles;
+//                         the histogram phase finds each chunk's offsets with
+//                         a decoupled look-back across chunks, so the scatter
+//                         phase streams its chunk with plain running cursors
 //   medium (sub)arrays -> one task that runs every phase in one CTA
 //   leaves             -> one task that sorts a group of small buckets in smem
+// Tiles reach shared memory through double-buffered bulk copies (TMA).
 #pragma once
 #include "zsort_device.cuh"
 
@@ -46,13 +49,19 @@ __device__ void q_write(const Params &P, uint32_t e, uint32_t type, uint32_t arg
 __device__ void q_release_all(const Params &P, uint32_t e, uint32_t count)
 {
     __threadfence();
-    for (uint32_t i = 0; i < count; i++) st_release(&P.ready[e + i], P.epoch);
+    for (uint32_t i = 0; i < count; i++) st_relaxed(&P.ready[e + i], P.epoch);
 }
 
-// Thread 0: next (entry, tile) to run, or T_NONE when all work is done or an
-// error was recorded.  A wait without any progress anywhere for longer than
-// P.wait_ns records ST_TIMEOUT.
-__device__ void dequeue(const Params &P, uint32_t *out)
+// Thread 0's cached copy of the entry at the queue head.
+struct QCache {
+    uint32_t e, type, arg, ntiles;
+};
+
+// Thread 0: claims the next tiles of the entry at the queue head.  out =
+// {type, arg, first tile, entry, ntiles, count}; type T_NONE when all work
+// is done or an error was recorded.  A wait without any progress anywhere for
+// longer than P.wait_ns records ST_TIMEOUT.
+__device__ void dequeue(const Params &P, uint32_t *out, QCache &qc)
 {
     Ctl *C = P.ctl;
     unsigned long long last = ld_relaxed64(&C->progress);
@@ -61,32 +70,39 @@ __device__ void dequeue(const Params &P, uint32_t *out)
     for (;;) {
         if (ld_relaxed(&C->error)) return;
         uint32_t e = ld_relaxed(&C->q_head);
-        if (e < P.qcap && ld_acquire(&P.ready[e]) == P.epoch) {
-            uint32_t type = __ldcg(&P.entries[e].type);
-            uint32_t arg = __ldcg(&P.entries[e].arg);
-            uint32_t ntiles = __ldcg(&P.entries[e].ntiles);
-            uint32_t t = atomicAdd(&P.tnext[e], 1u);
-            if (t < ntiles) {
-                out[0] = type;
-                out[1] = arg;
-                out[2] = t;
-                out[3] = e;
-                out[4] = ntiles;
-                return;
+        if (e != qc.e) {
+            if (e < P.qcap && ld_acquire(&P.ready[e]) == P.epoch) {
+                uint4 en = __ldcg(reinterpret_cast<const uint4 *>(P.entries + e));
+                qc.e = e;
+                qc.type = en.x;
+                qc.arg = en.y;
+                qc.ntiles = en.z;
+            } else {
+                if (ld_acquire(&C->pending) == 0) return;
+                unsigned long long pr = ld_relaxed64(&C->progress), now = globaltimer();
+                if (pr != last) {
+                    last = pr;
+                    t0 = now;
+                } else if (now - t0 > P.wait_ns) {
+                    set_error(P, ST_TIMEOUT);
+                    return;
+                }
+                __nanosleep(128);
+                continue;
             }
-            atomicCAS(&C->q_head, e, e + 1);
-            continue;
         }
-        if (ld_acquire(&C->pending) == 0) return;
-        unsigned long long pr = ld_relaxed64(&C->progress), now = globaltimer();
-        if (pr != last) {
-            last = pr;
-            t0 = now;
-        } else if (now - t0 > P.wait_ns) {
-            set_error(P, ST_TIMEOUT);
+        const uint32_t claim = qc.type == T_FINISH ? 2u : 1u;
+        uint32_t t = atomicAdd(&P.tnext[e], claim);
+        if (t < qc.ntiles) {
+            out[0] = qc.type;
+            out[1] = qc.arg;
+            out[2] = t;
+            out[3] = e;
+            out[4] = qc.ntiles;
+            out[5] = min(claim, qc.ntiles - t);
             return;
         }
-        __nanosleep(200);
+        atomicCAS(&C->q_head, e, e + 1);
     }
 }
 
@@ -112,6 +128,11 @@ __device__ __forceinline__ uint32_t *vals_of(const Params &P, uint32_t buf)
 {
     return buf ? P.svals : P.uvals;
 }
+// Bulk copies need 16-byte aligned bases: always true of the scratch arrays.
+__device__ __forceinline__ bool bulk_ok(const Params &P, uint32_t buf)
+{
+    return buf || P.user_aligned;
+}
 
 // Buckets of one partition pass: enough for leaf_target elements per bucket.
 __device__ __forceinline__ uint32_t choose_k(const Params &P, uint32_t len)
@@ -119,6 +140,16 @@ __device__ __forceinline__ uint32_t choose_k(const Params &P, uint32_t len)
     uint32_t k = pow2ceil32((len + P.leaf_target - 1) / P.leaf_target);
     k = k < (uint32_t)MIN_K ? (uint32_t)MIN_K : k;
     return k > P.kmax ? P.kmax : k;
+}
+
+// Tiles per chunk task of a large (sub)array: about four chunks per CTA of
+// the whole grid, at least four tiles each.
+__device__ __forceinline__ uint32_t choose_chunk_tiles(const Params &P, uint32_t tiles)
+{
+    uint32_t per = 4 * P.nctas;
+    uint32_t ct = (tiles + per - 1) / per;
+    ct = ct < 4u ? 4u : ct;
+    return ct > 512u ? 512u : ct;
 }
 
 // Fills the map for a (sub)array from its exact sums: Eq. 1 (z-score) unless
@@ -137,6 +168,7 @@ __device__ void map_from_sums(const Params &P, unsigned long long n, unsigned lo
     unsigned long long range = mx - mn;
     m.escale = __int_as_float((127 - (int)bitlen64(range)) << 23);  // 2^-bitlen(range)
     m.zc = 0.0f;
+    m.zsh = 0;
     m.rshift = 0;
     m.rmult = 0;
     if (level >= P.guard_level || !(*sd > 0.0)) {
@@ -145,8 +177,10 @@ __device__ void map_from_sums(const Params &P, unsigned long long n, unsigned lo
         atomicAdd(&P.ctl->n_guard, 1ull);
     } else {
         // scale = k/4 (Alg. 1); |z_min| = (mean - min)/sd cancels the mean.
+        const uint32_t e = bitlen64(range);
         m.kind = MAP_Z;
-        m.zc = (float)(((double)k / 4.0) / *sd);
+        m.zsh = e > 32 ? e - 32 : 0;
+        m.zc = (float)(((double)k / 4.0) / *sd * (double)(1ull << m.zsh));
     }
 }
 
@@ -167,25 +201,219 @@ __device__ void note_level(const Params &P, uint32_t level)
     atomicMax(&P.ctl->max_level, (unsigned long long)level);
 }
 
+// Bin table of the learned map: seg0[c] = the last piece s whose breakpoint
+// q[s] lies at or below the lower edge of bin c (float bits c << 19).
+__device__ void build_pwl_bins(MapSm &m)
+{
+    for (uint32_t c = threadIdx.x; c <= (uint32_t)PWL_BINS; c += BLOCK) {
+        const float edge = __uint_as_float(c << 19);
+        uint32_t lo = 0, hi = PWL_P - 1;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi + 1) >> 1;
+            if (m.q[mid] <= edge)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        m.seg0[c] = (uint8_t)lo;
+    }
+}
+
 // Loads a large segment's map into shared memory (all threads).
 __device__ void load_seg_map(const Params &P, uint32_t sid, SmemTile &s)
 {
     const Seg *S = &P.segs[sid];
-    uint32_t kind = __ldcg(&S->kind);
+    const uint32_t kind = __ldcg(&S->kind);
     if (threadIdx.x == 0) {
         s.map.mn = __ldcg(&S->mn);
         s.map.kind = kind;
         s.map.k = __ldcg(&S->k);
         s.map.K = s.map.k >= PWL_P ? s.map.k / PWL_P : 1;
         s.map.zc = __ldcg(&S->zc);
+        s.map.zsh = __ldcg(&S->zsh);
         s.map.escale = __ldcg(&S->escale);
         s.map.rshift = __ldcg(&S->rshift);
         s.map.rmult = __ldcg(&S->rmult);
     }
-    if (kind == MAP_PWL)
-        for (int j = threadIdx.x; j <= PWL_P; j += BLOCK)
-            s.map.q[j] = __ldcg(&P.pwl[(size_t)sid * (PWL_P + 1) + j]);
+    if (kind == MAP_PWL) {
+        const float *t = P.pwl + (size_t)sid * PWL_STRIDE;
+        for (int j = threadIdx.x; j <= PWL_P; j += BLOCK) s.map.q[j] = __ldcg(t + j);
+        for (int j = threadIdx.x; j < PWL_P; j += BLOCK) s.map.r[j] = __ldcg(t + PWL_P + 1 + j);
+        __syncthreads();
+        build_pwl_bins(s.map);
+    }
     __syncthreads();
+}
+
+// ------------------------------------------------------------ tile streaming
+// Per-thread copy (identical in every thread) of how often each of the two
+// tile mbarriers has completed, which gives the parity to wait for.
+struct Pipe {
+    uint32_t uses[2];
+};
+
+// Thread 0: bulk copies of elements [a, a+cnt) of keys (and vals) into
+// tile buffer w.  Copies start and end on 16-byte boundaries inside the
+// arrays ([0, n) rounded down), so the element a sits at index a & 1 of the
+// key buffer and a & 3 of the value buffer; up to 3 trailing elements past
+// the last full 16 bytes of the array are left to stream_fix_tail().
+template <bool VALS>
+__device__ void stream_issue(const Params &P, SmemTile &s, int w, const uint64_t *keys, const uint32_t *vals,
+                             unsigned long long a, uint32_t cnt)
+{
+    const unsigned long long a0 = a & ~1ull;
+    const unsigned long long a1 = min((a + cnt + 1) & ~1ull, P.n & ~1ull);
+    const uint32_t bk = a1 > a0 ? (uint32_t)(a1 - a0) * 8u : 0u;
+    uint32_t bv = 0;
+    unsigned long long b0 = 0;
+    if (VALS) {
+        b0 = a & ~3ull;
+        const unsigned long long b1 = min((a + cnt + 3) & ~3ull, P.n & ~3ull);
+        bv = b1 > b0 ? (uint32_t)(b1 - b0) * 4u : 0u;
+    }
+    mbar_expect_arrive(&s.bar[w], bk + bv);
+    if (bk) bulk_g2s(s.u.buf[w].key, keys + a0, bk, &s.bar[w]);
+    if (VALS && bv) bulk_g2s(s.u.buf[w].val, vals + b0, bv, &s.bar[w]);
+}
+
+template <bool VALS>
+__device__ void stream_fix_tail(const Params &P, unsigned long long *sk, uint32_t *sv, const uint64_t *keys,
+                                const uint32_t *vals, unsigned long long a, uint32_t cnt)
+{
+    const unsigned long long end = a + cnt;
+    const unsigned long long ka = max(a, P.n & ~1ull);
+    for (unsigned long long e = ka + threadIdx.x; e < end; e += BLOCK) sk[e - a] = __ldcg(keys + e);
+    if (VALS) {
+        const unsigned long long va = max(a, P.n & ~3ull);
+        for (unsigned long long e = va + threadIdx.x; e < end; e += BLOCK) sv[e - a] = __ldcg(vals + e);
+    }
+}
+
+// Streams elements [start, start+len) through the two tile buffers and calls
+// body(tile, cnt, keys_smem, vals_smem) for each tile, in order, with all
+// threads.  Returns false (error recorded) if a bulk copy did not complete.
+template <bool VALS, class Body>
+__device__ bool stream_tiles(const Params &P, SmemTile &s, Pipe &pp, const uint64_t *keys, const uint32_t *vals,
+                             bool bulk, unsigned long long start, unsigned long long len, Body body)
+{
+    const uint32_t nt = (uint32_t)((len + TILE - 1) / TILE);
+    if (nt == 0) return true;
+    if (bulk && threadIdx.x == 0)
+        stream_issue<VALS>(P, s, 0, keys, vals, start, (uint32_t)min(len, (unsigned long long)TILE));
+    for (uint32_t t = 0; t < nt; t++) {
+        const int w = t & 1;
+        const unsigned long long a = start + (unsigned long long)t * TILE;
+        const uint32_t cnt = (uint32_t)min((unsigned long long)TILE, len - (unsigned long long)t * TILE);
+        if (bulk && t + 1 < nt && threadIdx.x == 0) {
+            const unsigned long long an = a + TILE;
+            stream_issue<VALS>(P, s, w ^ 1, keys, vals, an,
+                               (uint32_t)min((unsigned long long)TILE, start + len - an));
+        }
+        unsigned long long *sk;
+        uint32_t *sv;
+        if (bulk) {
+            sk = s.u.buf[w].key + (a & 1ull);
+            sv = s.u.buf[w].val + (a & 3ull);
+            const bool ok = mbar_wait(&s.bar[w], pp.uses[w] & 1u, P.wait_ns);
+            pp.uses[w]++;
+            if (__syncthreads_or(!ok)) {  // CTA-uniform: every thread leaves together
+                set_error(P, ST_TIMEOUT);
+                return false;
+            }
+            stream_fix_tail<VALS>(P, sk, sv, keys, vals, a, cnt);
+        } else {
+            sk = s.u.buf[w].key;
+            sv = s.u.buf[w].val;
+            for (uint32_t i = threadIdx.x; i < cnt; i += BLOCK) {
+                sk[i] = __ldcg(keys + a + i);
+                if (VALS) sv[i] = __ldcg(vals + a + i);
+            }
+        }
+        __syncthreads();
+        body(t, cnt, sk, sv);
+        fence_proxy_async();  // this thread's smem accesses before the buffer's next bulk write
+        __syncthreads();
+    }
+    return true;
+}
+
+__device__ __forceinline__ uint32_t slot_index(int i)
+{
+    return (threadIdx.x >> 5) * WARP_SPAN + i * 32 + (threadIdx.x & 31);
+}
+__device__ __forceinline__ uint32_t leaf_slot(int i)
+{
+    return (threadIdx.x >> 5) * LEAF_SPAN + i * 32 + (threadIdx.x & 31);
+}
+
+// ------------------------------------------------------------ tile bodies
+// Exact sums of the tile's keys into a per-thread accumulator.
+__device__ __forceinline__ void body_stats(Acc &a, uint32_t cnt, const unsigned long long *sk)
+{
+#pragma unroll
+    for (int i = 0; i < IPT; i++) {
+        const uint32_t p = slot_index(i);
+        if (p < cnt) acc_key(a, sk[p]);
+    }
+}
+
+// Histogram of the tile's buckets into s.hist: one shared-memory atomic per
+// key, except when a whole warp slot shares one bucket (duplicate runs).
+__device__ __forceinline__ void body_hist(SmemTile &s, uint32_t cnt, const unsigned long long *sk)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int i = 0; i < IPT; i++) {
+        const uint32_t p = slot_index(i);
+        const uint32_t b = p < cnt ? map_key(s.map, sk[p]) : INVALID;
+        const uint32_t b0 = __shfl_sync(0xffffffffu, b, 0);
+        if (__all_sync(0xffffffffu, b == b0)) {
+            if (lane == 0 && b0 != INVALID) atomicAdd(&s.hist[b0], 32u);
+        } else if (b != INVALID) {
+            atomicAdd(&s.hist[b], 1u);
+        }
+    }
+}
+
+// Stable scatter of one tile: ranks by (bucket, position), stages the tile
+// ordered by bucket in shared memory, then writes each bucket's run at its
+// running cursor (coalesced within runs); cursors advance by the tile counts.
+__device__ __forceinline__ void body_scatter(const Params &P, SmemTile &s, uint32_t cnt, unsigned long long *sk,
+                                             uint32_t *sv, uint64_t *dstk, uint32_t *dstv, uint32_t seglen)
+{
+    const uint32_t k = s.map.k;
+    unsigned long long x[IPT];
+    uint32_t v[IPT], b[IPT], pos[IPT];
+#pragma unroll
+    for (int i = 0; i < IPT; i++) {
+        const uint32_t p = slot_index(i);
+        const bool ok = p < cnt;
+        x[i] = ok ? sk[p] : 0ull;
+        v[i] = ok ? sv[p] : 0u;
+        b[i] = ok ? map_key(s.map, x[i]) : INVALID;
+    }
+    tile_rank<IPT>(b, pos, k, s);
+    for (uint32_t q = threadIdx.x; q < k; q += BLOCK) s.gdelta[q] = s.cursor[q] - s.tstart[q];
+#pragma unroll
+    for (int i = 0; i < IPT; i++) {
+        if (b[i] != INVALID) {
+            sk[pos[i]] = x[i];
+            sv[pos[i]] = v[i];
+            s.bkt[pos[i]] = (uint16_t)b[i];
+        }
+    }
+    __syncthreads();
+    for (uint32_t p = threadIdx.x; p < cnt; p += BLOCK) {
+        const uint32_t rel = s.gdelta[s.bkt[p]] + p;
+        if (rel < seglen) {
+            __stcg(dstk + rel, sk[p]);
+            __stcg(dstv + rel, sv[p]);
+        } else {
+            set_error(P, ST_INTERNAL);
+        }
+    }
+    __syncthreads();
+    for (uint32_t q = threadIdx.x; q < k; q += BLOCK) s.cursor[q] += s.tcount[q];
 }
 
 // ------------------------------------------------------------ children
@@ -194,10 +422,10 @@ __device__ void load_seg_map(const Params &P, uint32_t sid, SmemTile &s)
 // buckets are grouped into leaves of at most LEAF_CAP elements (sorting a
 // group of whole, ordered buckets gives the same result as sorting each);
 // larger buckets become medium or large (sub)arrays of the next level.
-__device__ void classify_children(const Params &P, unsigned long long poff, uint32_t k,
+__device__ __noinline__ void classify_children(const Params &P, unsigned long long poff, uint32_t k,
                                   uint32_t child_buf, uint32_t child_level, SmemTile &s)
 {
-    ChildList &L = *reinterpret_cast<ChildList *>(s.key);
+    ChildList &L = s.u.children;
     if (threadIdx.x == 0) {
         uint32_t nl = 0, nm = 0, ng = 0, glen = 0, gstart = 0;
         for (uint32_t b = 0; b < k; b++) {
@@ -234,16 +462,19 @@ __device__ void classify_children(const Params &P, unsigned long long poff, uint
         // large children: descriptor + look-back rows, else demoted to medium
         uint32_t nok = 0;
         for (uint32_t g = 0; g < ng; g++) {
-            uint32_t len = L.lg_len[g];
-            uint32_t kk = choose_k(P, len);
-            uint32_t tiles = (len + TILE - 1) / TILE;
-            unsigned long long need = (unsigned long long)tiles * kk;
-            uint32_t sid = atomicAdd(&P.ctl->seg_alloc, 1u);
+            const uint32_t len = L.lg_len[g];
+            const uint32_t off_rel = L.lg_off[g];
+            const uint32_t kk = choose_k(P, len);
+            const uint32_t tiles = (len + TILE - 1) / TILE;
+            const uint32_t ct = choose_chunk_tiles(P, tiles);
+            const uint32_t chunks = (tiles + ct - 1) / ct;
+            const unsigned long long need = 2ull * chunks * kk;
+            const uint32_t sid = atomicAdd(&P.ctl->seg_alloc, 1u);
             unsigned long long sb = ~0ull;
             if (sid < P.segcap) sb = atomicAdd(&P.ctl->status_alloc, need);
             if (sid < P.segcap && sb + need <= P.statuscap) {
                 Seg *S = &P.segs[sid];
-                S->off = poff + L.lg_off[g];
+                S->off = poff + off_rel;
                 S->mn = ~0ull;
                 S->mx = 0ull;
                 S->s1[0] = S->s1[1] = 0ull;
@@ -252,16 +483,19 @@ __device__ void classify_children(const Params &P, unsigned long long poff, uint
                 S->len = len;
                 S->k = kk;
                 S->tiles = tiles;
+                S->chunk_tiles = ct;
+                S->chunks = chunks;
                 S->level = child_level;
                 S->buf = child_buf;
                 S->kind = MAP_Z;
                 S->train_slot = INVALID;
-                L.lg_sid[nok] = sid;
-                L.lg_len[nok] = len;  // compacted in place (nok <= g)
+                L.lg_sid[nok] = sid;  // compacted in place (nok <= g)
+                L.lg_len[nok] = len;
+                L.lg_off[nok] = chunks;
                 nok++;
             } else {
                 if (sid < P.segcap) P.segs[sid].len = 0;
-                L.med_off[nm] = L.lg_off[g];
+                L.med_off[nm] = off_rel;
                 L.med_len[nm++] = len;
             }
         }
@@ -279,7 +513,7 @@ __device__ void classify_children(const Params &P, unsigned long long poff, uint
     const uint32_t nl = s.n_leaf, nm = s.n_med, nok = s.n_large_ok, base = s.item_base;
     for (uint32_t i = threadIdx.x; i < nl + nm; i += BLOCK) {
         Item it;
-        bool leaf = i < nl;
+        const bool leaf = i < nl;
         it.off = poff + (leaf ? L.leaf_off[i] : L.med_off[i - nl]);
         it.len = leaf ? L.leaf_len[i] : L.med_len[i - nl];
         it.buf = (uint16_t)child_buf;
@@ -287,54 +521,61 @@ __device__ void classify_children(const Params &P, unsigned long long poff, uint
         P.items[base + i] = it;
     }
     for (uint32_t g = 0; g < nok; g++) {
-        uint32_t sid = L.lg_sid[g];
-        uint32_t kk = choose_k(P, L.lg_len[g]);
+        const uint32_t sid = L.lg_sid[g];
+        const uint32_t kk = choose_k(P, L.lg_len[g]);
         for (uint32_t q = threadIdx.x; q < kk; q += BLOCK) P.counts[(size_t)sid * NB_MAX + q] = 0;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        uint32_t cnt = (nl > 0) + (nm > 0) + nok;
-        uint32_t e = q_reserve(P, cnt);
+        const uint32_t cnt = (nl > 0) + (nm > 0) + nok;
+        const uint32_t e = q_reserve(P, cnt);
         if (e != INVALID && cnt) {
             uint32_t j = e;
             if (nl) q_write(P, j++, T_FINISH, base, nl);
             if (nm) q_write(P, j++, T_MPART, base + nl, nm);
-            for (uint32_t g = 0; g < nok; g++) {
-                uint32_t sid = L.lg_sid[g];
-                q_write(P, j++, T_LSTATS, sid, (L.lg_len[g] + TILE - 1) / TILE);
-            }
+            for (uint32_t g = 0; g < nok; g++) q_write(P, j++, T_LSTATS, L.lg_sid[g], L.lg_off[g]);
             q_release_all(P, e, cnt);
         }
     }
     __syncthreads();
 }
 
-// ------------------------------------------------------------ tile loads
-// Element (warp, slot i, lane) of a tile at `base`: base + warp*WARP_SPAN + i*32 + lane.
-__device__ __forceinline__ uint32_t slot_index(int i)
+// ------------------------------------------------------------ chunk geometry
+struct Chunk {
+    unsigned long long off, start, len;  // segment offset; chunk start; chunk length
+    unsigned long long sbase;
+    uint32_t seglen, buf, k, chunks;
+};
+
+__device__ __forceinline__ Chunk chunk_of(const Params &P, uint32_t sid, uint32_t c)
 {
-    return (threadIdx.x >> 5) * WARP_SPAN + i * 32 + (threadIdx.x & 31);
+    const Seg *S = &P.segs[sid];
+    Chunk ch;
+    ch.off = __ldcg(&S->off);
+    ch.seglen = __ldcg(&S->len);
+    ch.buf = __ldcg(&S->buf);
+    ch.k = __ldcg(&S->k);
+    ch.chunks = __ldcg(&S->chunks);
+    ch.sbase = __ldcg(&S->status_base);
+    const unsigned long long span = (unsigned long long)__ldcg(&S->chunk_tiles) * TILE;
+    const unsigned long long rel = (unsigned long long)c * span;
+    ch.start = ch.off + rel;
+    ch.len = min(span, (unsigned long long)ch.seglen - rel);
+    return ch;
 }
 
 // ------------------------------------------------------------ LSTATS
-__device__ void task_lstats(const Params &P, uint32_t sid, uint32_t tile, SmemTile &s)
+__device__ __noinline__ void task_lstats(const Params &P, uint32_t sid, uint32_t c, SmemTile &s, Pipe &pp)
 {
-    const Seg *S = &P.segs[sid];
-    const unsigned long long off = __ldcg(&S->off);
-    const uint32_t len = __ldcg(&S->len), buf = __ldcg(&S->buf);
-    const uint64_t *src = keys_of(P, buf) + off + (size_t)tile * TILE;
-    const uint32_t cnt = min((uint32_t)TILE, len - tile * TILE);
-    unsigned long long x[IPT];
-#pragma unroll
-    for (int i = 0; i < IPT; i++) {
-        uint32_t p = slot_index(i);
-        x[i] = p < cnt ? __ldcg(src + p) : 0ull;
-    }
+    const Chunk ch = chunk_of(P, sid, c);
+    // this chunk's look-back row must read zero before the histogram phase
+    uint32_t *row = P.status + ch.sbase + (size_t)c * ch.k;
+    for (uint32_t q = threadIdx.x; q < ch.k; q += BLOCK) __stcg(row + q, 0u);
     Acc a;
     acc_init(a);
-#pragma unroll
-    for (int i = 0; i < IPT; i++)
-        if (slot_index(i) < cnt) acc_key(a, x[i]);
+    const uint64_t *src = keys_of(P, ch.buf);
+    stream_tiles<false>(P, s, pp, src, nullptr, bulk_ok(P, ch.buf), ch.start, ch.len,
+                        [&](uint32_t, uint32_t cnt, unsigned long long *sk, uint32_t *) { body_stats(a, cnt, sk); });
     acc_block_reduce(a, s.acc);
     if (threadIdx.x == 0) {
         Seg *W = &P.segs[sid];
@@ -344,22 +585,22 @@ __device__ void task_lstats(const Params &P, uint32_t sid, uint32_t tile, SmemTi
         unsigned long long v2[3] = {(unsigned long long)a.s2lo, (unsigned long long)(a.s2lo >> 64), a.s2hi};
         atomic_add_wide(W->s1, v1, 2);
         atomic_add_wide(W->s2, v2, 3);
-        atomicAdd(&P.ctl->bytes, 8ull * cnt);
+        atomicAdd(&P.ctl->bytes, 8ull * ch.len);
     }
 }
 
-__device__ void lstats_done(const Params &P, uint32_t sid, SmemTile &s)
+__device__ __noinline__ void lstats_done(const Params &P, uint32_t sid, SmemTile &s)
 {
     if (threadIdx.x == 0) {
         Seg *S = &P.segs[sid];
         const unsigned long long mn = __ldcg(&S->mn), mx = __ldcg(&S->mx);
-        const uint32_t len = __ldcg(&S->len), level = __ldcg(&S->level), tiles = __ldcg(&S->tiles);
-        const uint32_t sbuf = __ldcg(&S->buf), sk = __ldcg(&S->k);
+        const uint32_t len = __ldcg(&S->len), level = __ldcg(&S->level);
+        const uint32_t sbuf = __ldcg(&S->buf), sk = __ldcg(&S->k), chunks = __ldcg(&S->chunks);
         if (mn == mx) {  // a set of identical keys is sorted (Alg. 1 early exit)
             if (sbuf) {
                 uint32_t e = q_reserve(P, 1);
                 if (e != INVALID) {
-                    q_write(P, e, T_COPY, sid, tiles);
+                    q_write(P, e, T_COPY, sid, (len + LEAF_CAP - 1) / LEAF_CAP);
                     q_release_all(P, e, 1);
                 }
                 atomicAdd(&P.ctl->n_copies, 1ull);
@@ -374,11 +615,12 @@ __device__ void lstats_done(const Params &P, uint32_t sid, SmemTile &s)
             S->sd = sd;
             S->kind = m.kind;
             S->zc = m.zc;
+            S->zsh = m.zsh;
             S->escale = m.escale;
             S->rshift = m.rshift;
             S->rmult = m.rmult;
             if (level == 0 && sid == 0) record_top(P, m, mn, mx, mean_d, sd);
-            uint32_t next = T_LHIST, nt = tiles;
+            uint32_t next = T_LHIST, nt = chunks;
             if (m.kind == MAP_Z && P.mapper == 1 && len >= P.learn_min && P.sample <= len &&
                 sk >= (uint32_t)PWL_P) {
                 uint32_t slot = atomicAdd(&P.ctl->train_alloc, 1u);
@@ -416,7 +658,7 @@ __device__ void cta_lsd_pass(const uint32_t *src, uint32_t *dst, uint32_t m, uin
             v[i] = p < cnt ? __ldcg(src + t0 + p) : 0u;
             b[i] = p < cnt ? (v[i] >> shift) & 255u : INVALID;
         }
-        tile_rank(b, pos, 256, s);
+        tile_rank<IPT>(b, pos, 256, s);
 #pragma unroll
         for (int i = 0; i < IPT; i++)
             if (b[i] != INVALID) __stcg(dst + s.cursor[b[i]] + pos[i] - s.tstart[b[i]], v[i]);
@@ -426,42 +668,24 @@ __device__ void cta_lsd_pass(const uint32_t *src, uint32_t *dst, uint32_t m, uin
     }
 }
 
-// Bucket of a normalised key u under the learned map in s.map (the part of
-// map_key after the normalisation).
-__device__ __forceinline__ uint32_t pwl_bucket_u(const MapSm &m, float u)
-{
-    int s = 0;
-#pragma unroll
-    for (int st = PWL_P / 2; st; st >>= 1)
-        if (m.q[s + st] <= u) s += st;
-    float lo = m.q[s], hi = m.q[s + 1];
-    float frac = 0.0f;
-    if (hi > lo) frac = __fdiv_rn(__fsub_rn(u, lo), __fsub_rn(hi, lo));
-    frac = fminf(fmaxf(frac, 0.0f), 0x1.fffffep-1f);
-    uint32_t w = __float2uint_rz(__fmul_rn(frac, (float)m.K));
-    w = w < m.K ? w : m.K - 1;
-    return (uint32_t)s * m.K + w;
-}
-
 // Learned-map training: sample, exact sort of the normalised sample,
-// breakpoints at the 1/256 quantiles, then the load test that keeps Eq. 1
-// as the fallback.
-__device__ void task_ltrain(const Params &P, uint32_t sid, SmemTile &s)
+// breakpoints at the 1/256 quantiles and their reciprocal widths, then the
+// load test that keeps Eq. 1 as the fallback.
+__device__ __noinline__ void task_ltrain(const Params &P, uint32_t sid, SmemTile &s)
 {
     Seg *S = &P.segs[sid];
     const unsigned long long off = __ldcg(&S->off), mn = __ldcg(&S->mn), mx = __ldcg(&S->mx);
     const uint32_t len = __ldcg(&S->len), buf = __ldcg(&S->buf), k = __ldcg(&S->k);
-    const uint32_t slot = __ldcg(&S->train_slot), tiles = __ldcg(&S->tiles);
+    const uint32_t slot = __ldcg(&S->train_slot), chunks = __ldcg(&S->chunks);
     const float escale = __ldcg(&S->escale), zc = __ldcg(&S->zc);
+    const uint32_t zsh = __ldcg(&S->zsh);
     const uint32_t m = P.sample;
     uint32_t *A = P.trainbuf + (size_t)slot * 2 * SAMPLE_MAX;
     uint32_t *B = A + SAMPLE_MAX;
     const uint64_t *src = keys_of(P, buf) + off;
     for (uint32_t i = threadIdx.x; i < m; i += BLOCK) {
-        unsigned long long pos = sample_pos(P.seed, len, m, i);
-        unsigned long long key = __ldcg(src + pos);
-        float u = __fmul_rn(__ull2float_rn(key - mn), escale);
-        __stcg(A + i, __float_as_uint(u));
+        const unsigned long long key = __ldcg(src + sample_pos(P.seed, len, m, i));
+        __stcg(A + i, __float_as_uint(__fmul_rn(u64_to_f32_rn(key - mn), escale)));
     }
     __syncthreads();
     // non-negative floats order as their bit patterns
@@ -476,31 +700,38 @@ __device__ void task_ltrain(const Params &P, uint32_t sid, SmemTile &s)
         s.map.K = k / PWL_P;
         s.map.escale = escale;
         s.map.zc = zc;
+        s.map.zsh = zsh;
     }
+    float *t = P.pwl + (size_t)sid * PWL_STRIDE;
     for (int j = threadIdx.x; j <= PWL_P; j += BLOCK) {
         float q;
         if (j == 0)
             q = 0.0f;
         else if (j == PWL_P)
-            q = __fmul_rn(__ull2float_rn(mx - mn), escale);
+            q = __fmul_rn(u64_to_f32_rn(mx - mn), escale);
         else
             q = __uint_as_float(__ldcg(A + (size_t)j * m / PWL_P));
         s.map.q[j] = q;
-        P.pwl[(size_t)sid * (PWL_P + 1) + j] = q;
+        t[j] = q;
     }
     for (uint32_t q = threadIdx.x; q < k; q += BLOCK) {
         s.hist[q] = 0;
         s.cursor[q] = 0;
     }
     __syncthreads();
+    for (int j = threadIdx.x; j < PWL_P; j += BLOCK) {
+        const float lo = s.map.q[j], hi = s.map.q[j + 1];
+        const float r = hi > lo ? __fdiv_rn(1.0f, __fsub_rn(hi, lo)) : 0.0f;
+        s.map.r[j] = r;
+        t[PWL_P + 1 + j] = r;
+    }
+    build_pwl_bins(s.map);
+    __syncthreads();
     // load test on the sample: largest learned bucket vs largest Eq. 1 bucket
-    // 2^E from escale = 2^-E (exponent field 127 - E -> 127 + E)
-    const float two_e = __uint_as_float((uint32_t)(254 - ((__float_as_uint(escale) >> 23) & 0xff)) << 23);
     for (uint32_t i = threadIdx.x; i < m; i += BLOCK) {
-        float u = __uint_as_float(__ldcg(A + i));
-        atomicAdd(&s.hist[pwl_bucket_u(s.map, u)], 1u);
-        float fd = __fmul_rn(u, two_e);  // = fl32(key - min), exactly
-        uint32_t bz = __float2uint_rz(__fmul_rn(fd, zc));
+        const unsigned long long d = __ldcg(src + sample_pos(P.seed, len, m, i)) - mn;
+        atomicAdd(&s.hist[pwl_bucket_u(s.map, __fmul_rn(u64_to_f32_rn(d), escale))], 1u);
+        const uint32_t bz = __float2uint_rz(__fmul_rn(__uint2float_rz((uint32_t)(d >> zsh)), zc));
         atomicAdd(&s.cursor[bz < k ? bz : k - 1], 1u);
     }
     __syncthreads();
@@ -527,126 +758,67 @@ __device__ void task_ltrain(const Params &P, uint32_t sid, SmemTile &s)
         if (__ldcg(&S->level) == 0 && sid == 0) P.ctl->top_map = ok ? MAP_PWL : MAP_Z;
         uint32_t e = q_reserve(P, 1);
         if (e != INVALID) {
-            q_write(P, e, T_LHIST, sid, tiles);
+            q_write(P, e, T_LHIST, sid, chunks);
             q_release_all(P, e, 1);
         }
     }
 }
 
 // ------------------------------------------------------------ LHIST
-__device__ void task_lhist(const Params &P, uint32_t sid, uint32_t tile, SmemTile &s)
+// Histogram of one chunk, then its bucket offsets over the preceding chunks
+// by a decoupled look-back: the chunk publishes, per bucket, its count
+// (FLAG_A) and then its inclusive prefix over chunks 0..c (FLAG_P), walking
+// back over predecessors until one has FLAG_P.  Chunks are handed out in
+// increasing order, so a predecessor is always running or done.
+__device__ __noinline__ void task_lhist(const Params &P, uint32_t sid, uint32_t c, SmemTile &s, Pipe &pp)
 {
     load_seg_map(P, sid, s);
-    const Seg *S = &P.segs[sid];
-    const unsigned long long off = __ldcg(&S->off), sbase = __ldcg(&S->status_base);
-    const uint32_t len = __ldcg(&S->len), buf = __ldcg(&S->buf), k = s.map.k;
-    const uint32_t cnt = min((uint32_t)TILE, len - tile * TILE);
-    const uint64_t *src = keys_of(P, buf) + off + (size_t)tile * TILE;
-    uint32_t *row = P.status + sbase + (size_t)tile * k;
+    const Chunk ch = chunk_of(P, sid, c);
+    const uint32_t k = ch.k;
+    for (uint32_t q = threadIdx.x; q < k; q += BLOCK) s.hist[q] = 0;
+    __syncthreads();
+    const uint64_t *src = keys_of(P, ch.buf);
+    stream_tiles<false>(P, s, pp, src, nullptr, bulk_ok(P, ch.buf), ch.start, ch.len,
+                        [&](uint32_t, uint32_t cnt, unsigned long long *sk, uint32_t *) { body_hist(s, cnt, sk); });
+    uint32_t *status = P.status + ch.sbase;
+    uint32_t *row = status + (size_t)c * k;
+    uint32_t *offs = status + (size_t)ch.chunks * k + (size_t)c * k;
     for (uint32_t q = threadIdx.x; q < k; q += BLOCK) {
-        s.hist[q] = 0;
-        __stcg(row + q, 0u);
+        const uint32_t h = s.hist[q];
+        st_relaxed(row + q, (c == 0 ? FLAG_P : FLAG_A) | h);
+        if (h) atomicAdd(&P.counts[(size_t)sid * NB_MAX + q], h);
     }
-    unsigned long long x[IPT];
-#pragma unroll
-    for (int i = 0; i < IPT; i++) {
-        uint32_t p = slot_index(i);
-        x[i] = p < cnt ? __ldcg(src + p) : 0ull;
-    }
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int i = 0; i < IPT; i++) {
-        uint32_t b = slot_index(i) < cnt ? map_key(s.map, x[i]) : INVALID;
-        uint32_t peers = __match_any_sync(0xffffffffu, b);
-        if (b != INVALID && lane == __ffs(peers) - 1) atomicAdd(&s.hist[b], (uint32_t)__popc(peers));
-    }
-    __syncthreads();
-    for (uint32_t q = threadIdx.x; q < k; q += BLOCK)
-        if (s.hist[q]) atomicAdd(&P.counts[(size_t)sid * NB_MAX + q], s.hist[q]);
-    if (threadIdx.x == 0) atomicAdd(&P.ctl->bytes, 8ull * cnt);
-}
-
-__device__ void lhist_done(const Params &P, uint32_t sid, SmemTile &s)
-{
-    const Seg *S = &P.segs[sid];
-    const uint32_t k = __ldcg(&S->k), tiles = __ldcg(&S->tiles);
-    for (uint32_t q = threadIdx.x; q < k; q += BLOCK) s.hist[q] = __ldcg(&P.counts[(size_t)sid * NB_MAX + q]);
-    __syncthreads();
-    block_exclusive_scan(s.hist, s.bs, k, s.wsum);
-    for (uint32_t q = threadIdx.x; q < k; q += BLOCK) P.bstart[(size_t)sid * NB_MAX + q] = s.bs[q];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t e = q_reserve(P, 1);
-        if (e != INVALID) {
-            q_write(P, e, T_LSCATTER, sid, tiles);
-            q_release_all(P, e, 1);
-        }
-    }
-}
-
-// ------------------------------------------------------------ LSCATTER
-// Decoupled look-back: tile t publishes, per bucket, its count (FLAG_A) and
-// then its inclusive prefix over tiles 0..t (FLAG_P); it finds its exclusive
-// prefix by walking back over predecessors until one has FLAG_P.  Tiles are
-// handed out in increasing order, so a predecessor is always running or done.
-__device__ void task_lscatter(const Params &P, uint32_t sid, uint32_t tile, SmemTile &s)
-{
-    load_seg_map(P, sid, s);
-    const Seg *S = &P.segs[sid];
-    const unsigned long long off = __ldcg(&S->off), sbase = __ldcg(&S->status_base);
-    const uint32_t len = __ldcg(&S->len), buf = __ldcg(&S->buf), k = s.map.k;
-    const uint32_t cnt = min((uint32_t)TILE, len - tile * TILE);
-    const uint64_t *srck = keys_of(P, buf) + off + (size_t)tile * TILE;
-    const uint32_t *srcv = vals_of(P, buf) + off + (size_t)tile * TILE;
-    uint64_t *dstk = keys_of(P, buf ^ 1u) + off;
-    uint32_t *dstv = vals_of(P, buf ^ 1u) + off;
-    unsigned long long x[IPT];
-    uint32_t v[IPT], b[IPT], pos[IPT];
-#pragma unroll
-    for (int i = 0; i < IPT; i++) {
-        uint32_t p = slot_index(i);
-        x[i] = p < cnt ? __ldcg(srck + p) : 0ull;
-        v[i] = p < cnt ? __ldcg(srcv + p) : 0u;
-    }
-#pragma unroll
-    for (int i = 0; i < IPT; i++) b[i] = slot_index(i) < cnt ? map_key(s.map, x[i]) : INVALID;
-    tile_rank(b, pos, k, s);
-    uint32_t *status = P.status + sbase;
-    uint32_t *row = status + (size_t)tile * k;
-    for (uint32_t q = threadIdx.x; q < k; q += BLOCK) st_relaxed(row + q, (tile == 0 ? FLAG_P : FLAG_A) | s.tcount[q]);
-    // look-back, up to NB_MAX / BLOCK buckets per thread, polled together
     constexpr int PER = NB_MAX / BLOCK;
     uint32_t excl[PER], j[PER];
     bool done[PER];
 #pragma unroll
     for (int r = 0; r < PER; r++) {
         excl[r] = 0;
-        j[r] = tile;
-        done[r] = (threadIdx.x + r * BLOCK >= k) || tile == 0;
+        j[r] = c;
+        done[r] = (threadIdx.x + r * BLOCK >= k) || c == 0;
     }
     unsigned long long t0 = 0;
     uint32_t spins = 0;
-    bool timed_out = false;
+    bool failed = false;
     for (;;) {
         bool all = true, moved = false;
 #pragma unroll
         for (int r = 0; r < PER; r++) {
             if (done[r]) continue;
             const uint32_t q = threadIdx.x + r * BLOCK;
-            uint32_t w = ld_relaxed(status + (size_t)(j[r] - 1) * k + q);
-            uint32_t f = w & ~VAL_MASK;
+            const uint32_t w = ld_relaxed(status + (size_t)(j[r] - 1) * k + q);
+            const uint32_t f = w & ~VAL_MASK;
             if (f == FLAG_P) {
                 excl[r] += w & VAL_MASK;
                 done[r] = true;
-                st_relaxed(row + q, FLAG_P | (excl[r] + s.tcount[q]));
+                st_relaxed(row + q, FLAG_P | (excl[r] + s.hist[q]));
                 moved = true;
             } else if (f == FLAG_A && j[r] > 1) {
                 excl[r] += w & VAL_MASK;
                 j[r]--;
                 moved = true;
             } else if (f == FLAG_A || f == (FLAG_A | FLAG_P)) {
-                set_error(P, ST_INTERNAL);  // tile 0 always publishes FLAG_P
+                set_error(P, ST_INTERNAL);  // chunk 0 always publishes FLAG_P
                 done[r] = true;
             } else {
                 all = false;
@@ -655,55 +827,65 @@ __device__ void task_lscatter(const Params &P, uint32_t sid, uint32_t tile, Smem
 #pragma unroll
         for (int r = 0; r < PER; r++) all = all && done[r];
         if (all) break;
-        if (!moved) {
-            if ((++spins & 31u) == 0) {
-                unsigned long long now = globaltimer();
-                if (t0 == 0)
-                    t0 = now;
-                else if (now - t0 > P.wait_ns) {
-                    timed_out = true;
-                    break;
-                }
-                if (has_error(P)) {
-                    timed_out = true;
-                    break;
-                }
+        if (!moved && (++spins & 31u) == 0) {
+            const unsigned long long now = globaltimer();
+            if (t0 == 0)
+                t0 = now;
+            else if (now - t0 > P.wait_ns || has_error(P)) {
+                failed = true;
+                break;
             }
         }
     }
-    if (timed_out) set_error(P, ST_TIMEOUT);
+    if (failed) set_error(P, ST_TIMEOUT);
 #pragma unroll
     for (int r = 0; r < PER; r++) {
         const uint32_t q = threadIdx.x + r * BLOCK;
-        if (q < k) s.gdelta[q] = __ldcg(&P.bstart[(size_t)sid * NB_MAX + q]) + excl[r] - s.tstart[q];
+        if (q < k) __stcg(offs + q, excl[r]);
     }
-    if (threadIdx.x == 0) s.flag = timed_out ? 1u : 0u;
-    __syncthreads();
-    const bool skip = s.flag != 0 || has_error(P);
-#pragma unroll
-    for (int i = 0; i < IPT; i++) {
-        if (b[i] != INVALID) {
-            s.key[pos[i]] = x[i];
-            s.val[pos[i]] = v[i];
-            s.bkt[pos[i]] = (uint16_t)b[i];
-        }
-    }
-    __syncthreads();
-    if (!skip) {
-        for (uint32_t p = threadIdx.x; p < cnt; p += BLOCK) {
-            uint32_t rel = s.gdelta[s.bkt[p]] + p;
-            if (rel < len) {
-                __stcg(dstk + rel, s.key[p]);
-                __stcg(dstv + rel, s.val[p]);
-            } else {
-                set_error(P, ST_INTERNAL);
-            }
-        }
-    }
-    if (threadIdx.x == 0) atomicAdd(&P.ctl->bytes, 24ull * cnt);
+    if (threadIdx.x == 0) atomicAdd(&P.ctl->bytes, 8ull * ch.len);
 }
 
-__device__ void lscatter_done(const Params &P, uint32_t sid, SmemTile &s)
+__device__ __noinline__ void lhist_done(const Params &P, uint32_t sid, SmemTile &s)
+{
+    const Seg *S = &P.segs[sid];
+    const uint32_t k = __ldcg(&S->k), chunks = __ldcg(&S->chunks);
+    for (uint32_t q = threadIdx.x; q < k; q += BLOCK) s.hist[q] = __ldcg(&P.counts[(size_t)sid * NB_MAX + q]);
+    __syncthreads();
+    block_exclusive_scan(s.hist, s.bs, k, s.wsum);
+    for (uint32_t q = threadIdx.x; q < k; q += BLOCK) P.bstart[(size_t)sid * NB_MAX + q] = s.bs[q];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t e = q_reserve(P, 1);
+        if (e != INVALID) {
+            q_write(P, e, T_LSCATTER, sid, chunks);
+            q_release_all(P, e, 1);
+        }
+    }
+}
+
+// ------------------------------------------------------------ LSCATTER
+// Stable scatter of one chunk: its cursors start at the bucket start plus the
+// chunk's look-back offset, and its tiles are streamed in input order.
+__device__ __noinline__ void task_lscatter(const Params &P, uint32_t sid, uint32_t c, SmemTile &s, Pipe &pp)
+{
+    load_seg_map(P, sid, s);
+    const Chunk ch = chunk_of(P, sid, c);
+    const uint32_t k = ch.k;
+    const uint32_t *offs = P.status + ch.sbase + (size_t)ch.chunks * k + (size_t)c * k;
+    for (uint32_t q = threadIdx.x; q < k; q += BLOCK)
+        s.cursor[q] = __ldcg(&P.bstart[(size_t)sid * NB_MAX + q]) + __ldcg(offs + q);
+    __syncthreads();
+    uint64_t *dstk = keys_of(P, ch.buf ^ 1u) + ch.off;
+    uint32_t *dstv = vals_of(P, ch.buf ^ 1u) + ch.off;
+    stream_tiles<true>(P, s, pp, keys_of(P, ch.buf), vals_of(P, ch.buf), bulk_ok(P, ch.buf), ch.start, ch.len,
+                       [&](uint32_t, uint32_t cnt, unsigned long long *sk, uint32_t *sv) {
+                           body_scatter(P, s, cnt, sk, sv, dstk, dstv, ch.seglen);
+                       });
+    if (threadIdx.x == 0) atomicAdd(&P.ctl->bytes, 24ull * ch.len);
+}
+
+__device__ __noinline__ void lscatter_done(const Params &P, uint32_t sid, SmemTile &s)
 {
     const Seg *S = &P.segs[sid];
     const uint32_t k = __ldcg(&S->k), buf = __ldcg(&S->buf), level = __ldcg(&S->level);
@@ -721,29 +903,19 @@ __device__ void lscatter_done(const Params &P, uint32_t sid, SmemTile &s)
 }
 
 // ------------------------------------------------------------ MPART
-// A medium (sub)array: every step of Alg. 1 by one CTA, tile by tile in input
-// order, so the scatter is stable with plain running bucket cursors.
-__device__ void task_mpart(const Params &P, const Item it, SmemTile &s)
+// A medium (sub)array: every step of Alg. 1 by one CTA, three streamed
+// passes in input order, so the scatter is stable with running cursors.
+__device__ __noinline__ void task_mpart(const Params &P, const Item it, SmemTile &s, Pipe &pp)
 {
     const unsigned long long off = it.off;
     const uint32_t len = it.len, buf = it.buf, level = it.level;
-    const uint64_t *srck = keys_of(P, buf) + off;
-    const uint32_t *srcv = vals_of(P, buf) + off;
-    // statistics (exact sums)
+    const uint64_t *srck = keys_of(P, buf);
+    const uint32_t *srcv = vals_of(P, buf);
+    const bool bulk = bulk_ok(P, buf);
     Acc a;
     acc_init(a);
-    for (uint32_t t0 = 0; t0 < len; t0 += TILE) {
-        const uint32_t cnt = min((uint32_t)TILE, len - t0);
-        unsigned long long x[IPT];
-#pragma unroll
-        for (int i = 0; i < IPT; i++) {
-            uint32_t p = slot_index(i);
-            x[i] = p < cnt ? __ldcg(srck + t0 + p) : 0ull;
-        }
-#pragma unroll
-        for (int i = 0; i < IPT; i++)
-            if (slot_index(i) < cnt) acc_key(a, x[i]);
-    }
+    stream_tiles<false>(P, s, pp, srck, nullptr, bulk, off, len,
+                        [&](uint32_t, uint32_t cnt, unsigned long long *sk, uint32_t *) { body_stats(a, cnt, sk); });
     acc_block_reduce(a, s.acc);
     if (threadIdx.x == 0) {
         if (a.mn == a.mx) {
@@ -761,12 +933,12 @@ __device__ void task_mpart(const Params &P, const Item it, SmemTile &s)
     if (s.flag) {  // identical keys: already sorted
         if (buf) {
             for (uint32_t p = threadIdx.x; p < len; p += BLOCK) {
-                __stcg(P.ukeys + off + p, __ldcg(srck + p));
-                __stcg(P.uvals + off + p, __ldcg(srcv + p));
+                __stcg(P.ukeys + off + p, __ldcg(srck + off + p));
+                __stcg(P.uvals + off + p, __ldcg(srcv + off + p));
             }
             if (threadIdx.x == 0) {
                 atomicAdd(&P.ctl->n_copies, 1ull);
-                atomicAdd(&P.ctl->bytes, 8ull * len + 24ull * len);
+                atomicAdd(&P.ctl->bytes, 32ull * len);
             }
         } else if (threadIdx.x == 0) {
             atomicAdd(&P.ctl->bytes, 8ull * len);
@@ -774,68 +946,19 @@ __device__ void task_mpart(const Params &P, const Item it, SmemTile &s)
         return;
     }
     const uint32_t k = s.map.k;
-    const int lane = threadIdx.x & 31;
-    // histogram
     for (uint32_t q = threadIdx.x; q < k; q += BLOCK) s.hist[q] = 0;
     __syncthreads();
-    for (uint32_t t0 = 0; t0 < len; t0 += TILE) {
-        const uint32_t cnt = min((uint32_t)TILE, len - t0);
-        unsigned long long x[IPT];
-#pragma unroll
-        for (int i = 0; i < IPT; i++) {
-            uint32_t p = slot_index(i);
-            x[i] = p < cnt ? __ldcg(srck + t0 + p) : 0ull;
-        }
-#pragma unroll
-        for (int i = 0; i < IPT; i++) {
-            uint32_t b = slot_index(i) < cnt ? map_key(s.map, x[i]) : INVALID;
-            uint32_t peers = __match_any_sync(0xffffffffu, b);
-            if (b != INVALID && lane == __ffs(peers) - 1) atomicAdd(&s.hist[b], (uint32_t)__popc(peers));
-        }
-    }
-    __syncthreads();
+    stream_tiles<false>(P, s, pp, srck, nullptr, bulk, off, len,
+                        [&](uint32_t, uint32_t cnt, unsigned long long *sk, uint32_t *) { body_hist(s, cnt, sk); });
     block_exclusive_scan(s.hist, s.bs, k, s.wsum);
     for (uint32_t q = threadIdx.x; q < k; q += BLOCK) s.cursor[q] = s.bs[q];
     __syncthreads();
-    // stable scatter, tile by tile
     uint64_t *dstk = keys_of(P, buf ^ 1u) + off;
     uint32_t *dstv = vals_of(P, buf ^ 1u) + off;
-    for (uint32_t t0 = 0; t0 < len; t0 += TILE) {
-        const uint32_t cnt = min((uint32_t)TILE, len - t0);
-        unsigned long long x[IPT];
-        uint32_t v[IPT], b[IPT], pos[IPT];
-#pragma unroll
-        for (int i = 0; i < IPT; i++) {
-            uint32_t p = slot_index(i);
-            x[i] = p < cnt ? __ldcg(srck + t0 + p) : 0ull;
-            v[i] = p < cnt ? __ldcg(srcv + t0 + p) : 0u;
-        }
-#pragma unroll
-        for (int i = 0; i < IPT; i++) b[i] = slot_index(i) < cnt ? map_key(s.map, x[i]) : INVALID;
-        tile_rank(b, pos, k, s);
-        for (uint32_t q = threadIdx.x; q < k; q += BLOCK) s.gdelta[q] = s.cursor[q] - s.tstart[q];
-#pragma unroll
-        for (int i = 0; i < IPT; i++) {
-            if (b[i] != INVALID) {
-                s.key[pos[i]] = x[i];
-                s.val[pos[i]] = v[i];
-                s.bkt[pos[i]] = (uint16_t)b[i];
-            }
-        }
-        __syncthreads();
-        for (uint32_t p = threadIdx.x; p < cnt; p += BLOCK) {
-            uint32_t rel = s.gdelta[s.bkt[p]] + p;
-            if (rel < len) {
-                __stcg(dstk + rel, s.key[p]);
-                __stcg(dstv + rel, s.val[p]);
-            } else {
-                set_error(P, ST_INTERNAL);
-            }
-        }
-        __syncthreads();
-        for (uint32_t q = threadIdx.x; q < k; q += BLOCK) s.cursor[q] += s.tcount[q];
-        __syncthreads();
-    }
+    stream_tiles<true>(P, s, pp, srck, srcv, bulk, off, len,
+                       [&](uint32_t, uint32_t cnt, unsigned long long *sk, uint32_t *sv) {
+                           body_scatter(P, s, cnt, sk, sv, dstk, dstv, len);
+                       });
     if (threadIdx.x == 0) {
         atomicAdd(&P.ctl->n_small, 1ull);
         atomicAdd(&P.ctl->bytes, 40ull * len);
@@ -865,14 +988,14 @@ __device__ bool insertion_sort_budget(unsigned long long *k, uint32_t *v, uint32
     return true;
 }
 
-// Bitonic sort of s.key/s.val[0..len) by (key, current position): stable.
-__device__ void bitonic_fallback(SmemTile &s, uint32_t len)
+// Bitonic sort of key/val[0..len) by (key, current position): stable.
+__device__ void bitonic_fallback(SmemTile &s, unsigned long long *key, uint32_t *val, uint32_t len)
 {
     const uint32_t L = pow2ceil32(len);
     for (uint32_t p = threadIdx.x; p < L; p += BLOCK) {
         if (p >= len) {
-            s.key[p] = ~0ull;
-            s.val[p] = 0u;
+            key[p] = ~0ull;
+            val[p] = 0u;
             s.bkt[p] = 0xFFFFu;
         } else {
             s.bkt[p] = (uint16_t)p;
@@ -882,20 +1005,20 @@ __device__ void bitonic_fallback(SmemTile &s, uint32_t len)
     for (uint32_t size = 2; size <= L; size <<= 1) {
         for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
             for (uint32_t t = threadIdx.x; t < L / 2; t += BLOCK) {
-                uint32_t i = 2 * stride * (t / stride) + (t % stride);
-                uint32_t jj = i + stride;
-                bool asc = (i & size) == 0;
-                unsigned long long ki = s.key[i], kj = s.key[jj];
-                uint16_t ii = s.bkt[i], ij = s.bkt[jj];
-                bool gt = ki > kj || (ki == kj && ii > ij);
+                const uint32_t i = 2 * stride * (t / stride) + (t % stride);
+                const uint32_t jj = i + stride;
+                const bool asc = (i & size) == 0;
+                const unsigned long long ki = key[i], kj = key[jj];
+                const uint16_t ii = s.bkt[i], ij = s.bkt[jj];
+                const bool gt = ki > kj || (ki == kj && ii > ij);
                 if (gt == asc) {
-                    s.key[i] = kj;
-                    s.key[jj] = ki;
+                    key[i] = kj;
+                    key[jj] = ki;
                     s.bkt[i] = ij;
                     s.bkt[jj] = ii;
-                    uint32_t tv = s.val[i];
-                    s.val[i] = s.val[jj];
-                    s.val[jj] = tv;
+                    const uint32_t tv = val[i];
+                    val[i] = val[jj];
+                    val[jj] = tv;
                 }
             }
             __syncthreads();
@@ -909,22 +1032,56 @@ __device__ void bitonic_fallback(SmemTile &s, uint32_t len)
 // range-map partition into sub-buckets (exact counting sort when the key
 // range is smaller than the sub-bucket count), then insertion sort of each
 // sub-bucket; a bitonic sort is the fallback for a badly split leaf.
-__device__ void task_finish(const Params &P, const Item it, SmemTile &s)
+__device__ __noinline__ void task_finish(const Params &P, const Item it, SmemTile &s, Pipe &pp)
 {
     const unsigned long long off = it.off;
     const uint32_t len = it.len, buf = it.buf;
-    const uint64_t *srck = keys_of(P, buf) + off;
-    const uint32_t *srcv = vals_of(P, buf) + off;
+    const uint64_t *srck = keys_of(P, buf);
+    const uint32_t *srcv = vals_of(P, buf);
     uint64_t *dk = P.ukeys + off;
     uint32_t *dv = P.uvals + off;
-    unsigned long long x[IPT];
-    uint32_t v[IPT];
+    unsigned long long *key;
+    uint32_t *val;
+    if (bulk_ok(P, buf)) {
+        if (threadIdx.x == 0) {
+            const unsigned long long a0 = off & ~1ull, a1 = min((off + len + 1) & ~1ull, P.n & ~1ull);
+            const unsigned long long b0 = off & ~3ull, b1 = min((off + len + 3) & ~3ull, P.n & ~3ull);
+            const uint32_t bk = a1 > a0 ? (uint32_t)(a1 - a0) * 8u : 0u;
+            const uint32_t bv = b1 > b0 ? (uint32_t)(b1 - b0) * 4u : 0u;
+            mbar_expect_arrive(&s.bar[0], bk + bv);
+            if (bk) bulk_g2s(s.u.leaf.key, srck + a0, bk, &s.bar[0]);
+            if (bv) bulk_g2s(s.u.leaf.val, srcv + b0, bv, &s.bar[0]);
+        }
+        key = s.u.leaf.key + (off & 1ull);
+        val = s.u.leaf.val + (off & 3ull);
+        const bool ok = mbar_wait(&s.bar[0], pp.uses[0] & 1u, P.wait_ns);
+        pp.uses[0]++;
+        if (__syncthreads_or(!ok)) {  // CTA-uniform: every thread leaves together
+            set_error(P, ST_TIMEOUT);
+            return;
+        }
+        const unsigned long long end = off + len;
+        for (unsigned long long e = max(off, P.n & ~1ull) + threadIdx.x; e < end; e += BLOCK)
+            key[e - off] = __ldcg(srck + e);
+        for (unsigned long long e = max(off, P.n & ~3ull) + threadIdx.x; e < end; e += BLOCK)
+            val[e - off] = __ldcg(srcv + e);
+    } else {
+        key = s.u.leaf.key;
+        val = s.u.leaf.val;
+        for (uint32_t i = threadIdx.x; i < len; i += BLOCK) {
+            key[i] = __ldcg(srck + off + i);
+            val[i] = __ldcg(srcv + off + i);
+        }
+    }
+    __syncthreads();
+    unsigned long long x[LEAF_IPT];
+    uint32_t v[LEAF_IPT];
     unsigned long long mn = ~0ull, mx = 0ull;
 #pragma unroll
-    for (int i = 0; i < IPT; i++) {
-        uint32_t p = slot_index(i);
-        x[i] = p < len ? __ldcg(srck + p) : 0ull;
-        v[i] = p < len ? __ldcg(srcv + p) : 0u;
+    for (int i = 0; i < LEAF_IPT; i++) {
+        const uint32_t p = leaf_slot(i);
+        x[i] = p < len ? key[p] : 0ull;
+        v[i] = p < len ? val[p] : 0u;
         if (p < len) {
             mn = x[i] < mn ? x[i] : mn;
             mx = x[i] > mx ? x[i] : mx;
@@ -932,7 +1089,7 @@ __device__ void task_finish(const Params &P, const Item it, SmemTile &s)
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
-        unsigned long long a = shfl_down64(mn, o), b2 = shfl_down64(mx, o);
+        const unsigned long long a = shfl_down64(mn, o), b2 = shfl_down64(mx, o);
         mn = a < mn ? a : mn;
         mx = b2 > mx ? b2 : mx;
     }
@@ -953,37 +1110,24 @@ __device__ void task_finish(const Params &P, const Item it, SmemTile &s)
     }
     if (mn == mx) {  // identical keys: in order already
         if (buf) {
-#pragma unroll
-            for (int i = 0; i < IPT; i++) {
-                uint32_t p = slot_index(i);
-                if (p < len) {
-                    __stcg(dk + p, x[i]);
-                    __stcg(dv + p, v[i]);
-                }
+            for (uint32_t p = threadIdx.x; p < len; p += BLOCK) {
+                __stcg(dk + p, key[p]);
+                __stcg(dv + p, val[p]);
             }
         }
         return;
     }
     if (len <= (uint32_t)RANK_SMALL) {
-#pragma unroll
-        for (int i = 0; i < IPT; i++) {
-            uint32_t p = slot_index(i);
-            if (p < len) {
-                s.key[p] = x[i];
-                s.val[p] = v[i];
-            }
-        }
-        __syncthreads();
         const uint32_t t = threadIdx.x;
         if (t < len) {
-            const unsigned long long kt = s.key[t];
+            const unsigned long long kt = key[t];
             uint32_t r = 0;
             for (uint32_t q = 0; q < len; q++) {
-                unsigned long long kq = s.key[q];
+                const unsigned long long kq = key[q];
                 r += (kq < kt) || (kq == kt && q < t);
             }
             __stcg(dk + r, kt);
-            __stcg(dv + r, s.val[t]);
+            __stcg(dv + r, val[t]);
         }
         return;
     }
@@ -991,22 +1135,22 @@ __device__ void task_finish(const Params &P, const Item it, SmemTile &s)
     const uint32_t M = min((uint32_t)NB_MAX, pow2ceil32(len) / 4);
     uint32_t rshift, rmult;
     range_params(mx - mn, M, &rshift, &rmult);
-    uint32_t b[IPT], pos[IPT];
+    uint32_t b[LEAF_IPT], pos[LEAF_IPT];
 #pragma unroll
-    for (int i = 0; i < IPT; i++) {
-        if (slot_index(i) < len) {
-            unsigned long long d = x[i] - mn;
+    for (int i = 0; i < LEAF_IPT; i++) {
+        if (leaf_slot(i) < len) {
+            const unsigned long long d = x[i] - mn;
             b[i] = rmult == 0 ? (uint32_t)d : __umulhi((uint32_t)(d >> rshift), rmult);
         } else {
             b[i] = INVALID;
         }
     }
-    tile_rank(b, pos, M, s);
+    tile_rank<LEAF_IPT>(b, pos, M, s);
 #pragma unroll
-    for (int i = 0; i < IPT; i++) {
+    for (int i = 0; i < LEAF_IPT; i++) {
         if (b[i] != INVALID) {
-            s.key[pos[i]] = x[i];
-            s.val[pos[i]] = v[i];
+            key[pos[i]] = x[i];
+            val[pos[i]] = v[i];
         }
     }
     if (threadIdx.x == 0) s.flag = 0;
@@ -1014,27 +1158,28 @@ __device__ void task_finish(const Params &P, const Item it, SmemTile &s)
     bool ok = true;
     for (uint32_t q = threadIdx.x; q < M; q += BLOCK) {
         const uint32_t c = s.tcount[q];
-        if (c >= 2) ok = ok && insertion_sort_budget(s.key + s.tstart[q], s.val + s.tstart[q], c, 1024);
+        if (c >= 2) ok = ok && insertion_sort_budget(key + s.tstart[q], val + s.tstart[q], c, 1024);
     }
     if (!ok) s.flag = 1;
     __syncthreads();
     if (s.flag) {
-        bitonic_fallback(s, len);
+        bitonic_fallback(s, key, val, len);
         if (threadIdx.x == 0) atomicAdd(&P.ctl->n_leaf_fb, 1ull);
     }
     for (uint32_t p = threadIdx.x; p < len; p += BLOCK) {
-        __stcg(dk + p, s.key[p]);
-        __stcg(dv + p, s.val[p]);
+        __stcg(dk + p, key[p]);
+        __stcg(dv + p, val[p]);
     }
 }
 
 // ------------------------------------------------------------ COPY
-__device__ void task_copy(const Params &P, uint32_t sid, uint32_t tile)
+// All-equal large (sub)array living in scratch: one LEAF_CAP slice per task.
+__device__ __noinline__ void task_copy(const Params &P, uint32_t sid, uint32_t tile)
 {
     const Seg *S = &P.segs[sid];
-    const unsigned long long off = __ldcg(&S->off) + (size_t)tile * TILE;
+    const unsigned long long off = __ldcg(&S->off) + (size_t)tile * LEAF_CAP;
     const uint32_t len = __ldcg(&S->len);
-    const uint32_t cnt = min((uint32_t)TILE, len - tile * TILE);
+    const uint32_t cnt = min((uint32_t)LEAF_CAP, len - tile * LEAF_CAP);
     for (uint32_t p = threadIdx.x; p < cnt; p += BLOCK) {
         __stcg(P.ukeys + off + p, __ldcg(P.skeys + off + p));
         __stcg(P.uvals + off + p, __ldcg(P.svals + off + p));
