@@ -172,6 +172,33 @@ int zsort_sync_status(zsort_stream_t stream);
 /* Waits for `stream` and copies the counters of its last call to *out. */
 int zsort_last_stats(zsort_stream_t stream, zsort_stats *out);
 
+/* Largest n accepted by zsort_pairs_noalloc. */
+#define ZSORT_NOALLOC_MAX_N ((uint64_t)1 << 20)
+
+/* zsort_pairs_noalloc -- the sort of zsort_pairs (default options, uint64
+ * keys) for callers that cannot allocate device memory: code running while
+ * a CUDA graph is being captured, hosts that forbid device allocation after
+ * start-up, or processes that must stay inside a fixed memory pool.  The
+ * paper has no counterpart; it is a deployment variant.
+ *   - Allocates nothing: no cudaMalloc/cudaFree and no allocating library
+ *     call.  Its scratch is a static __device__ array of about 18 MB for up
+ *     to ZSORT_NOALLOC_MAX_N (2^20) elements that every GPU which loads this
+ *     library holds until the process exits.  n > ZSORT_NOALLOC_MAX_N is
+ *     rejected with ZSORT_ERR_INVALID before anything is enqueued.
+ *   - The first call on a device does its set-up (looks up the array's device
+ *     address and sets a kernel attribute), so make that first call before
+ *     any stream capture.
+ *   - Every call, on every stream, shares the one array and leaves its
+ *     contents behind; calls that overlap on the GPU race and corrupt each
+ *     other's results, so order them (one stream, or events).
+ *   - status: optional caller-owned DEVICE int32 that receives the call's
+ *     device status (ZSORT_OK or a negative code) in stream order; NULL
+ *     skips it.  zsort_sync_status() and zsort_last_stats() do not cover
+ *     this entry point.
+ * keys/vals as for zsort_pairs; returns host-detected errors at once. */
+int zsort_pairs_noalloc(uint64_t *keys, uint32_t *vals, uint64_t n, int32_t *status,
+                        zsort_stream_t stream);
+
 /* Human-readable text of a status code (static storage). */
 const char *zsort_strerror(int code);
 

@@ -28,6 +28,7 @@ ERR_INVALID, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_BAD_OFFSETS, ERR_CAPACITY, ER
 MAP_ZSCORE, MAP_LEARNED = 0, 1
 KEY_TYPES = {"u64": 0, "i64": 1, "f64": 2}
 MAX_N = 1 << 30
+NOALLOC_MAX_N = 1 << 20
 
 
 class ZsortError(RuntimeError):
@@ -128,6 +129,7 @@ def load():
         "zsort_sync_status": (i32, [vp]),
         "zsort_last_stats": (i32, [vp, ctypes.POINTER(Stats)]),
         "zsort_strerror": (ctypes.c_char_p, [i32]),
+        "zsort_pairs_noalloc": (i32, [vp, vp, u64, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

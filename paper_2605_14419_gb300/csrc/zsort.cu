@@ -429,6 +429,75 @@ Workspace *find_ws(cudaStream_t stream)
 
 }  // namespace
 
+// ---------------------------------------------------------------- no-alloc entry
+// Some callers cannot call cudaMalloc at all: code that runs while a CUDA
+// graph is being captured, real-time or embedded hosts that forbid device
+// allocation after start-up, and processes whose device memory is owned by
+// a pool they may not grow.  zsort_pairs_noalloc serves them: its scratch
+// is one file-scope __device__ array, sized for NA_MAX_N elements and held by
+// every GPU that loads this library until the process exits.
+namespace {
+
+constexpr unsigned long long NA_MAX_N = ZSORT_NOALLOC_MAX_N;
+constexpr unsigned long long NA_LARGE_MIN = 65536;  // the default large_min
+constexpr size_t na_align(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Layout of the static scratch: the same regions as a regular workspace for
+// NA_MAX_N elements and one segment, with one learned-map training slot.
+struct NaLayout {
+    unsigned long long qcap, segcap, itemcap, statuscap, traincap;
+    size_t skeys, svals, ctl, entries, ready, tnext, tdone, segs, items, counts, bstart, status, pwl,
+        train, total;
+};
+constexpr NaLayout na_layout()
+{
+    NaLayout L{};
+    L.qcap = NA_MAX_N / 128 + 4 + 4096;
+    L.segcap = 3 * (NA_MAX_N / (NA_LARGE_MIN + 1)) + 64;
+    L.itemcap = 2 + NA_MAX_N / 32 + 4096;
+    L.statuscap = 4ull * NB_MAX * (NA_MAX_N / (4 * TILE) + 64);
+    L.traincap = 1;
+    size_t o = 0;
+    L.skeys = o; o = na_align(o + NA_MAX_N * 8);
+    L.svals = o; o = na_align(o + NA_MAX_N * 4);
+    L.ctl = o; o = na_align(o + sizeof(Ctl));
+    L.entries = o; o = na_align(o + L.qcap * sizeof(Entry));
+    L.ready = o; o = na_align(o + L.qcap * 4);
+    L.tnext = o; o = na_align(o + L.qcap * 4);
+    L.tdone = o; o = na_align(o + L.qcap * 4);
+    L.segs = o; o = na_align(o + L.segcap * sizeof(Seg));
+    L.items = o; o = na_align(o + L.itemcap * sizeof(Item));
+    L.counts = o; o = na_align(o + L.segcap * NB_MAX * 4);
+    L.bstart = o; o = na_align(o + L.segcap * NB_MAX * 4);
+    L.status = o; o = na_align(o + L.statuscap * 4);
+    L.pwl = o; o = na_align(o + L.segcap * PWL_STRIDE * 4);
+    L.train = o; o = na_align(o + L.traincap * 2 * SAMPLE_MAX * 4);
+    L.total = o;
+    return L;
+}
+constexpr NaLayout NA = na_layout();
+
+// Per-device set-up of the no-alloc path (the symbol's device address).
+struct NaDevice {
+    bool ready = false;
+    char *base = nullptr;
+    int sms = 0, occ = 0;
+    uint32_t epoch = 0;
+};
+std::mutex g_na_mu;
+NaDevice g_na_dev[64];
+
+}  // namespace
+
+// The scratch itself: zero at module load, reused (not cleared) by every call.
+static __device__ __align__(256) unsigned char g_na_scratch[NA.total];
+
+// Copies a call's device status word to the caller's int.
+__global__ void k_na_status(const Ctl *ctl, int32_t *out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) *out = (int32_t)ctl->error;
+}
+
 // ---------------------------------------------------------------- C ABI
 extern "C" {
 
@@ -594,6 +663,92 @@ int zsort_last_stats(zsort_stream_t stream, zsort_stats *out)
     out->idle_ns = c.idle_ns;
     out->busy_window_ns = (c.t_last > c.t_first && c.t_first != ~0ull) ? c.t_last - c.t_first : 0;
     return ZSORT_OK;
+}
+
+// zsort_pairs_noalloc: see include/zsort.h.  The first call on a device
+// looks up the address of the static scratch (cudaGetSymbolAddress, with
+// that device current) and sets the kernel's shared-memory attribute; make
+// that first call before any stream capture.
+int zsort_pairs_noalloc(uint64_t *keys, uint32_t *vals, uint64_t n, int32_t *status, zsort_stream_t stream)
+{
+    if (n > NA_MAX_N) return ZSORT_ERR_INVALID;
+    if (n <= 1) {
+        if (status) {
+            cudaError_t ce = cudaMemsetAsync(status, 0, sizeof(int32_t), reinterpret_cast<cudaStream_t>(stream));
+            if (ce != cudaSuccess) return cuda_err(ce);
+        }
+        return ZSORT_OK;
+    }
+    if (!keys || !vals) return ZSORT_ERR_INVALID;
+    int dev = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce != cudaSuccess) return cuda_err(ce);
+    if (dev < 0 || dev >= 64) return ZSORT_ERR_INVALID;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    std::lock_guard<std::mutex> lock(g_na_mu);
+    NaDevice &D = g_na_dev[dev];
+    if (!D.ready) {
+        void *addr = nullptr;
+        ce = cudaGetSymbolAddress(&addr, g_na_scratch);
+        if (ce != cudaSuccess || !addr) return ZSORT_ERR_CUDA;
+        ce = cudaDeviceGetAttribute(&D.sms, cudaDevAttrMultiProcessorCount, dev);
+        if (ce != cudaSuccess) return cuda_err(ce);
+        ce = cudaFuncSetAttribute(k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+        if (ce != cudaSuccess) return cuda_err(ce);
+        ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&D.occ, k_persistent, BLOCK, SMEM_BYTES);
+        if (ce != cudaSuccess) return cuda_err(ce);
+        if (D.occ < 1) return ZSORT_ERR_CUDA;
+        D.base = static_cast<char *>(addr);
+        D.ready = true;
+    }
+    zsort_opts o;
+    zsort_default_opts(&o);
+    char *b = D.base;
+    Params P{};
+    P.ukeys = keys;
+    P.uvals = vals;
+    P.n = n;
+    P.skeys = reinterpret_cast<uint64_t *>(b + NA.skeys);
+    P.svals = reinterpret_cast<uint32_t *>(b + NA.svals);
+    P.ctl = reinterpret_cast<Ctl *>(b + NA.ctl);
+    P.entries = reinterpret_cast<Entry *>(b + NA.entries);
+    P.ready = reinterpret_cast<uint32_t *>(b + NA.ready);
+    P.tnext = reinterpret_cast<uint32_t *>(b + NA.tnext);
+    P.tdone = reinterpret_cast<uint32_t *>(b + NA.tdone);
+    P.qcap = (uint32_t)NA.qcap;
+    P.segs = reinterpret_cast<Seg *>(b + NA.segs);
+    P.segcap = (uint32_t)NA.segcap;
+    P.items = reinterpret_cast<Item *>(b + NA.items);
+    P.itemcap = (uint32_t)NA.itemcap;
+    P.counts = reinterpret_cast<uint32_t *>(b + NA.counts);
+    P.bstart = reinterpret_cast<uint32_t *>(b + NA.bstart);
+    P.status = reinterpret_cast<uint32_t *>(b + NA.status);
+    P.statuscap = NA.statuscap;
+    P.pwl = reinterpret_cast<float *>(b + NA.pwl);
+    P.trainbuf = reinterpret_cast<uint32_t *>(b + NA.train);
+    P.traincap = (uint32_t)NA.traincap;
+    // ready flags from earlier calls hold older epochs; the array starts at 0
+    if (++D.epoch == 0) D.epoch = 1;
+    P.epoch = D.epoch;
+    P.kmax = o.kmax;
+    P.leaf_target = o.leaf_target;
+    P.large_min = o.large_min;
+    P.learn_min = o.learn_min;
+    P.sample = o.sample;
+    P.mapper = o.mapper;
+    P.guard_level = o.guard_level;
+    P.fallback_ratio = o.fallback_ratio;
+    P.seed = o.seed;
+    P.wait_ns = (unsigned long long)o.wait_limit_ms * 1000000ull;
+    P.user_aligned = ((reinterpret_cast<uintptr_t>(keys) | reinterpret_cast<uintptr_t>(vals)) & 15u) == 0;
+    P.nctas = (uint32_t)(D.sms * D.occ);
+    ce = cudaMemsetAsync(P.ctl, 0, sizeof(Ctl), st);  // the control block must start at zero
+    if (ce != cudaSuccess) return cuda_err(ce);
+    k_init_segments<<<1, 256, 0, st>>>(P, nullptr, 1);
+    k_init_publish<<<1, 32, 0, st>>>(P, 1);
+    k_persistent<<<P.nctas, BLOCK, SMEM_BYTES, st>>>(P);
+    if (status) k_na_status<<<1, 32, 0, st>>>(P.ctl, status);
+    return cuda_err(cudaGetLastError());
 }
 
 const char *zsort_strerror(int code)
