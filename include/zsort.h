@@ -128,7 +128,7 @@ typedef struct {
     uint64_t busy_window_ns;    /* first task start to last task end              */
 } zsort_stats;
 
-/* Fills *o with the defaults (z-score map, kmax 1024, ...). */
+/* Fills *o with the defaults (z-score map, kmax 512, leaf target 2048, ...). */
 void zsort_default_opts(zsort_opts *o);
 
 /* Sorts n (uint64 key, uint32 payload) pairs in place, stably (see above).

@@ -22,7 +22,7 @@
 using namespace zs;
 
 // ---------------------------------------------------------------- kernels
-__global__ void __launch_bounds__(BLOCK, 2) k_persistent(Params P)
+__global__ void __launch_bounds__(BLOCK, 2) k_persistent(const __grid_constant__ Params P)
 {
     extern __shared__ __align__(128) unsigned char smraw[];
     SmemTile &s = *reinterpret_cast<SmemTile *>(smraw);
@@ -507,7 +507,7 @@ void zsort_default_opts(zsort_opts *o)
     std::memset(o, 0, sizeof(*o));
     o->struct_size = sizeof(zsort_opts);
     o->mapper = ZSORT_MAP_ZSCORE;
-    o->kmax = 1024;
+    o->kmax = 512;
     o->leaf_target = 2048;
     o->large_min = 65536;
     o->learn_min = 1u << 20;

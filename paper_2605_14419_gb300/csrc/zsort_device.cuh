@@ -9,6 +9,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <cstddef>
 
 namespace zs {
 
@@ -444,7 +445,7 @@ struct SmemTile {
         ChildList children;
     } u;
     uint16_t bkt[LEAF_CAP];          // bucket of each staged element / bitonic index
-    uint16_t wcnt[WARPS * NB_MAX];   // per-warp counts, then warp prefixes
+    __align__(16) uint16_t wcnt[NB_MAX * WARPS];  // [bucket][warp] counts, then warp prefixes
     uint32_t tcount[NB_MAX];         // tile count per bucket
     uint32_t tstart[NB_MAX];         // tile-local exclusive start per bucket
     uint32_t gdelta[NB_MAX];         // global position - tile position (mod 2^32)
@@ -460,18 +461,23 @@ struct SmemTile {
     unsigned long long red64[WARPS * 2];
 };
 static_assert(sizeof(LeafBuf) <= sizeof(TileBuf) * 2, "leaf fits the tile buffers");
+// The leaf finish keeps LEAF_CAP u16 ranks in hist + cursor (adjacent).
+static_assert(offsetof(SmemTile, cursor) == offsetof(SmemTile, hist) + 4 * NB_MAX, "hist, cursor adjacent");
+static_assert(8 * NB_MAX >= 2 * LEAF_CAP, "rank array fits hist + cursor");
 
 // ------------------------------------------------------------ block scan
 // Exclusive scan of in[0..nb) into out (may alias); returns the total.
+// nb <= BLOCK * MAXPER.
+template <int MAXPER = NB_MAX / BLOCK>
 __device__ uint32_t block_exclusive_scan(const uint32_t *in, uint32_t *out, uint32_t nb, uint32_t *wsum)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t per = (nb + BLOCK - 1) / BLOCK;  // <= 4
+    const uint32_t per = (nb + BLOCK - 1) / BLOCK;
     const uint32_t base = threadIdx.x * per;
-    uint32_t loc[4];
+    uint32_t loc[MAXPER];
     uint32_t sum = 0;
 #pragma unroll
-    for (uint32_t j = 0; j < 4; j++) {
+    for (uint32_t j = 0; j < (uint32_t)MAXPER; j++) {
         if (j < per) {
             uint32_t idx = base + j;
             uint32_t v = idx < nb ? in[idx] : 0u;
@@ -501,7 +507,7 @@ __device__ uint32_t block_exclusive_scan(const uint32_t *in, uint32_t *out, uint
     __syncthreads();
     uint32_t excl = wsum[warp] + x - sum;
 #pragma unroll
-    for (uint32_t j = 0; j < 4; j++) {
+    for (uint32_t j = 0; j < (uint32_t)MAXPER; j++) {
         if (j < per) {
             uint32_t idx = base + j;
             if (idx < nb) out[idx] = excl + loc[j];
@@ -524,14 +530,13 @@ __device__ uint32_t block_exclusive_scan(const uint32_t *in, uint32_t *out, uint
 template <int NI, int NBITS>
 __device__ void tile_rank_bits(const uint32_t (&b)[NI], uint32_t (&pos)[NI], uint32_t nb, SmemTile &s)
 {
+    static_assert(WARPS == 8, "per-bucket warp counters are packed in 16 bytes");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    {
-        uint32_t *w32 = reinterpret_cast<uint32_t *>(s.wcnt);
-        for (uint32_t i = threadIdx.x; i < (uint32_t)WARPS * nb / 2; i += BLOCK) w32[i] = 0u;
-    }
+    // per-bucket counters of the 8 warps, [bucket][warp] u16: 16 bytes a bucket
+    uint4 *w4 = reinterpret_cast<uint4 *>(s.wcnt);
+    for (uint32_t q = threadIdx.x; q < nb; q += BLOCK) w4[q] = make_uint4(0u, 0u, 0u, 0u);
     __syncthreads();
     const uint32_t lt = (1u << lane) - 1u;
-    uint16_t *wc = s.wcnt + warp * nb;
 #pragma unroll
     for (int i = 0; i < NI; i++) {
         // lanes with an equal bucket: AND over the bucket's bits of the ballot
@@ -548,28 +553,29 @@ __device__ void tile_rank_bits(const uint32_t (&b)[NI], uint32_t (&pos)[NI], uin
         const int leader = __ffs(peers) - 1;
         uint32_t before = 0;
         if (lane == leader && bi != INVALID) {
-            before = wc[bi];
-            wc[bi] = (uint16_t)(before + __popc(peers));
+            uint16_t *c = s.wcnt + bi * WARPS + warp;
+            before = *c;
+            *c = (uint16_t)(before + __popc(peers));
         }
         before = __shfl_sync(0xffffffffu, before, leader);
         pos[i] = before + __popc(peers & lt);
     }
     __syncthreads();
+    // exclusive prefix over the warps of each bucket, in registers
     for (uint32_t q = threadIdx.x; q < nb; q += BLOCK) {
-        uint32_t run = 0;
-#pragma unroll
-        for (int w = 0; w < WARPS; w++) {
-            uint32_t c = s.wcnt[w * nb + q];
-            s.wcnt[w * nb + q] = (uint16_t)run;
-            run += c;
-        }
-        s.tcount[q] = run;
+        const uint4 c = w4[q];
+        const uint32_t c0 = c.x & 0xffffu, c1 = c.x >> 16, c2 = c.y & 0xffffu, c3 = c.y >> 16;
+        const uint32_t c4 = c.z & 0xffffu, c5 = c.z >> 16, c6 = c.w & 0xffffu, c7 = c.w >> 16;
+        const uint32_t p1 = c0, p2 = p1 + c1, p3 = p2 + c2, p4 = p3 + c3, p5 = p4 + c4, p6 = p5 + c5,
+                       p7 = p6 + c6;
+        w4[q] = make_uint4(p1 << 16, p2 | (p3 << 16), p4 | (p5 << 16), p6 | (p7 << 16));
+        s.tcount[q] = p7 + c7;
     }
     __syncthreads();
     block_exclusive_scan(s.tcount, s.tstart, nb, s.wsum);
 #pragma unroll
     for (int i = 0; i < NI; i++)
-        if (b[i] != INVALID) pos[i] += s.tstart[b[i]] + s.wcnt[warp * nb + b[i]];
+        if (b[i] != INVALID) pos[i] += s.tstart[b[i]] + s.wcnt[b[i] * WARPS + warp];
 }
 
 // Bucket ids below nb <= NB_MAX = 2^10: ten ballots identify equal buckets.

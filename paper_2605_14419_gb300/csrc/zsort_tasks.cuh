@@ -378,10 +378,13 @@ __device__ __forceinline__ void body_hist(SmemTile &s, uint32_t cnt, const unsig
 // Stable scatter of one tile: ranks by (bucket, position), stages the tile
 // ordered by bucket in shared memory, then writes each bucket's run at its
 // running cursor (coalesced within runs); cursors advance by the tile counts.
+// The output pass recomputes each staged key's bucket, except for the learned
+// map, whose buckets are staged.
 __device__ __forceinline__ void body_scatter(const Params &P, SmemTile &s, uint32_t cnt, unsigned long long *sk,
                                              uint32_t *sv, uint64_t *dstk, uint32_t *dstv, uint32_t seglen)
 {
     const uint32_t k = s.map.k;
+    const bool stage_b = s.map.kind == MAP_PWL;
     unsigned long long x[IPT];
     uint32_t v[IPT], b[IPT], pos[IPT];
 #pragma unroll
@@ -393,27 +396,31 @@ __device__ __forceinline__ void body_scatter(const Params &P, SmemTile &s, uint3
         b[i] = ok ? map_key(s.map, x[i]) : INVALID;
     }
     tile_rank<IPT>(b, pos, k, s);
-    for (uint32_t q = threadIdx.x; q < k; q += BLOCK) s.gdelta[q] = s.cursor[q] - s.tstart[q];
+    for (uint32_t q = threadIdx.x; q < k; q += BLOCK) {
+        const uint32_t c = s.cursor[q];
+        s.gdelta[q] = c - s.tstart[q];
+        s.cursor[q] = c + s.tcount[q];
+    }
 #pragma unroll
     for (int i = 0; i < IPT; i++) {
         if (b[i] != INVALID) {
             sk[pos[i]] = x[i];
             sv[pos[i]] = v[i];
-            s.bkt[pos[i]] = (uint16_t)b[i];
+            if (stage_b) s.bkt[pos[i]] = (uint16_t)b[i];
         }
     }
     __syncthreads();
     for (uint32_t p = threadIdx.x; p < cnt; p += BLOCK) {
-        const uint32_t rel = s.gdelta[s.bkt[p]] + p;
+        const unsigned long long key = sk[p];
+        const uint32_t q = stage_b ? (uint32_t)s.bkt[p] : map_key(s.map, key);
+        const uint32_t rel = s.gdelta[q] + p;
         if (rel < seglen) {
-            __stcg(dstk + rel, sk[p]);
+            __stcg(dstk + rel, key);
             __stcg(dstv + rel, sv[p]);
         } else {
             set_error(P, ST_INTERNAL);
         }
     }
-    __syncthreads();
-    for (uint32_t q = threadIdx.x; q < k; q += BLOCK) s.cursor[q] += s.tcount[q];
 }
 
 // ------------------------------------------------------------ children
@@ -1026,12 +1033,143 @@ __device__ void bitonic_fallback(SmemTile &s, unsigned long long *key, uint32_t 
     }
 }
 
+// Sub-bucket of a leaf key: range map (the counting map when rm == 0).
+__device__ __forceinline__ uint32_t leaf_sub(unsigned long long key, unsigned long long mn, uint32_t rs,
+                                             uint32_t rm)
+{
+    const unsigned long long d = key - mn;
+    return rm == 0 ? (uint32_t)d : __umulhi((uint32_t)(d >> rs), rm);
+}
+
+constexpr uint32_t LEAF_M2_MAX = 2048;  // sub-buckets of the fast leaf path
+constexpr uint32_t LEAF_FAST_MAX = 32;  // largest sub-bucket the fast path ranks by counting
+
+// Fast leaf path: sub-bucket counts in cnt[0..M2) are known.  Pairs are
+// placed by sub-bucket with smem atomics (unstable), then each pair's rank
+// is counted inside its sub-bucket on (key, leaf position), a total order
+// whose sorted sequence is the stable sort; pairs move to their ranks.
+__device__ __noinline__ void finish_fast(SmemTile &s, unsigned long long *key, uint32_t *val, uint32_t len,
+                                         unsigned long long mn, uint32_t rs, uint32_t rm, uint32_t M2,
+                                         uint64_t *dk, uint32_t *dv)
+{
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(s.wcnt);
+    uint32_t *cur = cnt + LEAF_M2_MAX;
+    uint16_t *sidx = s.bkt;                                // leaf position of each placed pair
+    uint16_t *rank = reinterpret_cast<uint16_t *>(s.hist);  // hist + cursor: LEAF_CAP u16
+    block_exclusive_scan<LEAF_M2_MAX / BLOCK>(cnt, cnt, M2, s.wsum);
+    for (uint32_t q = threadIdx.x; q < M2; q += BLOCK) cur[q] = cnt[q];
+    unsigned long long kk[LEAF_IPT];
+    uint32_t vv[LEAF_IPT];
+#pragma unroll
+    for (int j = 0; j < LEAF_IPT; j++) {
+        const uint32_t p = threadIdx.x + j * BLOCK;
+        kk[j] = p < len ? key[p] : 0ull;
+        vv[j] = p < len ? val[p] : 0u;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < LEAF_IPT; j++) {
+        const uint32_t p = threadIdx.x + j * BLOCK;
+        if (p < len) {
+            const uint32_t q = atomicAdd(&cur[leaf_sub(kk[j], mn, rs, rm)], 1u);
+            key[q] = kk[j];
+            val[q] = vv[j];
+            sidx[q] = (uint16_t)p;
+        }
+    }
+    __syncthreads();
+    for (uint32_t p = threadIdx.x; p < len; p += BLOCK) {
+        const unsigned long long xk = key[p];
+        const uint32_t me = sidx[p];
+        const uint32_t q = leaf_sub(xk, mn, rs, rm);
+        const uint32_t lo = cnt[q], hi = cur[q];
+        uint32_t r = lo;
+        for (uint32_t j = lo; j < hi; j++) {
+            const unsigned long long kj = key[j];
+            r += (kj < xk) || (kj == xk && sidx[j] < me);
+        }
+        rank[p] = (uint16_t)r;
+    }
+    __syncthreads();
+    uint32_t rr[LEAF_IPT];
+#pragma unroll
+    for (int j = 0; j < LEAF_IPT; j++) {
+        const uint32_t p = threadIdx.x + j * BLOCK;
+        if (p < len) {
+            kk[j] = key[p];
+            vv[j] = val[p];
+            rr[j] = rank[p];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < LEAF_IPT; j++) {
+        const uint32_t p = threadIdx.x + j * BLOCK;
+        if (p < len) {
+            key[rr[j]] = kk[j];
+            val[rr[j]] = vv[j];
+        }
+    }
+    __syncthreads();
+    for (uint32_t p = threadIdx.x; p < len; p += BLOCK) {
+        __stcg(dk + p, key[p]);
+        __stcg(dv + p, val[p]);
+    }
+}
+
+// Stable leaf path, for leaves with a large sub-bucket (typically many equal
+// keys): sub-buckets by the range map placed in input order by the ballot
+// ranking, then insertion sort per sub-bucket (no moves among equal keys); a
+// bitonic sort on (key, position) if a sub-bucket needs too many moves.
+__device__ __noinline__ void finish_stable(const Params &P, SmemTile &s, unsigned long long *key, uint32_t *val,
+                                           uint32_t len, unsigned long long mn, unsigned long long mx,
+                                           uint64_t *dk, uint32_t *dv)
+{
+    const uint32_t M = min((uint32_t)NB_MAX, pow2ceil32(len) / 4);
+    uint32_t rshift, rmult;
+    range_params(mx - mn, M, &rshift, &rmult);
+    unsigned long long x[LEAF_IPT];
+    uint32_t v[LEAF_IPT], b[LEAF_IPT], pos[LEAF_IPT];
+#pragma unroll
+    for (int i = 0; i < LEAF_IPT; i++) {
+        const uint32_t p = leaf_slot(i);
+        x[i] = p < len ? key[p] : 0ull;
+        v[i] = p < len ? val[p] : 0u;
+        b[i] = p < len ? leaf_sub(x[i], mn, rshift, rmult) : INVALID;
+    }
+    tile_rank<LEAF_IPT>(b, pos, M, s);
+#pragma unroll
+    for (int i = 0; i < LEAF_IPT; i++) {
+        if (b[i] != INVALID) {
+            key[pos[i]] = x[i];
+            val[pos[i]] = v[i];
+        }
+    }
+    if (threadIdx.x == 0) s.flag = 0;
+    __syncthreads();
+    bool ok = true;
+    for (uint32_t q = threadIdx.x; q < M; q += BLOCK) {
+        const uint32_t c = s.tcount[q];
+        if (c >= 2) ok = ok && insertion_sort_budget(key + s.tstart[q], val + s.tstart[q], c, 1024);
+    }
+    if (!ok) s.flag = 1;
+    __syncthreads();
+    if (s.flag) {
+        bitonic_fallback(s, key, val, len);
+        if (threadIdx.x == 0) atomicAdd(&P.ctl->n_leaf_fb, 1ull);
+    }
+    for (uint32_t p = threadIdx.x; p < len; p += BLOCK) {
+        __stcg(dk + p, key[p]);
+        __stcg(dv + p, val[p]);
+    }
+}
+
 // Leaf: a group of whole buckets, at most LEAF_CAP pairs, sorted in shared
 // memory and written to the caller's arrays.  Mirrors the paper's finish
-// (insertion sort of small clusters, counting sort of small ranges): a
-// range-map partition into sub-buckets (exact counting sort when the key
-// range is smaller than the sub-bucket count), then insertion sort of each
-// sub-bucket; a bitonic sort is the fallback for a badly split leaf.
+// (insertion sort of small clusters, counting sort of small ranges): one
+// partition of the leaf into sub-buckets by the range map, an exact counting
+// sort when the key range is smaller than the sub-bucket count, then each
+// sub-bucket ordered (finish_fast / finish_stable).
 __device__ __noinline__ void task_finish(const Params &P, const Item it, SmemTile &s, Pipe &pp)
 {
     const unsigned long long off = it.off;
@@ -1074,18 +1212,11 @@ __device__ __noinline__ void task_finish(const Params &P, const Item it, SmemTil
         }
     }
     __syncthreads();
-    unsigned long long x[LEAF_IPT];
-    uint32_t v[LEAF_IPT];
     unsigned long long mn = ~0ull, mx = 0ull;
-#pragma unroll
-    for (int i = 0; i < LEAF_IPT; i++) {
-        const uint32_t p = leaf_slot(i);
-        x[i] = p < len ? key[p] : 0ull;
-        v[i] = p < len ? val[p] : 0u;
-        if (p < len) {
-            mn = x[i] < mn ? x[i] : mn;
-            mx = x[i] > mx ? x[i] : mx;
-        }
+    for (uint32_t p = threadIdx.x; p < len; p += BLOCK) {
+        const unsigned long long xk = key[p];
+        mn = xk < mn ? xk : mn;
+        mx = xk > mx ? xk : mx;
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
@@ -1131,45 +1262,20 @@ __device__ __noinline__ void task_finish(const Params &P, const Item it, SmemTil
         }
         return;
     }
-    // sub-buckets: range map with M buckets (counting map if max - min < M)
-    const uint32_t M = min((uint32_t)NB_MAX, pow2ceil32(len) / 4);
-    uint32_t rshift, rmult;
-    range_params(mx - mn, M, &rshift, &rmult);
-    uint32_t b[LEAF_IPT], pos[LEAF_IPT];
-#pragma unroll
-    for (int i = 0; i < LEAF_IPT; i++) {
-        if (leaf_slot(i) < len) {
-            const unsigned long long d = x[i] - mn;
-            b[i] = rmult == 0 ? (uint32_t)d : __umulhi((uint32_t)(d >> rshift), rmult);
-        } else {
-            b[i] = INVALID;
-        }
-    }
-    tile_rank<LEAF_IPT>(b, pos, M, s);
-#pragma unroll
-    for (int i = 0; i < LEAF_IPT; i++) {
-        if (b[i] != INVALID) {
-            key[pos[i]] = x[i];
-            val[pos[i]] = v[i];
-        }
-    }
-    if (threadIdx.x == 0) s.flag = 0;
+    const uint32_t M2 = min(LEAF_M2_MAX, pow2ceil32(len) / 2);
+    uint32_t rs2, rm2;
+    range_params(mx - mn, M2, &rs2, &rm2);
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(s.wcnt);
+    for (uint32_t q = threadIdx.x; q < M2; q += BLOCK) cnt[q] = 0u;
     __syncthreads();
-    bool ok = true;
-    for (uint32_t q = threadIdx.x; q < M; q += BLOCK) {
-        const uint32_t c = s.tcount[q];
-        if (c >= 2) ok = ok && insertion_sort_budget(key + s.tstart[q], val + s.tstart[q], c, 1024);
-    }
-    if (!ok) s.flag = 1;
+    for (uint32_t p = threadIdx.x; p < len; p += BLOCK) atomicAdd(&cnt[leaf_sub(key[p], mn, rs2, rm2)], 1u);
     __syncthreads();
-    if (s.flag) {
-        bitonic_fallback(s, key, val, len);
-        if (threadIdx.x == 0) atomicAdd(&P.ctl->n_leaf_fb, 1ull);
-    }
-    for (uint32_t p = threadIdx.x; p < len; p += BLOCK) {
-        __stcg(dk + p, key[p]);
-        __stcg(dv + p, val[p]);
-    }
+    uint32_t big = 0;
+    for (uint32_t q = threadIdx.x; q < M2; q += BLOCK) big = max(big, cnt[q]);
+    if (!__syncthreads_or(big > LEAF_FAST_MAX))
+        finish_fast(s, key, val, len, mn, rs2, rm2, M2, dk, dv);
+    else
+        finish_stable(P, s, key, val, len, mn, mx, dk, dv);
 }
 
 // ------------------------------------------------------------ COPY

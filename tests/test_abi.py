@@ -37,7 +37,7 @@ def test_struct_sizes_match_header(lib):
     o = z.Opts()
     lib.zsort_default_opts(ctypes.byref(o))
     assert o.struct_size == ctypes.sizeof(z.Opts)
-    assert o.kmax == 1024 and o.mapper == z.MAP_ZSCORE and o.fallback_ratio == 4.0
+    assert o.kmax == 512 and o.mapper == z.MAP_ZSCORE and o.fallback_ratio == 4.0
 
 
 def test_strerror_texts(lib):
