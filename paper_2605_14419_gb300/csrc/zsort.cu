@@ -127,7 +127,7 @@ __global__ void k_init_segments(Params P, const uint64_t *off, unsigned long lon
     if (len > P.large_min) {
         const uint32_t kk = choose_k(P, (uint32_t)len);
         const uint32_t tiles = (uint32_t)((len + TILE - 1) / TILE);
-        const uint32_t ct = choose_chunk_tiles(P, tiles);
+        const uint32_t ct = choose_chunk_tiles(P, tiles, (uint32_t)len);
         const uint32_t chunks = (tiles + ct - 1) / ct;
         const unsigned long long need = 2ull * chunks * kk;
         const uint32_t sid = atomicAdd(&C->seg_alloc, 1u);
@@ -238,13 +238,16 @@ struct Plan {
         off_items, off_counts, off_bstart, off_status, off_pwl, off_train, total;
 };
 
-Plan make_plan(unsigned long long n, unsigned long long nseg, unsigned long long large_min)
+Plan make_plan(unsigned long long n, unsigned long long nseg, unsigned long long large_min, int sms)
 {
     Plan p{};
     p.qcap = n / 128 + 4 * nseg + 4096;
     p.segcap = 3 * (n / (large_min + 1)) + 64;
     p.itemcap = 2 * nseg + n / 32 + 4096;
-    p.statuscap = (n / (2 * TILE) + 8192) * 256ull;
+    // look-back rows: 2 x chunks x k words per large (sub)array; the chunks of
+    // one level add up to ~4 per CTA plus at most 2 per (sub)array
+    const unsigned long long nctas = 2ull * (unsigned long long)(sms > 0 ? sms : 160);
+    p.statuscap = 2ull * NB_MAX * (std::min<unsigned long long>(8 * nctas, n / TILE + 64) + 2 * p.segcap);
     p.traincap = std::min<unsigned long long>(p.segcap, 32);
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -298,7 +301,10 @@ int get_workspace(cudaStream_t stream, unsigned long long n, unsigned long long 
         unsigned long long scap = std::max<unsigned long long>(nseg, ws->nseg_cap);
         ncap = std::max<unsigned long long>(ncap, 1);
         scap = std::max<unsigned long long>(scap, 1);
-        Plan p = make_plan(ncap, scap, large_min);
+        int sms = 0;
+        ce = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (ce != cudaSuccess) return cuda_err(ce);
+        Plan p = make_plan(ncap, scap, large_min, sms);
         if (ws->block) {
             ce = cudaStreamSynchronize(stream);  // the old block may still be in use
             if (ce != cudaSuccess) return cuda_err(ce);

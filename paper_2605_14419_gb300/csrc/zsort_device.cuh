@@ -519,16 +519,18 @@ __device__ uint32_t block_exclusive_scan(const uint32_t *in, uint32_t *out, uint
 }
 
 // ------------------------------------------------------------ tile ranking
-// Stable multisplit of one tile of N = BLOCK * NI elements.  Element (warp
-// w, slot i, lane l) is the tile's element w*32*NI + i*32 + l, so (w, i, l)
-// order is input order.  In each slot the warp's lanes with equal buckets are
-// found with __match_any_sync; their rank is the count of earlier equal lanes
-// plus the warp's running count for that bucket.  Warp prefixes per bucket
-// and a block scan over buckets then give each element its position in the
-// tile ordered by (bucket, input position).  Buckets INVALID are skipped.
+// Stable multisplit of one tile of N = BLOCK * NI elements, cnt of them
+// valid.  Element (warp w, slot i, lane l) is the tile's element
+// w*32*NI + i*32 + l, so (w, i, l) order is input order.  In each slot the
+// warp's lanes with equal buckets are found from NBITS ballots (one per bit
+// of the bucket id); their rank is the count of earlier equal lanes plus
+// the warp's running count for that bucket.  Warp prefixes per bucket and a
+// block scan over buckets then give each element its position in the tile
+// ordered by (bucket, input position).  Buckets must be below 2^NBITS;
+// lanes past cnt are ignored (their bucket value does not matter).
 // On return s.tcount / s.tstart hold the per-bucket counts and starts.
 template <int NI, int NBITS>
-__device__ void tile_rank_bits(const uint32_t (&b)[NI], uint32_t (&pos)[NI], uint32_t nb, SmemTile &s)
+__device__ void tile_rank(const uint32_t (&b)[NI], uint32_t (&pos)[NI], uint32_t nb, uint32_t cnt, SmemTile &s)
 {
     static_assert(WARPS == 8, "per-bucket warp counters are packed in 16 bytes");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -537,28 +539,38 @@ __device__ void tile_rank_bits(const uint32_t (&b)[NI], uint32_t (&pos)[NI], uin
     for (uint32_t q = threadIdx.x; q < nb; q += BLOCK) w4[q] = make_uint4(0u, 0u, 0u, 0u);
     __syncthreads();
     const uint32_t lt = (1u << lane) - 1u;
+    // phase 1 (registers only): lanes with an equal bucket, per slot: AND
+    // over the bucket's bits of the ballot of that bit (or of its complement)
+    uint32_t peers[NI];
 #pragma unroll
     for (int i = 0; i < NI; i++) {
-        // lanes with an equal bucket: AND over the bucket's bits of the ballot
-        // of that bit (or of its complement), then separate INVALID lanes
         const uint32_t bi = b[i];
-        uint32_t peers = __ballot_sync(0xffffffffu, bi == INVALID);
-        peers = bi == INVALID ? peers : ~peers;
+        uint32_t p = 0xffffffffu;
 #pragma unroll
         for (int bit = 0; bit < NBITS; bit++) {
             const uint32_t f = (bi >> bit) & 1u;
             const uint32_t bal = __ballot_sync(0xffffffffu, f);
-            peers &= f ? bal : ~bal;
+            p &= f ? bal : ~bal;
         }
-        const int leader = __ffs(peers) - 1;
+        // valid lanes of this slot, from the tile count
+        const int first = warp * 32 * NI + i * 32;
+        const int nv = (int)cnt - first;
+        const uint32_t vmask = nv >= 32 ? 0xffffffffu : (nv <= 0 ? 0u : (1u << nv) - 1u);
+        peers[i] = p & vmask;
+    }
+    // phase 2: the group leader reads and advances the warp's bucket counter
+#pragma unroll
+    for (int i = 0; i < NI; i++) {
+        const bool valid = (peers[i] >> lane) & 1u;
+        const int leader = valid ? __ffs(peers[i]) - 1 : lane;
         uint32_t before = 0;
-        if (lane == leader && bi != INVALID) {
-            uint16_t *c = s.wcnt + bi * WARPS + warp;
+        if (valid && lane == leader) {
+            uint16_t *c = s.wcnt + b[i] * WARPS + warp;
             before = *c;
-            *c = (uint16_t)(before + __popc(peers));
+            *c = (uint16_t)(before + __popc(peers[i]));
         }
         before = __shfl_sync(0xffffffffu, before, leader);
-        pos[i] = before + __popc(peers & lt);
+        pos[i] = valid ? before + __popc(peers[i] & lt) : INVALID;
     }
     __syncthreads();
     // exclusive prefix over the warps of each bucket, in registers
@@ -575,14 +587,15 @@ __device__ void tile_rank_bits(const uint32_t (&b)[NI], uint32_t (&pos)[NI], uin
     block_exclusive_scan(s.tcount, s.tstart, nb, s.wsum);
 #pragma unroll
     for (int i = 0; i < NI; i++)
-        if (b[i] != INVALID) pos[i] += s.tstart[b[i]] + s.wcnt[b[i] * WARPS + warp];
+        if (pos[i] != INVALID) pos[i] += s.tstart[b[i]] + s.wcnt[b[i] * WARPS + warp];
 }
 
-// Bucket ids below nb <= NB_MAX = 2^10: ten ballots identify equal buckets.
-template <int NI>
-__device__ __forceinline__ void tile_rank(const uint32_t (&b)[NI], uint32_t (&pos)[NI], uint32_t nb, SmemTile &s)
+// Bits of the ranking ballots for nb buckets (nb a power of two, 16..1024),
+// grouped so that few instantiations exist: 7 (<=128), 8, 9, 10.
+__device__ __forceinline__ int rank_bits(uint32_t nb)
 {
-    tile_rank_bits<NI, 10>(b, pos, nb, s);
+    const int e = 31 - __clz((int)nb);
+    return e < 7 ? 7 : e;
 }
 
 // ------------------------------------------------------------ bulk copies

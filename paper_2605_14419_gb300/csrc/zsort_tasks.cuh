@@ -142,14 +142,16 @@ __device__ __forceinline__ uint32_t choose_k(const Params &P, uint32_t len)
     return k > P.kmax ? P.kmax : k;
 }
 
-// Tiles per chunk task of a large (sub)array: about four chunks per CTA of
-// the whole grid, at least four tiles each.
-__device__ __forceinline__ uint32_t choose_chunk_tiles(const Params &P, uint32_t tiles)
+// Tiles per chunk task of a large (sub)array of len elements: chunks in
+// proportion to its share of the call's n, about four per CTA of the grid
+// over a whole level (so one level needs ~4 * nctas look-back rows in all),
+// at least four tiles each.
+__device__ __forceinline__ uint32_t choose_chunk_tiles(const Params &P, uint32_t tiles, uint32_t len)
 {
-    uint32_t per = 4 * P.nctas;
-    uint32_t ct = (tiles + per - 1) / per;
-    ct = ct < 4u ? 4u : ct;
-    return ct > 512u ? 512u : ct;
+    const unsigned long long want = ((unsigned long long)4 * P.nctas * len + P.n - 1) / P.n;
+    const uint32_t target = (uint32_t)(want < 1 ? 1 : want);
+    const uint32_t ct = (tiles + target - 1) / target;
+    return ct < 4u ? 4u : ct;
 }
 
 // Fills the map for a (sub)array from its exact sums: Eq. 1 (z-score) unless
@@ -380,6 +382,7 @@ __device__ __forceinline__ void body_hist(SmemTile &s, uint32_t cnt, const unsig
 // running cursor (coalesced within runs); cursors advance by the tile counts.
 // The output pass recomputes each staged key's bucket, except for the learned
 // map, whose buckets are staged.
+template <int NBITS>
 __device__ __forceinline__ void body_scatter(const Params &P, SmemTile &s, uint32_t cnt, unsigned long long *sk,
                                              uint32_t *sv, uint64_t *dstk, uint32_t *dstv, uint32_t seglen)
 {
@@ -393,9 +396,9 @@ __device__ __forceinline__ void body_scatter(const Params &P, SmemTile &s, uint3
         const bool ok = p < cnt;
         x[i] = ok ? sk[p] : 0ull;
         v[i] = ok ? sv[p] : 0u;
-        b[i] = ok ? map_key(s.map, x[i]) : INVALID;
+        b[i] = ok ? map_key(s.map, x[i]) : 0u;
     }
-    tile_rank<IPT>(b, pos, k, s);
+    tile_rank<IPT, NBITS>(b, pos, k, cnt, s);
     for (uint32_t q = threadIdx.x; q < k; q += BLOCK) {
         const uint32_t c = s.cursor[q];
         s.gdelta[q] = c - s.tstart[q];
@@ -403,7 +406,7 @@ __device__ __forceinline__ void body_scatter(const Params &P, SmemTile &s, uint3
     }
 #pragma unroll
     for (int i = 0; i < IPT; i++) {
-        if (b[i] != INVALID) {
+        if (pos[i] != INVALID) {
             sk[pos[i]] = x[i];
             sv[pos[i]] = v[i];
             if (stage_b) s.bkt[pos[i]] = (uint16_t)b[i];
@@ -420,6 +423,31 @@ __device__ __forceinline__ void body_scatter(const Params &P, SmemTile &s, uint3
         } else {
             set_error(P, ST_INTERNAL);
         }
+    }
+}
+
+// Streams [start, start+len) of a (sub)array through body_scatter with the
+// ballot width chosen for its bucket count.
+template <int NBITS>
+__device__ __noinline__ void scatter_stream(const Params &P, SmemTile &s, Pipe &pp, const uint64_t *srck,
+                                            const uint32_t *srcv, bool bulk, unsigned long long start,
+                                            unsigned long long len, uint64_t *dstk, uint32_t *dstv, uint32_t seglen)
+{
+    stream_tiles<true>(P, s, pp, srck, srcv, bulk, start, len,
+                       [&](uint32_t, uint32_t cnt, unsigned long long *sk, uint32_t *sv) {
+                           body_scatter<NBITS>(P, s, cnt, sk, sv, dstk, dstv, seglen);
+                       });
+}
+
+__device__ void scatter_dispatch(const Params &P, SmemTile &s, Pipe &pp, const uint64_t *srck, const uint32_t *srcv,
+                                 bool bulk, unsigned long long start, unsigned long long len, uint64_t *dstk,
+                                 uint32_t *dstv, uint32_t seglen, uint32_t k)
+{
+    switch (rank_bits(k)) {
+    case 7: scatter_stream<7>(P, s, pp, srck, srcv, bulk, start, len, dstk, dstv, seglen); break;
+    case 8: scatter_stream<8>(P, s, pp, srck, srcv, bulk, start, len, dstk, dstv, seglen); break;
+    case 9: scatter_stream<9>(P, s, pp, srck, srcv, bulk, start, len, dstk, dstv, seglen); break;
+    default: scatter_stream<10>(P, s, pp, srck, srcv, bulk, start, len, dstk, dstv, seglen); break;
     }
 }
 
@@ -473,7 +501,7 @@ __device__ __noinline__ void classify_children(const Params &P, unsigned long lo
             const uint32_t off_rel = L.lg_off[g];
             const uint32_t kk = choose_k(P, len);
             const uint32_t tiles = (len + TILE - 1) / TILE;
-            const uint32_t ct = choose_chunk_tiles(P, tiles);
+            const uint32_t ct = choose_chunk_tiles(P, tiles, len);
             const uint32_t chunks = (tiles + ct - 1) / ct;
             const unsigned long long need = 2ull * chunks * kk;
             const uint32_t sid = atomicAdd(&P.ctl->seg_alloc, 1u);
@@ -663,12 +691,12 @@ __device__ void cta_lsd_pass(const uint32_t *src, uint32_t *dst, uint32_t m, uin
         for (int i = 0; i < IPT; i++) {
             uint32_t p = slot_index(i);
             v[i] = p < cnt ? __ldcg(src + t0 + p) : 0u;
-            b[i] = p < cnt ? (v[i] >> shift) & 255u : INVALID;
+            b[i] = (v[i] >> shift) & 255u;
         }
-        tile_rank<IPT>(b, pos, 256, s);
+        tile_rank<IPT, 8>(b, pos, 256, cnt, s);
 #pragma unroll
         for (int i = 0; i < IPT; i++)
-            if (b[i] != INVALID) __stcg(dst + s.cursor[b[i]] + pos[i] - s.tstart[b[i]], v[i]);
+            if (pos[i] != INVALID) __stcg(dst + s.cursor[b[i]] + pos[i] - s.tstart[b[i]], v[i]);
         __syncthreads();
         for (int q = threadIdx.x; q < 256; q += BLOCK) s.cursor[q] += s.tcount[q];
         __syncthreads();
@@ -885,10 +913,8 @@ __device__ __noinline__ void task_lscatter(const Params &P, uint32_t sid, uint32
     __syncthreads();
     uint64_t *dstk = keys_of(P, ch.buf ^ 1u) + ch.off;
     uint32_t *dstv = vals_of(P, ch.buf ^ 1u) + ch.off;
-    stream_tiles<true>(P, s, pp, keys_of(P, ch.buf), vals_of(P, ch.buf), bulk_ok(P, ch.buf), ch.start, ch.len,
-                       [&](uint32_t, uint32_t cnt, unsigned long long *sk, uint32_t *sv) {
-                           body_scatter(P, s, cnt, sk, sv, dstk, dstv, ch.seglen);
-                       });
+    scatter_dispatch(P, s, pp, keys_of(P, ch.buf), vals_of(P, ch.buf), bulk_ok(P, ch.buf), ch.start, ch.len, dstk,
+                     dstv, ch.seglen, k);
     if (threadIdx.x == 0) atomicAdd(&P.ctl->bytes, 24ull * ch.len);
 }
 
@@ -962,10 +988,7 @@ __device__ __noinline__ void task_mpart(const Params &P, const Item it, SmemTile
     __syncthreads();
     uint64_t *dstk = keys_of(P, buf ^ 1u) + off;
     uint32_t *dstv = vals_of(P, buf ^ 1u) + off;
-    stream_tiles<true>(P, s, pp, srck, srcv, bulk, off, len,
-                       [&](uint32_t, uint32_t cnt, unsigned long long *sk, uint32_t *sv) {
-                           body_scatter(P, s, cnt, sk, sv, dstk, dstv, len);
-                       });
+    scatter_dispatch(P, s, pp, srck, srcv, bulk, off, len, dstk, dstv, len, k);
     if (threadIdx.x == 0) {
         atomicAdd(&P.ctl->n_small, 1ull);
         atomicAdd(&P.ctl->bytes, 40ull * len);
@@ -1135,12 +1158,12 @@ __device__ __noinline__ void finish_stable(const Params &P, SmemTile &s, unsigne
         const uint32_t p = leaf_slot(i);
         x[i] = p < len ? key[p] : 0ull;
         v[i] = p < len ? val[p] : 0u;
-        b[i] = p < len ? leaf_sub(x[i], mn, rshift, rmult) : INVALID;
+        b[i] = p < len ? leaf_sub(x[i], mn, rshift, rmult) : 0u;
     }
-    tile_rank<LEAF_IPT>(b, pos, M, s);
+    tile_rank<LEAF_IPT, 10>(b, pos, M, len, s);
 #pragma unroll
     for (int i = 0; i < LEAF_IPT; i++) {
-        if (b[i] != INVALID) {
+        if (pos[i] != INVALID) {
             key[pos[i]] = x[i];
             val[pos[i]] = v[i];
         }
