@@ -172,6 +172,31 @@ int zsort_sync_status(zsort_stream_t stream);
 /* Waits for `stream` and copies the counters of its last call to *out. */
 int zsort_last_stats(zsort_stream_t stream, zsort_stats *out);
 
+/* Top-level partition plan of one array (zsort_map_buckets). */
+typedef struct {
+    uint32_t map;               /* ZSORT_MAP_ZSCORE, ZSORT_MAP_LEARNED, or 2 = range map */
+    uint32_t k;                 /* buckets                                            */
+    uint64_t min, max;          /* exact min / max of the keys                        */
+    double mean_d, sd;          /* mean of key - min, population sd (exact sums)      */
+    float zc;                   /* Eq. 1 multiplier: bucket = min(k-1, trunc(fl32(u32((key - min) >> zsh)) * zc)) */
+    uint32_t zsh;
+    float escale;               /* learned map: u = fl32(key - min) * escale           */
+    uint32_t trained;           /* 1 if a learned map was trained (q, r valid)         */
+    float q[257];               /* learned map breakpoints                             */
+    float r[256];               /* learned map reciprocal piece widths                 */
+    uint32_t learned_max_load;  /* load test: largest learned bucket on the sample     */
+    uint32_t zscore_max_load;   /* load test: largest Eq. 1 bucket on the sample       */
+} zsort_map_info;
+
+/* Inspection: runs the statistics step and the bucket-map choice (Eq. 1 of
+ * section "Proposed Work", or the learned map with its load test) that
+ * zsort_pairs_ex would run at the top level of keys[0..n), and writes every
+ * key's top-level bucket to the device array buckets[0..n) instead of
+ * sorting.  keys are not modified.  Synchronous: waits for `stream` and fills
+ * *info.  2 <= n <= ZSORT_MAX_N. */
+int zsort_map_buckets(const uint64_t *keys, uint64_t n, const zsort_opts *opts, uint32_t *buckets,
+                      zsort_map_info *info, zsort_stream_t stream);
+
 /* Largest n accepted by zsort_pairs_noalloc. */
 #define ZSORT_NOALLOC_MAX_N ((uint64_t)1 << 20)
 

@@ -87,6 +87,9 @@ def _load():
         lib.oracle_pwl_train.restype = None
         lib.oracle_pwl_train.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
                                          ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p]
+        lib.oracle_pwl_buckets.restype = None
+        lib.oracle_pwl_buckets.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
+                                           ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p]
         lib.oracle_pwl_bucket.restype = ctypes.c_uint32
         lib.oracle_pwl_bucket.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
                                           ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32]
@@ -194,11 +197,12 @@ def pwl_train(sample_keys, mn: int, mx: int, P: int = P_PIECES):
 
 
 def pwl_buckets(keys, mn: int, mx: int, q, k: int, P: int = P_PIECES):
-    """Learned-map bucket of every key (slow: one C call per key)."""
+    """Learned-map bucket of every key."""
     qq = np.ascontiguousarray(q, dtype=np.float32)
-    f = _load().oracle_pwl_bucket
-    return np.array([f(int(x), mn, mx, _ptr(qq), P, k) for x in np.asarray(keys, dtype=np.uint64)],
-                    dtype=np.uint32)
+    kk = np.ascontiguousarray(keys, dtype=np.uint64)
+    out = np.empty(kk.size, dtype=np.uint32)
+    _load().oracle_pwl_buckets(_ptr(kk), kk.size, mn, mx, _ptr(qq), P, k, _ptr(out))
+    return out
 
 
 def learned_map(keys, seed: int, m: int, k: int, P: int = P_PIECES):

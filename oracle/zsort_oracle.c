@@ -496,3 +496,10 @@ void oracle_level1_buckets(const uint64_t *keys, uint64_t n, uint64_t k,
     for (uint64_t i = 0; i < n; i++)
         out[i] = zmap((double)(keys[i] - mn), mean, sd, zmin, scale, k);
 }
+
+/* The learned-map bucket of each of n keys (the same map as above). */
+void oracle_pwl_buckets(const uint64_t *keys, uint64_t n, uint64_t mn, uint64_t mx,
+                        const float *q, uint32_t P, uint32_t k, uint32_t *out)
+{
+    for (uint64_t i = 0; i < n; i++) out[i] = oracle_pwl_bucket(keys[i], mn, mx, q, P, k);
+}

@@ -95,6 +95,27 @@ class Stats(ctypes.Structure):
         return out
 
 
+class MapInfo(ctypes.Structure):
+    """``zsort_map_info``: the top-level partition plan of one array."""
+
+    _fields_ = [
+        ("map", ctypes.c_uint32),
+        ("k", ctypes.c_uint32),
+        ("min", ctypes.c_uint64),
+        ("max", ctypes.c_uint64),
+        ("mean_d", ctypes.c_double),
+        ("sd", ctypes.c_double),
+        ("zc", ctypes.c_float),
+        ("zsh", ctypes.c_uint32),
+        ("escale", ctypes.c_float),
+        ("trained", ctypes.c_uint32),
+        ("q", ctypes.c_float * 257),
+        ("r", ctypes.c_float * 256),
+        ("learned_max_load", ctypes.c_uint32),
+        ("zscore_max_load", ctypes.c_uint32),
+    ]
+
+
 def header_functions() -> list[str]:
     """Names of the functions declared in include/zsort.h."""
     with open(_HEADER) as f:
@@ -130,6 +151,7 @@ def load():
         "zsort_last_stats": (i32, [vp, ctypes.POINTER(Stats)]),
         "zsort_strerror": (ctypes.c_char_p, [i32]),
         "zsort_pairs_noalloc": (i32, [vp, vp, u64, vp, vp]),
+        "zsort_map_buckets": (i32, [vp, u64, ctypes.POINTER(Opts), vp, ctypes.POINTER(MapInfo), vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -209,6 +231,21 @@ def sort_segmented(keys, vals, offsets, opts: Opts | None = None, stream=None, c
     if check:
         _raise(lib.zsort_sync_status(st), "zsort_segmented (device)")
     return keys, vals
+
+
+def map_buckets(keys, opts: Opts | None = None, stream=None):
+    """Top-level bucket of every key (uint32 CUDA tensor) and the MapInfo."""
+    import torch
+
+    _check_tensor(keys, 8, "keys")
+    out = torch.empty(keys.numel(), dtype=torch.int32, device=keys.device)
+    info = MapInfo()
+    rc = load().zsort_map_buckets(ctypes.c_void_p(keys.data_ptr()), keys.numel(),
+                                  ctypes.byref(opts) if opts is not None else None,
+                                  ctypes.c_void_p(out.data_ptr()), ctypes.byref(info),
+                                  _stream_handle(stream))
+    _raise(rc, "zsort_map_buckets")
+    return out, info
 
 
 def reserve(n: int, nseg: int = 1, stream=None):

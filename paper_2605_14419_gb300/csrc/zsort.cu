@@ -60,6 +60,7 @@ __global__ void __launch_bounds__(BLOCK, 2) k_persistent(const __grid_constant__
             case T_MPART: task_mpart(P, load_item(P, arg + tile), s, pp); break;
             case T_FINISH: task_finish(P, load_item(P, arg + tile), s, pp); break;
             case T_COPY: task_copy(P, arg, tile); break;
+            case T_DUMP: task_dump(P, arg, tile, s, pp); break;
             default: set_error(P, ST_INTERNAL); break;
             }
             fence_proxy_async();  // order this task's smem writes before later bulk copies
@@ -119,12 +120,12 @@ __global__ void k_init_segments(Params P, const uint64_t *off, unsigned long lon
     it.len = (uint32_t)len;
     it.buf = 0;
     it.level = 0;
-    if (len <= (unsigned long long)LEAF_CAP) {
+    if (len <= (unsigned long long)LEAF_CAP && !P.plan_out) {
         uint32_t j = atomicAdd(&C->init_leaf, 1u);
         P.items[j] = it;
         return;
     }
-    if (len > P.large_min) {
+    if (len > P.large_min || P.plan_out) {
         const uint32_t kk = choose_k(P, (uint32_t)len);
         const uint32_t tiles = (uint32_t)((len + TILE - 1) / TILE);
         const uint32_t ct = choose_chunk_tiles(P, tiles, (uint32_t)len);
@@ -381,7 +382,7 @@ bool opts_valid(const zsort_opts &o)
 
 // Enqueues one sort (single array when off == nullptr).
 int launch(uint64_t *keys, uint32_t *vals, unsigned long long n, const uint64_t *off,
-           unsigned long long nseg, const zsort_opts &o, cudaStream_t stream)
+           unsigned long long nseg, const zsort_opts &o, cudaStream_t stream, uint32_t *plan_out = nullptr)
 {
     std::lock_guard<std::mutex> lock(g_mu);
     Workspace *ws = nullptr;
@@ -406,6 +407,7 @@ int launch(uint64_t *keys, uint32_t *vals, unsigned long long n, const uint64_t 
     P.user_aligned = ((reinterpret_cast<uintptr_t>(keys) | reinterpret_cast<uintptr_t>(vals)) & 15u) == 0;
     int per_sm = o.ctas_per_sm ? (int)std::min<uint32_t>(o.ctas_per_sm, (uint32_t)ws->occ) : ws->occ;
     P.nctas = (uint32_t)(ws->sms * per_sm);
+    P.plan_out = plan_out;
     cudaError_t ce = cudaMemsetAsync(P.ctl, 0, sizeof(Ctl), stream);
     if (ce != cudaSuccess) return cuda_err(ce);
     const unsigned int gi = (unsigned int)div_up(nseg, 256);
@@ -668,6 +670,60 @@ int zsort_last_stats(zsort_stream_t stream, zsort_stats *out)
     out->handler_ns = c.handler_ns;
     out->idle_ns = c.idle_ns;
     out->busy_window_ns = (c.t_last > c.t_first && c.t_first != ~0ull) ? c.t_last - c.t_first : 0;
+    return ZSORT_OK;
+}
+
+int zsort_map_buckets(const uint64_t *keys, uint64_t n, const zsort_opts *opts, uint32_t *buckets,
+                      zsort_map_info *info, zsort_stream_t stream)
+{
+    zsort_opts o;
+    if (opts)
+        o = *opts;
+    else
+        zsort_default_opts(&o);
+    if (!opts_valid(o)) return ZSORT_ERR_INVALID;
+    if (n < 2 || n > ZSORT_MAX_N || !keys || !buckets || !info) return ZSORT_ERR_INVALID;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    // the executor reads keys only in inspection mode; vals are never touched
+    int rc = launch(const_cast<uint64_t *>(keys), reinterpret_cast<uint32_t *>(buckets), n, nullptr, 1, o, st,
+                    buckets);
+    if (rc != ZSORT_OK) return rc;
+    cudaError_t ce = cudaStreamSynchronize(st);
+    if (ce != cudaSuccess) return cuda_err(ce);
+    std::lock_guard<std::mutex> lock(g_mu);
+    Workspace *ws = find_ws(st);
+    if (!ws) return ZSORT_ERR_INTERNAL;
+    unsigned int err = 0;
+    ce = cudaMemcpy(&err, &ws->P.ctl->error, sizeof(err), cudaMemcpyDeviceToHost);
+    if (ce != cudaSuccess) return cuda_err(ce);
+    if (err) {
+        unsigned int zero = 0;
+        cudaMemcpy(&ws->P.ctl->error, &zero, sizeof(zero), cudaMemcpyHostToDevice);
+        return (int)err;
+    }
+    Seg S;
+    ce = cudaMemcpy(&S, ws->P.segs, sizeof(Seg), cudaMemcpyDeviceToHost);
+    if (ce != cudaSuccess) return cuda_err(ce);
+    std::memset(info, 0, sizeof(*info));
+    info->map = S.kind == MAP_Z ? ZSORT_MAP_ZSCORE : (S.kind == MAP_PWL ? ZSORT_MAP_LEARNED : 2u);
+    info->k = S.k;
+    info->min = S.mn;
+    info->max = S.mx;
+    info->mean_d = S.mean_d;
+    info->sd = S.sd;
+    info->zc = S.zc;
+    info->zsh = S.zsh;
+    info->escale = S.escale;
+    info->learned_max_load = S.max_learned;
+    info->zscore_max_load = S.max_z;
+    if (S.train_slot != INVALID) {
+        float t[PWL_STRIDE];
+        ce = cudaMemcpy(t, ws->P.pwl, sizeof(t), cudaMemcpyDeviceToHost);
+        if (ce != cudaSuccess) return cuda_err(ce);
+        std::memcpy(info->q, t, sizeof(info->q));
+        std::memcpy(info->r, t + PWL_P + 1, sizeof(info->r));
+        info->trained = 1;
+    }
     return ZSORT_OK;
 }
 

@@ -49,7 +49,8 @@ enum TaskType : uint32_t {
     T_LSCATTER = 4,  // large segment: look-back stable scatter tile
     T_MPART = 5,     // medium segment: whole partition pass by one CTA
     T_FINISH = 6,    // leaf (group of small buckets): shared-memory sort
-    T_COPY = 7       // all-equal large segment living in scratch: copy back
+    T_COPY = 7,      // all-equal large segment living in scratch: copy back
+    T_DUMP = 8       // map inspection: bucket of every key of a chunk
 };
 
 // ---------------------------------------------------------------- records
@@ -68,6 +69,7 @@ struct Seg {
     uint32_t kind;               // MapKind
     uint32_t rshift, rmult;      // range map
     uint32_t train_slot;         // learned map training buffer, INVALID if none
+    uint32_t max_learned, max_z; // load test: largest sample bucket per map
     uint32_t chunk_tiles;        // tiles per chunk task
     uint32_t chunks;             // chunk tasks per phase
     uint32_t pad[3];
@@ -121,6 +123,7 @@ struct Params {
     uint32_t *status;            // look-back words and chunk offsets: 2 * chunks * k per segment
     unsigned long long statuscap;
     uint32_t nctas;              // CTAs of the persistent launch
+    uint32_t *plan_out;          // map inspection: bucket of every key (else null)
     uint32_t user_aligned;       // caller's keys and vals 16-byte aligned: bulk copies allowed
     float *pwl;         // segcap * PWL_STRIDE: breakpoints q[0..P], reciprocals r[0..P)
     uint32_t *trainbuf; // traincap * 2 * SAMPLE_MAX

@@ -631,7 +631,22 @@ __device__ __noinline__ void lstats_done(const Params &P, uint32_t sid, SmemTile
         const unsigned long long mn = __ldcg(&S->mn), mx = __ldcg(&S->mx);
         const uint32_t len = __ldcg(&S->len), level = __ldcg(&S->level);
         const uint32_t sbuf = __ldcg(&S->buf), sk = __ldcg(&S->k), chunks = __ldcg(&S->chunks);
-        if (mn == mx) {  // a set of identical keys is sorted (Alg. 1 early exit)
+        if (mn == mx && P.plan_out) {  // inspection of identical keys: all in bucket 0
+            S->kind = MAP_RANGE;
+            S->rshift = 0;
+            S->rmult = 0;
+            if (level == 0 && sid == 0) {
+                MapSm m0;
+                m0.k = sk;
+                m0.kind = MAP_RANGE;
+                record_top(P, m0, mn, mx, 0.0, 0.0);
+            }
+            uint32_t e = q_reserve(P, 1);
+            if (e != INVALID) {
+                q_write(P, e, T_DUMP, sid, chunks);
+                q_release_all(P, e, 1);
+            }
+        } else if (mn == mx) {  // a set of identical keys is sorted (Alg. 1 early exit)
             if (sbuf) {
                 uint32_t e = q_reserve(P, 1);
                 if (e != INVALID) {
@@ -655,7 +670,7 @@ __device__ __noinline__ void lstats_done(const Params &P, uint32_t sid, SmemTile
             S->rshift = m.rshift;
             S->rmult = m.rmult;
             if (level == 0 && sid == 0) record_top(P, m, mn, mx, mean_d, sd);
-            uint32_t next = T_LHIST, nt = chunks;
+            uint32_t next = P.plan_out ? T_DUMP : T_LHIST, nt = chunks;
             if (m.kind == MAP_Z && P.mapper == 1 && len >= P.learn_min && P.sample <= len &&
                 sk >= (uint32_t)PWL_P) {
                 uint32_t slot = atomicAdd(&P.ctl->train_alloc, 1u);
@@ -789,14 +804,31 @@ __device__ __noinline__ void task_ltrain(const Params &P, uint32_t sid, SmemTile
         }
         const bool ok = (float)ml <= P.fallback_ratio * (float)m / (float)k && ml <= mz;
         S->kind = ok ? MAP_PWL : MAP_Z;
+        S->max_learned = ml;
+        S->max_z = mz;
         atomicAdd(ok ? &P.ctl->n_learn_ok : &P.ctl->n_learn_rej, 1ull);
         if (__ldcg(&S->level) == 0 && sid == 0) P.ctl->top_map = ok ? MAP_PWL : MAP_Z;
         uint32_t e = q_reserve(P, 1);
         if (e != INVALID) {
-            q_write(P, e, T_LHIST, sid, chunks);
+            q_write(P, e, P.plan_out ? T_DUMP : T_LHIST, sid, chunks);
             q_release_all(P, e, 1);
         }
     }
+}
+
+// ------------------------------------------------------------ DUMP
+// Map inspection: the bucket the histogram and scatter would compute for
+// every key of one chunk (same map_key, same shared-memory map).
+__device__ __noinline__ void task_dump(const Params &P, uint32_t sid, uint32_t c, SmemTile &s, Pipe &pp)
+{
+    load_seg_map(P, sid, s);
+    const Chunk ch = chunk_of(P, sid, c);
+    uint32_t *out = P.plan_out;
+    stream_tiles<false>(P, s, pp, keys_of(P, ch.buf), nullptr, bulk_ok(P, ch.buf), ch.start, ch.len,
+                        [&](uint32_t t, uint32_t cnt, unsigned long long *sk, uint32_t *) {
+                            const unsigned long long a = ch.start + (unsigned long long)t * TILE;
+                            for (uint32_t p = threadIdx.x; p < cnt; p += BLOCK) __stcg(out + a + p, map_key(s.map, sk[p]));
+                        });
 }
 
 // ------------------------------------------------------------ LHIST

@@ -179,3 +179,66 @@ def test_full_size_2p28_properties(gen, mapper):
     _check_full_properties(k_in, k, v)
     del k_in, k, v
     torch.cuda.empty_cache()
+
+
+# ---------------------------------------------------------------- map rows
+def _map_case(gen, n, seed):
+    keys = gen(n, seed)
+    kd = torch.from_numpy(keys.view(np.int64)).to(DEV)
+    return keys, kd
+
+
+@pytest.mark.parametrize("gen", [inputs.lognormal, inputs.gaussian_mixture, inputs.uniform,
+                                 inputs.dense_interval_u64, inputs.zipf])
+def test_learned_map_buckets_bit_exact(gen):
+    """Learned map (training sample, breakpoints, buckets) against the oracle's
+    definition, bit for bit; the Eq. 1 fallback decision is checked from the
+    load-test numbers the device reports."""
+    n, m = 400_000, 65536
+    keys, kd = _map_case(gen, n, 13)
+    opts = z.default_opts(mapper=z.MAP_LEARNED, learn_min=m, sample=m, kmax=1024)
+    gb, info = z.map_buckets(kd, opts)
+    mn, mx = int(keys.min()), int(keys.max())
+    assert info.min == mn and info.max == mx
+    if mn == mx:
+        assert np.all(gb.cpu().numpy() == 0)
+        return
+    assert info.trained == 1
+    pos = oracle.sample_positions(opts.seed, n, m).astype(np.int64)
+    q = oracle.pwl_train(keys[pos], mn, mx)
+    assert np.array_equal(np.frombuffer(bytes(info.q), dtype=np.float32), q)
+    k = info.k
+    if info.map == z.MAP_LEARNED:
+        ob = oracle.pwl_buckets(keys, mn, mx, q, k)
+        assert np.array_equal(gb.cpu().numpy().view(np.uint32), ob)
+    else:  # rejected by the load test: its rule, from the reported loads
+        assert (info.learned_max_load > opts.fallback_ratio * m / k
+                or info.learned_max_load > info.zscore_max_load)
+
+
+@pytest.mark.parametrize("gen", [inputs.uniform, inputs.normal, inputs.lognormal, inputs.nearly_sorted])
+def test_zscore_map_and_stats(gen):
+    """Eq. 1 map on the device: exact statistics match the oracle's FP64
+    loops (relative 1e-12), the map is monotone, covers [min, min + 4 sd)
+    with k/4 buckets per sd, and every bucket equals the formula evaluated
+    from the reported constants."""
+    n = 500_000
+    keys, kd = _map_case(gen, n, 21)
+    gb, info = z.map_buckets(kd, z.default_opts())
+    mn, mx, mean_d, sd = oracle.stats(keys)
+    assert info.min == mn and info.max == mx
+    assert abs(info.mean_d - mean_d) <= 1e-12 * max(1.0, mean_d)
+    assert abs(info.sd - sd) <= 1e-12 * sd
+    assert info.map == z.MAP_ZSCORE
+    k = info.k
+    assert abs(info.zc / 2.0 ** info.zsh - (k / 4.0) / sd) <= 1e-6 * (k / 4.0) / sd
+    b = gb.cpu().numpy().view(np.uint32)
+    d = ((keys - np.uint64(mn)) >> np.uint64(info.zsh)).astype(np.float64)  # < 2^32: exact
+    f32 = d.astype(np.float32)  # round to nearest; the device converts toward zero
+    f32 = np.where(f32.astype(np.float64) > d, np.nextafter(f32, np.float32(0)), f32)
+    f = f32 * np.float32(info.zc)  # binary32 product, round to nearest
+    expect = np.minimum(np.floor(f.astype(np.float64)).astype(np.int64), k - 1)
+    assert np.array_equal(expect, b.astype(np.int64))
+    order = np.argsort(keys, kind="stable")
+    assert np.all(np.diff(b[order].astype(np.int64)) >= 0)  # monotone
+    assert b[order[0]] == 0 and b[order[-1]] >= 1
