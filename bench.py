@@ -115,6 +115,67 @@ def make_workload(n: int):
     return [("lognormal", inputs.lognormal(n, 30)), ("gmm8", inputs.gaussian_mixture(n, 31))]
 
 
+def batched_measure(z, torch, dev, nseg: int, seed: int, steps: int, warmup: int, plain_segments: int):
+    """zsort_segmented on a batch of nseg log-uniform (32..2^20) segments, one
+    persistent launch replayed from a CUDA graph; beside it the plain path,
+    one zsort_pairs call per segment on the same data (first plain_segments
+    segments, scaled to pairs/s)."""
+    keys, vals, off, _ = inputs.segmented(nseg, seed)
+    n = keys.size
+    kp = torch.from_numpy(keys.view(np.int64)).to(dev)
+    vp = torch.from_numpy(vals.view(np.int32)).to(dev)
+    od = torch.from_numpy(off.view(np.int64)).to(dev)
+    kb, vb = torch.empty_like(kp), torch.empty_like(vp)
+    stream = torch.cuda.Stream(device=dev)
+    opts = z.default_opts(flags=z.FLAG_GRAPH)
+    with torch.cuda.stream(stream):
+        z.reserve(n, nseg, stream)
+        times = []
+        for i in range(warmup + steps):
+            kb.copy_(kp)
+            vb.copy_(vp)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            z.sort_segmented(kb, vb, od, opts=opts, stream=stream, check=False)
+            e1.record(stream)
+            rc = z.sync_status(stream)
+            if rc != 0:
+                raise z.ZsortError(rc, "bench batched")
+            if i >= warmup:
+                times.append(e0.elapsed_time(e1))
+        st = z.last_stats(stream)
+        # output check: sorted inside every segment, payload = position in segment
+        seg_id = torch.repeat_interleave(torch.arange(nseg, device=dev),
+                                         (od[1:] - od[:-1]).to(torch.int64))
+        sk = kb ^ torch.tensor(-(2 ** 63), dtype=torch.int64, device=dev)
+        same = seg_id[1:] == seg_id[:-1]
+        assert bool((sk[1:][same] >= sk[:-1][same]).all()), "batched: not sorted"
+        src = od[:-1][seg_id] + (vb.to(torch.int64) & 0xFFFFFFFF)
+        assert bool(torch.equal(kp[src], kb)), "batched: payload does not follow its key"
+        # plain path: one zsort_pairs call per segment
+        m = min(plain_segments, nseg)
+        a, b = int(off[0]), int(off[m])
+        kb[a:b].copy_(kp[a:b])
+        vb[a:b].copy_(vp[a:b])
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(m):
+            s0, s1 = int(off[i]), int(off[i + 1])
+            if s1 - s0 > 1:
+                z.sort_pairs(kb[s0:s1], vb[s0:s1], stream=stream, check=False)
+        e1.record(stream)
+        stream.synchronize()
+        plain_ms = e0.elapsed_time(e1)
+    ms = sum(times) / len(times)
+    return {"segments": nseg, "pairs": n, "value": n / (ms / 1e3), "unit": UNIT, "ms": ms,
+            "graph": True, "bytes_per_pair": st["bytes_algorithmic"] / n,
+            "plain_per_segment_calls": {"segments": m, "pairs": b - a,
+                                        "value": (b - a) / (plain_ms / 1e3), "unit": UNIT}}
+
+
 def cpu_oracle_rate(n_sample: int, budget_s: float = 12.0):
     """Oracle pairs/s on bounded samples of the same two distributions."""
     import oracle
@@ -183,6 +244,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the z-score comparison run")
+    ap.add_argument("--workload", default="pairs", choices=["pairs", "batched"],
+                    help="pairs: 2 x 2^logn arrays; batched: segmented sort of --segments arrays")
+    ap.add_argument("--segments", type=int, default=20_000)
+    ap.add_argument("--batched-side", type=int, default=2000,
+                    help="segments of the batched measurement reported beside the pairs workload (0: none)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -208,6 +274,23 @@ def main():
     if world > 1:
         dist.barrier()
     z.load()
+
+    if args.workload == "batched":
+        res = batched_measure(z, torch, dev, args.segments, 5, args.steps, args.warmup, 2000)
+        if rank == 0:
+            line = {
+                "metric": METRIC, "value": world * res["value"], "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+                "data": "synthetic (seeded numpy PCG64)",
+                "config": {"workload": f"zsort_segmented, {args.segments} arrays, log-uniform sizes 32..2^20, "
+                                       "each from one of five families (uniform, normal, zipf, nearly sorted, "
+                                       "descending), one persistent launch from a CUDA graph",
+                           "pairs_per_step": res["pairs"], "l2": "inputs far larger than L2; restored between steps"},
+                "batched": res, "gpu_launches": 3 * args.steps,
+            }
+            print(json.dumps(line), flush=True)
+        return
 
     n = 1 << args.logn
     work = make_workload(n)
@@ -343,6 +426,12 @@ def main():
                "h2d_bytes_per_step": pairs_per_step * BYTES_PER_PAIR,
                "d2h_bytes_per_step": pairs_per_step * BYTES_PER_PAIR}
 
+    batched = None
+    if args.batched_side > 0:
+        del bufs
+        torch.cuda.empty_cache()
+        batched = batched_measure(z, torch, dev, args.batched_side, 5, 5, 3, min(args.batched_side, 2000))
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         rate, secs, reps = cpu_oracle_rate(args.sample)
@@ -378,6 +467,7 @@ def main():
                        "learned_accepted": last_stats[i]["learned_accepted"]}
                       for i, (name, _, _) in enumerate(pristine)],
         "plain_zscore": plain,
+        "batched": batched,
     }
     print(json.dumps(line), flush=True)
     if world > 1:

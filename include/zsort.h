@@ -58,9 +58,11 @@ enum {
     ZSORT_ERR_INTERNAL = -7     /* a device-side consistency check failed    */
 };
 
-/* Largest n accepted by every entry point (look-back status words carry
- * 30-bit counts). */
+/* Largest n accepted by zsort_pairs* (look-back status words carry 30-bit
+ * counts); zsort_segmented* accept arrays up to ZSORT_MAX_SEG_TOTAL with
+ * every segment at most ZSORT_MAX_N long. */
 #define ZSORT_MAX_N ((uint64_t)1 << 30)
+#define ZSORT_MAX_SEG_TOTAL ((uint64_t)1 << 34)
 
 /* Bucket maps. */
 enum {
@@ -94,8 +96,14 @@ typedef struct {
     uint32_t guard_level;    /* from this depth on, the exact range map is used */
     uint32_t ctas_per_sm;    /* persistent CTAs per SM, 0 = from occupancy     */
     uint32_t wait_limit_ms;  /* bound of every device-side wait (no progress)  */
-    uint32_t reserved;
+    uint32_t flags;          /* ZSORT_FLAG_*                                    */
 } zsort_opts;
+
+/* flags: capture the call's launch sequence (control-block reset, two set-up
+ * kernels, the persistent kernel) in a CUDA graph on first use and replay it
+ * with one cudaGraphLaunch while the workspace, pointers, sizes and options
+ * stay the same.  Needs a non-default stream (else ignored). */
+#define ZSORT_FLAG_GRAPH 1u
 
 /* Counters of the last completed call on a (device, stream) workspace. */
 typedef struct {
@@ -147,7 +155,8 @@ int zsort_pairs_ex(void *keys, uint32_t key_type, uint32_t *vals, uint64_t n,
 
 /* Batched sort: keys/vals hold n elements; segment i is
  * [seg_offsets[i], seg_offsets[i+1]) and is sorted on its own, stably.
- * seg_offsets is a device array of nseg + 1 non-decreasing values <= n;
+ * seg_offsets is a device array of nseg + 1 non-decreasing values <= n, and no
+ * segment may be longer than ZSORT_MAX_N;
  * empty segments are allowed and elements outside
  * [seg_offsets[0], seg_offsets[nseg]) are untouched.  The whole batch runs
  * as one persistent kernel over a device work queue.  A violation of the
@@ -159,7 +168,8 @@ int zsort_segmented_ex(uint64_t *keys, uint32_t *vals, uint64_t n, const uint64_
                        uint64_t nseg, const zsort_opts *opts, zsort_stream_t stream);
 
 /* Sizes the (device, stream) workspace for calls of up to n elements and
- * nseg segments, so that those calls allocate nothing. */
+ * nseg segments (n <= ZSORT_MAX_SEG_TOTAL), so that those calls allocate
+ * nothing. */
 int zsort_reserve(uint64_t n, uint64_t nseg, zsort_stream_t stream);
 
 /* Frees every workspace of the current device.  No call may be in flight. */

@@ -28,6 +28,8 @@ ERR_INVALID, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_BAD_OFFSETS, ERR_CAPACITY, ER
 MAP_ZSCORE, MAP_LEARNED = 0, 1
 KEY_TYPES = {"u64": 0, "i64": 1, "f64": 2}
 MAX_N = 1 << 30
+MAX_SEG_TOTAL = 1 << 34
+FLAG_GRAPH = 1
 NOALLOC_MAX_N = 1 << 20
 
 
@@ -53,7 +55,7 @@ class Opts(ctypes.Structure):
         ("guard_level", ctypes.c_uint32),
         ("ctas_per_sm", ctypes.c_uint32),
         ("wait_limit_ms", ctypes.c_uint32),
-        ("reserved", ctypes.c_uint32),
+        ("flags", ctypes.c_uint32),
     ]
 
 

@@ -114,6 +114,10 @@ __global__ void k_init_segments(Params P, const uint64_t *off, unsigned long lon
     }
     const unsigned long long len = b - a;
     if (len <= 1) return;
+    if (len > (1ull << 30)) {  // per-(sub)array counts are 30-bit
+        set_error(P, ST_BAD_OFFSETS);
+        return;
+    }
     Ctl *C = P.ctl;
     Item it;
     it.off = a;
@@ -169,6 +173,11 @@ __global__ void k_init_publish(Params P, unsigned long long nseg)
         C->pending = 0;
         return;
     }
+    // a fresh epoch for this call: ready words of earlier calls never match
+    uint32_t ep = *P.epoch_ctr + 1u;
+    if (ep == 0) ep = 1;
+    *P.epoch_ctr = ep;
+    C->epoch = ep;
     const uint32_t nl = C->init_leaf, nm = C->init_med;
     const uint32_t ns = min(C->seg_alloc, P.segcap);
     uint32_t e = 0;
@@ -187,7 +196,7 @@ __global__ void k_init_publish(Params P, unsigned long long nseg)
     C->q_alloc = e;
     C->pending = e;
     C->item_alloc = (uint32_t)(2 * nseg);
-    for (uint32_t i = 0; i < e; i++) P.ready[i] = P.epoch;
+    for (uint32_t i = 0; i < e; i++) P.ready[i] = ep;
 }
 
 // Order-preserving encodings to uint64 and back (in place).
@@ -210,7 +219,20 @@ __global__ void k_encode(uint64_t *keys, unsigned long long n, uint32_t type, in
 // ---------------------------------------------------------------- host side
 namespace {
 
+// A captured launch sequence and the arguments it was captured with.
+struct GraphCache {
+    bool valid = false;
+    uint64_t *keys = nullptr;
+    uint32_t *vals = nullptr;
+    const uint64_t *off = nullptr;
+    unsigned long long n = 0, nseg = 0;
+    uint32_t *plan = nullptr;
+    zsort_opts o{};
+    cudaGraphExec_t exec = nullptr;
+};
+
 struct Workspace {
+    GraphCache graph;
     int device = -1;
     cudaStream_t stream = nullptr;
     unsigned long long n_cap = 0, nseg_cap = 0;
@@ -235,7 +257,7 @@ size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 // Capacity plan for calls of up to n elements and nseg segments.
 struct Plan {
     unsigned long long qcap, segcap, itemcap, statuscap, traincap;
-    size_t off_skeys, off_svals, off_ctl, off_entries, off_ready, off_tnext, off_tdone, off_segs,
+    size_t off_skeys, off_svals, off_ctl, off_epoch, off_entries, off_ready, off_tnext, off_tdone, off_segs,
         off_items, off_counts, off_bstart, off_status, off_pwl, off_train, total;
 };
 
@@ -248,7 +270,8 @@ Plan make_plan(unsigned long long n, unsigned long long nseg, unsigned long long
     // look-back rows: 2 x chunks x k words per large (sub)array; the chunks of
     // one level add up to ~4 per CTA plus at most 2 per (sub)array
     const unsigned long long nctas = 2ull * (unsigned long long)(sms > 0 ? sms : 160);
-    p.statuscap = 2ull * NB_MAX * (std::min<unsigned long long>(8 * nctas, n / TILE + 64) + 2 * p.segcap);
+    p.statuscap = 2ull * NB_MAX *
+                  (std::min<unsigned long long>(8 * nctas, n / TILE + 64) + std::min<unsigned long long>(2 * p.segcap, 16384));
     p.traincap = std::min<unsigned long long>(p.segcap, 32);
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -259,6 +282,7 @@ Plan make_plan(unsigned long long n, unsigned long long nseg, unsigned long long
     p.off_skeys = take(n * 8);
     p.off_svals = take(n * 4);
     p.off_ctl = take(sizeof(Ctl));
+    p.off_epoch = take(16);
     p.off_entries = take(p.qcap * sizeof(Entry));
     p.off_ready = take(p.qcap * 4);
     p.off_tnext = take(p.qcap * 4);
@@ -312,6 +336,10 @@ int get_workspace(cudaStream_t stream, unsigned long long n, unsigned long long 
             cudaFree(ws->block);
             ws->block = nullptr;
         }
+        if (ws->graph.valid) {  // captured with the old block's addresses
+            cudaGraphExecDestroy(ws->graph.exec);
+            ws->graph = GraphCache{};
+        }
         void *blk = nullptr;
         ce = cudaMalloc(&blk, p.total);
         if (ce != cudaSuccess) {
@@ -331,6 +359,7 @@ int get_workspace(cudaStream_t stream, unsigned long long n, unsigned long long 
         P.skeys = reinterpret_cast<uint64_t *>(b + p.off_skeys);
         P.svals = reinterpret_cast<uint32_t *>(b + p.off_svals);
         P.ctl = reinterpret_cast<Ctl *>(b + p.off_ctl);
+        P.epoch_ctr = reinterpret_cast<uint32_t *>(b + p.off_epoch);
         P.entries = reinterpret_cast<Entry *>(b + p.off_entries);
         P.ready = reinterpret_cast<uint32_t *>(b + p.off_ready);
         P.tnext = reinterpret_cast<uint32_t *>(b + p.off_tnext);
@@ -392,8 +421,7 @@ int launch(uint64_t *keys, uint32_t *vals, unsigned long long n, const uint64_t 
     P.ukeys = keys;
     P.uvals = vals;
     P.n = n;
-    P.epoch = ++ws->epoch;
-    if (P.epoch == 0) P.epoch = ws->epoch = 1;
+
     P.kmax = o.kmax;
     P.leaf_target = o.leaf_target;
     P.large_min = o.large_min;
@@ -408,14 +436,46 @@ int launch(uint64_t *keys, uint32_t *vals, unsigned long long n, const uint64_t 
     int per_sm = o.ctas_per_sm ? (int)std::min<uint32_t>(o.ctas_per_sm, (uint32_t)ws->occ) : ws->occ;
     P.nctas = (uint32_t)(ws->sms * per_sm);
     P.plan_out = plan_out;
-    cudaError_t ce = cudaMemsetAsync(P.ctl, 0, sizeof(Ctl), stream);
-    if (ce != cudaSuccess) return cuda_err(ce);
-    const unsigned int gi = (unsigned int)div_up(nseg, 256);
-    k_init_segments<<<gi, 256, 0, stream>>>(P, off, nseg);
-    k_init_publish<<<1, 32, 0, stream>>>(P, nseg);
-    k_persistent<<<P.nctas, BLOCK, SMEM_BYTES, stream>>>(P);
-    ce = cudaGetLastError();
-    return cuda_err(ce);
+    auto enqueue = [&]() -> cudaError_t {
+        cudaError_t e = cudaMemsetAsync(P.ctl, 0, sizeof(Ctl), stream);
+        if (e != cudaSuccess) return e;
+        const unsigned int gi = (unsigned int)div_up(nseg, 256);
+        k_init_segments<<<gi, 256, 0, stream>>>(P, off, nseg);
+        k_init_publish<<<1, 32, 0, stream>>>(P, nseg);
+        k_persistent<<<P.nctas, BLOCK, SMEM_BYTES, stream>>>(P);
+        return cudaGetLastError();
+    };
+    if (!(o.flags & ZSORT_FLAG_GRAPH) || stream == nullptr) return cuda_err(enqueue());
+    GraphCache &g = ws->graph;
+    const bool hit = g.valid && g.keys == keys && g.vals == vals && g.off == off && g.n == n && g.nseg == nseg &&
+                     g.plan == plan_out && std::memcmp(&g.o, &o, sizeof(o)) == 0;
+    if (!hit) {
+        if (g.valid) cudaGraphExecDestroy(g.exec);
+        g = GraphCache{};
+        cudaGraph_t graph = nullptr;
+        cudaError_t ce = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal);
+        if (ce != cudaSuccess) return cuda_err(ce);
+        cudaError_t le = enqueue();
+        ce = cudaStreamEndCapture(stream, &graph);
+        if (le != cudaSuccess || ce != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return cuda_err(le != cudaSuccess ? le : ce);
+        }
+        cudaGraphExec_t exec = nullptr;
+        ce = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) return cuda_err(ce);
+        g.valid = true;
+        g.keys = keys;
+        g.vals = vals;
+        g.off = off;
+        g.n = n;
+        g.nseg = nseg;
+        g.plan = plan_out;
+        g.o = o;
+        g.exec = exec;
+    }
+    return cuda_err(cudaGraphLaunch(g.exec, stream));
 }
 
 int encode(void *keys, unsigned long long n, uint32_t type, int inverse, cudaStream_t stream)
@@ -454,7 +514,7 @@ constexpr size_t na_align(size_t x) { return (x + 255) & ~size_t(255); }
 // NA_MAX_N elements and one segment, with one learned-map training slot.
 struct NaLayout {
     unsigned long long qcap, segcap, itemcap, statuscap, traincap;
-    size_t skeys, svals, ctl, entries, ready, tnext, tdone, segs, items, counts, bstart, status, pwl,
+    size_t skeys, svals, ctl, epoch, entries, ready, tnext, tdone, segs, items, counts, bstart, status, pwl,
         train, total;
 };
 constexpr NaLayout na_layout()
@@ -469,6 +529,7 @@ constexpr NaLayout na_layout()
     L.skeys = o; o = na_align(o + NA_MAX_N * 8);
     L.svals = o; o = na_align(o + NA_MAX_N * 4);
     L.ctl = o; o = na_align(o + sizeof(Ctl));
+    L.epoch = o; o = na_align(o + 16);
     L.entries = o; o = na_align(o + L.qcap * sizeof(Entry));
     L.ready = o; o = na_align(o + L.qcap * 4);
     L.tnext = o; o = na_align(o + L.qcap * 4);
@@ -571,7 +632,7 @@ int zsort_segmented_ex(uint64_t *keys, uint32_t *vals, uint64_t n, const uint64_
     else
         zsort_default_opts(&o);
     if (!opts_valid(o)) return ZSORT_ERR_INVALID;
-    if (n > ZSORT_MAX_N || nseg > (1ull << 31)) return ZSORT_ERR_INVALID;
+    if (n > ZSORT_MAX_SEG_TOTAL || nseg > (1ull << 31)) return ZSORT_ERR_INVALID;
     if (nseg == 0) return ZSORT_OK;
     if (!seg_offsets || (n > 0 && (!keys || !vals))) return ZSORT_ERR_INVALID;
     return launch(keys, vals, n, seg_offsets, nseg, o, reinterpret_cast<cudaStream_t>(stream));
@@ -585,7 +646,7 @@ int zsort_segmented(uint64_t *keys, uint32_t *vals, uint64_t n, const uint64_t *
 
 int zsort_reserve(uint64_t n, uint64_t nseg, zsort_stream_t stream)
 {
-    if (n > ZSORT_MAX_N) return ZSORT_ERR_INVALID;
+    if (n > ZSORT_MAX_SEG_TOTAL) return ZSORT_ERR_INVALID;
     zsort_opts o;
     zsort_default_opts(&o);
     std::lock_guard<std::mutex> lock(g_mu);
@@ -606,6 +667,7 @@ int zsort_release(void)
             keep.push_back(w);
             continue;
         }
+        if (w->graph.valid) cudaGraphExecDestroy(w->graph.exec);
         if (w->block && cudaFree(w->block) != cudaSuccess) rc = ZSORT_ERR_CUDA;
         delete w;
     }
@@ -773,6 +835,7 @@ int zsort_pairs_noalloc(uint64_t *keys, uint32_t *vals, uint64_t n, int32_t *sta
     P.skeys = reinterpret_cast<uint64_t *>(b + NA.skeys);
     P.svals = reinterpret_cast<uint32_t *>(b + NA.svals);
     P.ctl = reinterpret_cast<Ctl *>(b + NA.ctl);
+    P.epoch_ctr = reinterpret_cast<uint32_t *>(b + NA.epoch);
     P.entries = reinterpret_cast<Entry *>(b + NA.entries);
     P.ready = reinterpret_cast<uint32_t *>(b + NA.ready);
     P.tnext = reinterpret_cast<uint32_t *>(b + NA.tnext);
@@ -789,9 +852,6 @@ int zsort_pairs_noalloc(uint64_t *keys, uint32_t *vals, uint64_t n, int32_t *sta
     P.pwl = reinterpret_cast<float *>(b + NA.pwl);
     P.trainbuf = reinterpret_cast<uint32_t *>(b + NA.train);
     P.traincap = (uint32_t)NA.traincap;
-    // ready flags from earlier calls hold older epochs; the array starts at 0
-    if (++D.epoch == 0) D.epoch = 1;
-    P.epoch = D.epoch;
     P.kmax = o.kmax;
     P.leaf_target = o.leaf_target;
     P.large_min = o.large_min;

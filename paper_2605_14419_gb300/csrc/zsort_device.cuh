@@ -99,6 +99,7 @@ struct Ctl {
     double top_mean_d, top_sd;
     unsigned long long top_min, top_max;
     unsigned int top_k, top_map;
+    unsigned int epoch, pad3;      // this call's queue epoch (from the persistent counter)
     // device time per task type (ns, summed over CTAs), handler and idle time
     unsigned long long task_ns[8], task_cnt[8], handler_ns, idle_ns;
     unsigned long long t_first, t_last;
@@ -113,7 +114,8 @@ struct Params {
     Ctl *ctl;
     Entry *entries;
     uint32_t *ready, *tnext, *tdone;
-    uint32_t qcap, epoch;
+    uint32_t qcap, epoch_unused;
+    uint32_t *epoch_ctr;         // persistent call counter (not cleared between calls)
     Seg *segs;
     uint32_t segcap;
     Item *items;

@@ -45,11 +45,18 @@ __device__ void q_write(const Params &P, uint32_t e, uint32_t type, uint32_t arg
     P.tdone[e] = 0;
 }
 
+// This call's queue epoch: ready words equal to it mark published entries.
+__device__ __forceinline__ uint32_t call_epoch(const Params &P)
+{
+    return __ldcg(&P.ctl->epoch);
+}
+
 // Publishes entries [e, e+count): one fence, then the ready flags.
 __device__ void q_release_all(const Params &P, uint32_t e, uint32_t count)
 {
     __threadfence();
-    for (uint32_t i = 0; i < count; i++) st_relaxed(&P.ready[e + i], P.epoch);
+    const uint32_t ep = call_epoch(P);
+    for (uint32_t i = 0; i < count; i++) st_relaxed(&P.ready[e + i], ep);
 }
 
 // Thread 0's cached copy of the entry at the queue head.
@@ -66,12 +73,13 @@ __device__ void dequeue(const Params &P, uint32_t *out, QCache &qc)
     Ctl *C = P.ctl;
     unsigned long long last = ld_relaxed64(&C->progress);
     unsigned long long t0 = globaltimer();
+    const uint32_t ep = call_epoch(P);
     out[0] = T_NONE;
     for (;;) {
         if (ld_relaxed(&C->error)) return;
         uint32_t e = ld_relaxed(&C->q_head);
         if (e != qc.e) {
-            if (e < P.qcap && ld_acquire(&P.ready[e]) == P.epoch) {
+            if (e < P.qcap && ld_acquire(&P.ready[e]) == ep) {
                 uint4 en = __ldcg(reinterpret_cast<const uint4 *>(P.entries + e));
                 qc.e = e;
                 qc.type = en.x;

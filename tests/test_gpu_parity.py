@@ -242,3 +242,40 @@ def test_zscore_map_and_stats(gen):
     order = np.argsort(keys, kind="stable")
     assert np.all(np.diff(b[order].astype(np.int64)) >= 0)  # monotone
     assert b[order[0]] == 0 and b[order[-1]] >= 1
+
+
+# ---------------------------------------------------------------- graphs
+def test_segmented_graph_capture_and_replays():
+    """ZSORT_FLAG_GRAPH: the first call captures the launch sequence, the next
+    ones replay it; every replay sorts fresh data exactly."""
+    keys, vals, off, _ = inputs.segmented(250, 12, lo=1, hi=150_000)
+    kp, vp = to_dev(keys, vals)
+    offs = torch.from_numpy(off.view(np.int64)).to(DEV)
+    ok, ov = oracle.zsort_segmented(keys, vals, off)
+    stream = torch.cuda.Stream()
+    opts = z.default_opts(flags=z.FLAG_GRAPH)
+    kb, vb = torch.empty_like(kp), torch.empty_like(vp)
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            kb.copy_(kp)
+            vb.copy_(vp)
+            z.sort_segmented(kb, vb, offs, opts=opts, stream=stream)
+            assert np.array_equal(kb.cpu().numpy().view(np.uint64), ok)
+            assert np.array_equal(vb.cpu().numpy().view(np.uint32), ov)
+
+
+def test_pairs_graph_replays_with_learned_map():
+    keys = inputs.gaussian_mixture(1_500_000, 14)
+    vals = inputs.index_payload(keys.size)
+    kp, vp = to_dev(keys, vals)
+    ok, ov = oracle.zsort_pairs(keys, vals)
+    stream = torch.cuda.Stream()
+    opts = z.default_opts(flags=z.FLAG_GRAPH, mapper=z.MAP_LEARNED, learn_min=65536, sample=65536)
+    kb, vb = torch.empty_like(kp), torch.empty_like(vp)
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            kb.copy_(kp)
+            vb.copy_(vp)
+            z.sort_pairs(kb, vb, opts=opts, stream=stream)
+            assert np.array_equal(kb.cpu().numpy().view(np.uint64), ok)
+            assert np.array_equal(vb.cpu().numpy().view(np.uint32), ov)
