@@ -58,7 +58,10 @@ __global__ void __launch_bounds__(BLOCK, 2) k_persistent(const __grid_constant__
             case T_LHIST: task_lhist(P, arg, tile, s, pp); break;
             case T_LSCATTER: task_lscatter(P, arg, tile, s, pp); break;
             case T_MPART: task_mpart(P, load_item(P, arg + tile), s, pp); break;
-            case T_FINISH: task_finish(P, load_item(P, arg + tile), s, pp); break;
+            case T_FINISH:
+                if (threadIdx.x == 0 && j + 1 < count) prefetch_item_l2(P, load_item(P, arg + tile + 1));
+                task_finish(P, load_item(P, arg + tile), s, pp);
+                break;
             case T_COPY: task_copy(P, arg, tile); break;
             case T_DUMP: task_dump(P, arg, tile, s, pp); break;
             default: set_error(P, ST_INTERNAL); break;
@@ -268,10 +271,10 @@ Plan make_plan(unsigned long long n, unsigned long long nseg, unsigned long long
     p.segcap = 3 * (n / (large_min + 1)) + 64;
     p.itemcap = 2 * nseg + n / 32 + 4096;
     // look-back rows: 2 x chunks x k words per large (sub)array; the chunks of
-    // one level add up to ~4 per CTA plus at most 2 per (sub)array
+    // one level add up to ~8 per CTA plus at most 2 per (sub)array
     const unsigned long long nctas = 2ull * (unsigned long long)(sms > 0 ? sms : 160);
     p.statuscap = 2ull * NB_MAX *
-                  (std::min<unsigned long long>(8 * nctas, n / TILE + 64) + std::min<unsigned long long>(2 * p.segcap, 16384));
+                  (std::min<unsigned long long>(16 * nctas, n / TILE + 64) + std::min<unsigned long long>(2 * p.segcap, 16384));
     p.traincap = std::min<unsigned long long>(p.segcap, 32);
     size_t o = 0;
     auto take = [&](size_t bytes) {

@@ -392,21 +392,48 @@ __device__ __forceinline__ uint32_t pwl_bucket_u(const MapSm &m, float u)
     return lo * m.K + w;
 }
 
-__device__ __forceinline__ uint32_t map_key(const MapSm &m, unsigned long long key)
+// The scalar part of a map, held in registers by the tile loops (the tables
+// of the learned map stay in shared memory).
+struct MapK {
+    unsigned long long mn;
+    uint32_t kind, k, rshift, rmult, zsh;
+    float zc, escale;
+};
+
+__device__ __forceinline__ MapK map_regs(const MapSm &m)
 {
-    const unsigned long long d = key - m.mn;
-    if (m.kind == MAP_Z) {
+    MapK r;
+    r.mn = m.mn;
+    r.kind = m.kind;
+    r.k = m.k;
+    r.rshift = m.rshift;
+    r.rmult = m.rmult;
+    r.zsh = m.zsh;
+    r.zc = m.zc;
+    r.escale = m.escale;
+    return r;
+}
+
+__device__ __forceinline__ uint32_t map_key(const MapK &r, const MapSm &m, unsigned long long key)
+{
+    const unsigned long long d = key - r.mn;
+    if (r.kind == MAP_Z) {
         // Eq. 1 with |z_min| = (mean - min)/sd: h = (key - min) * (k/4) / sd,
         // on d >> zsh (a 32-bit value; zc carries the 2^zsh back).
-        const float f = __fmul_rn(__uint2float_rz((uint32_t)(d >> m.zsh)), m.zc);
+        const float f = __fmul_rn(__uint2float_rz((uint32_t)(d >> r.zsh)), r.zc);
         const uint32_t b = __float2uint_rz(f);
-        return b < m.k ? b : m.k - 1;
+        return b < r.k ? b : r.k - 1;
     }
-    if (m.kind == MAP_RANGE) {
-        if (m.rmult == 0) return (uint32_t)d;  // range < k: counting map
-        return __umulhi((uint32_t)(d >> m.rshift), m.rmult);
+    if (r.kind == MAP_RANGE) {
+        if (r.rmult == 0) return (uint32_t)d;  // range < k: counting map
+        return __umulhi((uint32_t)(d >> r.rshift), r.rmult);
     }
-    return pwl_bucket_u(m, __fmul_rn(u64_to_f32_rn(d), m.escale));
+    return pwl_bucket_u(m, __fmul_rn(u64_to_f32_rn(d), r.escale));
+}
+
+__device__ __forceinline__ uint32_t map_key(const MapSm &m, unsigned long long key)
+{
+    return map_key(map_regs(m), m, key);
 }
 
 // Range map parameters: floor-like (d >> shift) * mult / 2^32, monotone,
@@ -431,7 +458,7 @@ __device__ __forceinline__ void range_params(unsigned long long range, uint32_t 
 struct ChildList {
     uint32_t leaf_off[NB_MAX], leaf_len[NB_MAX];
     uint32_t med_off[NB_MAX], med_len[NB_MAX];
-    uint32_t lg_off[NB_MAX], lg_len[NB_MAX], lg_sid[NB_MAX];
+    uint32_t lg_off[NB_MAX], lg_len[NB_MAX], lg_need[NB_MAX];
 };
 
 struct TileBuf {
@@ -466,9 +493,6 @@ struct SmemTile {
     unsigned long long red64[WARPS * 2];
 };
 static_assert(sizeof(LeafBuf) <= sizeof(TileBuf) * 2, "leaf fits the tile buffers");
-// The leaf finish keeps LEAF_CAP u16 ranks in hist + cursor (adjacent).
-static_assert(offsetof(SmemTile, cursor) == offsetof(SmemTile, hist) + 4 * NB_MAX, "hist, cursor adjacent");
-static_assert(8 * NB_MAX >= 2 * LEAF_CAP, "rank array fits hist + cursor");
 
 // ------------------------------------------------------------ block scan
 // Exclusive scan of in[0..nb) into out (may alias); returns the total.
@@ -498,19 +522,14 @@ __device__ uint32_t block_exclusive_scan(const uint32_t *in, uint32_t *out, uint
     }
     if (lane == 31) wsum[warp] = x;
     __syncthreads();
-    if (warp == 0) {
-        uint32_t w = lane < WARPS ? wsum[lane] : 0u;
-        uint32_t incl = w;
+    uint32_t wofs = 0, total = 0;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        if (lane < WARPS) wsum[lane] = incl - w;
-        if (lane == WARPS - 1) wsum[WARPS] = incl;  // the total
+    for (int w = 0; w < WARPS; w++) {
+        const uint32_t ws = wsum[w];
+        wofs += w < warp ? ws : 0u;
+        total += ws;
     }
-    __syncthreads();
-    uint32_t excl = wsum[warp] + x - sum;
+    const uint32_t excl = wofs + x - sum;
 #pragma unroll
     for (uint32_t j = 0; j < (uint32_t)MAXPER; j++) {
         if (j < per) {
@@ -518,7 +537,6 @@ __device__ uint32_t block_exclusive_scan(const uint32_t *in, uint32_t *out, uint
             if (idx < nb) out[idx] = excl + loc[j];
         }
     }
-    uint32_t total = wsum[WARPS];
     __syncthreads();
     return total;
 }
@@ -534,19 +552,21 @@ __device__ uint32_t block_exclusive_scan(const uint32_t *in, uint32_t *out, uint
 // ordered by (bucket, input position).  Buckets must be below 2^NBITS;
 // lanes past cnt are ignored (their bucket value does not matter).
 // On return s.tcount / s.tstart hold the per-bucket counts and starts.
+// The ranking in steps, so that a tile loop can place its own barriers:
+//   rank_peers    (registers)  lanes of the warp with an equal bucket, per slot
+//   rank_leaders  (smem)       the group leader reads and advances the warp's
+//                              counter of the bucket; wcnt must start at zero
+//   -- barrier --
+//   rank_scan                  per bucket: exclusive prefix over the warps
+//                              (written back into wcnt), tile count, and the
+//                              tile start by a block scan over the buckets;
+//                              ends with a barrier
+//   rank_place                 position = tile start + warp prefix + rank
+// Bucket q's counters and prefixes belong to thread q / per (contiguous).
 template <int NI, int NBITS>
-__device__ void tile_rank(const uint32_t (&b)[NI], uint32_t (&pos)[NI], uint32_t nb, uint32_t cnt, SmemTile &s)
+__device__ __forceinline__ void rank_peers(const uint32_t (&b)[NI], uint32_t cnt, uint32_t (&peers)[NI])
 {
-    static_assert(WARPS == 8, "per-bucket warp counters are packed in 16 bytes");
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // per-bucket counters of the 8 warps, [bucket][warp] u16: 16 bytes a bucket
-    uint4 *w4 = reinterpret_cast<uint4 *>(s.wcnt);
-    for (uint32_t q = threadIdx.x; q < nb; q += BLOCK) w4[q] = make_uint4(0u, 0u, 0u, 0u);
-    __syncthreads();
-    const uint32_t lt = (1u << lane) - 1u;
-    // phase 1 (registers only): lanes with an equal bucket, per slot: AND
-    // over the bucket's bits of the ballot of that bit (or of its complement)
-    uint32_t peers[NI];
+    const int warp = threadIdx.x >> 5;
 #pragma unroll
     for (int i = 0; i < NI; i++) {
         const uint32_t bi = b[i];
@@ -563,7 +583,14 @@ __device__ void tile_rank(const uint32_t (&b)[NI], uint32_t (&pos)[NI], uint32_t
         const uint32_t vmask = nv >= 32 ? 0xffffffffu : (nv <= 0 ? 0u : (1u << nv) - 1u);
         peers[i] = p & vmask;
     }
-    // phase 2: the group leader reads and advances the warp's bucket counter
+}
+
+template <int NI>
+__device__ __forceinline__ void rank_leaders(const uint32_t (&b)[NI], const uint32_t (&peers)[NI],
+                                             uint32_t (&pos)[NI], SmemTile &s)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
 #pragma unroll
     for (int i = 0; i < NI; i++) {
         const bool valid = (peers[i] >> lane) & 1u;
@@ -577,22 +604,97 @@ __device__ void tile_rank(const uint32_t (&b)[NI], uint32_t (&pos)[NI], uint32_t
         before = __shfl_sync(0xffffffffu, before, leader);
         pos[i] = valid ? before + __popc(peers[i] & lt) : INVALID;
     }
+}
+
+// SCATTER: also advance the running cursors (gdelta = cursor - tile start,
+// cursor += count); else store the counts in s.tcount.
+template <bool SCATTER>
+__device__ __forceinline__ void rank_scan(uint32_t nb, SmemTile &s)
+{
+    static_assert(WARPS == 8, "per-bucket warp counters are packed in 16 bytes");
+    constexpr int MAXPER = NB_MAX / BLOCK;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint4 *w4 = reinterpret_cast<uint4 *>(s.wcnt);
+    const uint32_t per = nb >= (uint32_t)BLOCK ? nb / BLOCK : 1u;
+    const uint32_t q0 = threadIdx.x * per;
+    uint32_t tot[MAXPER], loc[MAXPER];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int j = 0; j < MAXPER; j++) {
+        tot[j] = 0;
+        loc[j] = sum;
+        if ((uint32_t)j < per && q0 + j < nb) {
+            const uint4 c = w4[q0 + j];
+            const uint32_t c0 = c.x & 0xffffu, c1 = c.x >> 16, c2 = c.y & 0xffffu, c3 = c.y >> 16;
+            const uint32_t c4 = c.z & 0xffffu, c5 = c.z >> 16, c6 = c.w & 0xffffu, c7 = c.w >> 16;
+            const uint32_t p1 = c0, p2 = p1 + c1, p3 = p2 + c2, p4 = p3 + c3, p5 = p4 + c4, p6 = p5 + c5,
+                           p7 = p6 + c6;
+            w4[q0 + j] = make_uint4(p1 << 16, p2 | (p3 << 16), p4 | (p5 << 16), p6 | (p7 << 16));
+            tot[j] = p7 + c7;
+            sum += tot[j];
+        }
+    }
+    uint32_t x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s.wsum[warp] = x;
     __syncthreads();
-    // exclusive prefix over the warps of each bucket, in registers
-    for (uint32_t q = threadIdx.x; q < nb; q += BLOCK) {
-        const uint4 c = w4[q];
-        const uint32_t c0 = c.x & 0xffffu, c1 = c.x >> 16, c2 = c.y & 0xffffu, c3 = c.y >> 16;
-        const uint32_t c4 = c.z & 0xffffu, c5 = c.z >> 16, c6 = c.w & 0xffffu, c7 = c.w >> 16;
-        const uint32_t p1 = c0, p2 = p1 + c1, p3 = p2 + c2, p4 = p3 + c3, p5 = p4 + c4, p6 = p5 + c5,
-                       p7 = p6 + c6;
-        w4[q] = make_uint4(p1 << 16, p2 | (p3 << 16), p4 | (p5 << 16), p6 | (p7 << 16));
-        s.tcount[q] = p7 + c7;
+    uint32_t wofs = 0;
+#pragma unroll
+    for (int w = 0; w < WARPS; w++) wofs += w < warp ? s.wsum[w] : 0u;
+    const uint32_t excl = wofs + x - sum;
+#pragma unroll
+    for (int j = 0; j < MAXPER; j++) {
+        if ((uint32_t)j < per && q0 + j < nb) {
+            const uint32_t q = q0 + j, st = excl + loc[j];
+            s.tstart[q] = st;
+            if (SCATTER) {
+                const uint32_t c = s.cursor[q];
+                s.gdelta[q] = c - st;
+                s.cursor[q] = c + tot[j];
+            } else {
+                s.tcount[q] = tot[j];
+            }
+        }
     }
     __syncthreads();
-    block_exclusive_scan(s.tcount, s.tstart, nb, s.wsum);
+}
+
+template <int NI>
+__device__ __forceinline__ void rank_place(const uint32_t (&b)[NI], uint32_t (&pos)[NI], SmemTile &s)
+{
+    const int warp = threadIdx.x >> 5;
 #pragma unroll
     for (int i = 0; i < NI; i++)
         if (pos[i] != INVALID) pos[i] += s.tstart[b[i]] + s.wcnt[b[i] * WARPS + warp];
+}
+
+// Zeroes this warp's counter of every bucket (its own column of wcnt).
+__device__ __forceinline__ void rank_zero_warp(uint32_t nb, SmemTile &s)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncwarp();
+    for (uint32_t q = lane; q < nb; q += 32) s.wcnt[q * WARPS + warp] = 0;
+    __syncwarp();
+}
+
+// Stable multisplit of one tile in one call (its own barriers).  On return
+// s.tcount / s.tstart hold the per-bucket counts and starts.
+template <int NI, int NBITS>
+__device__ void tile_rank(const uint32_t (&b)[NI], uint32_t (&pos)[NI], uint32_t nb, uint32_t cnt, SmemTile &s)
+{
+    uint4 *w4 = reinterpret_cast<uint4 *>(s.wcnt);
+    for (uint32_t q = threadIdx.x; q < nb; q += BLOCK) w4[q] = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
+    uint32_t peers[NI];
+    rank_peers<NI, NBITS>(b, cnt, peers);
+    rank_leaders<NI>(b, peers, pos, s);
+    __syncthreads();
+    rank_scan<false>(nb, s);
+    rank_place<NI>(b, pos, s);
 }
 
 // Bits of the ranking ballots for nb buckets (nb a power of two, 16..1024),
@@ -631,6 +733,11 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
             smem_u32(dst)),
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
+}
+// Hint: bring [src, src + bytes) into L2 (16-byte aligned address and size).
+__device__ __forceinline__ void bulk_prefetch_l2(const void *src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 // Waits for the given phase parity of an mbarrier; false after limit_ns.
 __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity, unsigned long long limit_ns)

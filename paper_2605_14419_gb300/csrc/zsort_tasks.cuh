@@ -99,7 +99,9 @@ __device__ void dequeue(const Params &P, uint32_t *out, QCache &qc)
                 continue;
             }
         }
-        const uint32_t claim = qc.type == T_FINISH ? 2u : 1u;
+        // leaves are claimed a few at a time, so that each can be prefetched
+        // while its predecessor is sorted
+        const uint32_t claim = qc.type != T_FINISH ? 1u : (qc.ntiles >= 64u ? 4u : (qc.ntiles >= 16u ? 2u : 1u));
         uint32_t t = atomicAdd(&P.tnext[e], claim);
         if (t < qc.ntiles) {
             out[0] = qc.type;
@@ -151,12 +153,12 @@ __device__ __forceinline__ uint32_t choose_k(const Params &P, uint32_t len)
 }
 
 // Tiles per chunk task of a large (sub)array of len elements: chunks in
-// proportion to its share of the call's n, about four per CTA of the grid
-// over a whole level (so one level needs ~4 * nctas look-back rows in all),
-// at least four tiles each.
+// proportion to its share of the call's n, about eight per CTA of the grid
+// over a whole level (so one level needs ~8 * nctas look-back rows in all;
+// eight keep the tail of a phase short), at least four tiles each.
 __device__ __forceinline__ uint32_t choose_chunk_tiles(const Params &P, uint32_t tiles, uint32_t len)
 {
-    const unsigned long long want = ((unsigned long long)4 * P.nctas * len + P.n - 1) / P.n;
+    const unsigned long long want = ((unsigned long long)8 * P.nctas * len + P.n - 1) / P.n;
     const uint32_t target = (uint32_t)(want < 1 ? 1 : want);
     const uint32_t ct = (tiles + target - 1) / target;
     return ct < 4u ? 4u : ct;
@@ -327,6 +329,9 @@ __device__ bool stream_tiles(const Params &P, SmemTile &s, Pipe &pp, const uint6
             const bool ok = mbar_wait(&s.bar[w], pp.uses[w] & 1u, P.wait_ns);
             pp.uses[w]++;
             if (__syncthreads_or(!ok)) {  // CTA-uniform: every thread leaves together
+                // one more bounded wait for each buffer's pending copy
+                mbar_wait(&s.bar[w], (pp.uses[w] - 1u) & 1u, P.wait_ns);
+                if (t + 1 < nt) mbar_wait(&s.bar[w ^ 1], pp.uses[w ^ 1] & 1u, P.wait_ns);
                 set_error(P, ST_TIMEOUT);
                 return false;
             }
@@ -369,13 +374,13 @@ __device__ __forceinline__ void body_stats(Acc &a, uint32_t cnt, const unsigned 
 
 // Histogram of the tile's buckets into s.hist: one shared-memory atomic per
 // key, except when a whole warp slot shares one bucket (duplicate runs).
-__device__ __forceinline__ void body_hist(SmemTile &s, uint32_t cnt, const unsigned long long *sk)
+__device__ __forceinline__ void body_hist(SmemTile &s, const MapK &mk, uint32_t cnt, const unsigned long long *sk)
 {
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int i = 0; i < IPT; i++) {
         const uint32_t p = slot_index(i);
-        const uint32_t b = p < cnt ? map_key(s.map, sk[p]) : INVALID;
+        const uint32_t b = p < cnt ? map_key(mk, s.map, sk[p]) : INVALID;
         const uint32_t b0 = __shfl_sync(0xffffffffu, b, 0);
         if (__all_sync(0xffffffffu, b == b0)) {
             if (lane == 0 && b0 != INVALID) atomicAdd(&s.hist[b0], 32u);
@@ -385,66 +390,104 @@ __device__ __forceinline__ void body_hist(SmemTile &s, uint32_t cnt, const unsig
     }
 }
 
-// Stable scatter of one tile: ranks by (bucket, position), stages the tile
-// ordered by bucket in shared memory, then writes each bucket's run at its
-// running cursor (coalesced within runs); cursors advance by the tile counts.
-// The output pass recomputes each staged key's bucket, except for the learned
-// map, whose buckets are staged.
-template <int NBITS>
-__device__ __forceinline__ void body_scatter(const Params &P, SmemTile &s, uint32_t cnt, unsigned long long *sk,
-                                             uint32_t *sv, uint64_t *dstk, uint32_t *dstv, uint32_t seglen)
-{
-    const uint32_t k = s.map.k;
-    const bool stage_b = s.map.kind == MAP_PWL;
-    unsigned long long x[IPT];
-    uint32_t v[IPT], b[IPT], pos[IPT];
-#pragma unroll
-    for (int i = 0; i < IPT; i++) {
-        const uint32_t p = slot_index(i);
-        const bool ok = p < cnt;
-        x[i] = ok ? sk[p] : 0ull;
-        v[i] = ok ? sv[p] : 0u;
-        b[i] = ok ? map_key(s.map, x[i]) : 0u;
-    }
-    tile_rank<IPT, NBITS>(b, pos, k, cnt, s);
-    for (uint32_t q = threadIdx.x; q < k; q += BLOCK) {
-        const uint32_t c = s.cursor[q];
-        s.gdelta[q] = c - s.tstart[q];
-        s.cursor[q] = c + s.tcount[q];
-    }
-#pragma unroll
-    for (int i = 0; i < IPT; i++) {
-        if (pos[i] != INVALID) {
-            sk[pos[i]] = x[i];
-            sv[pos[i]] = v[i];
-            if (stage_b) s.bkt[pos[i]] = (uint16_t)b[i];
-        }
-    }
-    __syncthreads();
-    for (uint32_t p = threadIdx.x; p < cnt; p += BLOCK) {
-        const unsigned long long key = sk[p];
-        const uint32_t q = stage_b ? (uint32_t)s.bkt[p] : map_key(s.map, key);
-        const uint32_t rel = s.gdelta[q] + p;
-        if (rel < seglen) {
-            __stcg(dstk + rel, key);
-            __stcg(dstv + rel, sv[p]);
-        } else {
-            set_error(P, ST_INTERNAL);
-        }
-    }
-}
-
-// Streams [start, start+len) of a (sub)array through body_scatter with the
-// ballot width chosen for its bucket count.
+// Stable scatter of [start, start+len) of a (sub)array whose map is in s.map
+// and whose running bucket cursors are in s.cursor.  Per tile: rank the
+// pairs by (bucket, position) with ballots, stage them in that order in the
+// tile's own buffer, then write each bucket's run at its cursor (coalesced
+// within runs); the output pass recomputes each staged key's bucket, except
+// for the learned map, whose buckets are staged.  Four barriers a tile: the
+// tile's bulk copy is issued once every thread has left the tile that last
+// used its buffer, and each warp clears its own bucket counters.
 template <int NBITS>
 __device__ __noinline__ void scatter_stream(const Params &P, SmemTile &s, Pipe &pp, const uint64_t *srck,
                                             const uint32_t *srcv, bool bulk, unsigned long long start,
                                             unsigned long long len, uint64_t *dstk, uint32_t *dstv, uint32_t seglen)
 {
-    stream_tiles<true>(P, s, pp, srck, srcv, bulk, start, len,
-                       [&](uint32_t, uint32_t cnt, unsigned long long *sk, uint32_t *sv) {
-                           body_scatter<NBITS>(P, s, cnt, sk, sv, dstk, dstv, seglen);
-                       });
+    const uint32_t nt = (uint32_t)((len + TILE - 1) / TILE);
+    if (nt == 0) return;
+    const MapK mk = map_regs(s.map);
+    const uint32_t k = mk.k;
+    const bool stage_b = mk.kind == MAP_PWL;
+    rank_zero_warp(k, s);
+    if (bulk && threadIdx.x == 0)
+        stream_issue<true>(P, s, 0, srck, srcv, start, (uint32_t)min(len, (unsigned long long)TILE));
+    bool err = false;
+    for (uint32_t t = 0; t < nt; t++) {
+        const int w = t & 1;
+        const unsigned long long a = start + (unsigned long long)t * TILE;
+        const uint32_t cnt = (uint32_t)min((unsigned long long)TILE, len - (unsigned long long)t * TILE);
+        unsigned long long *sk;
+        uint32_t *sv;
+        bool ok = true;
+        if (bulk) {
+            sk = s.u.buf[w].key + (a & 1ull);
+            sv = s.u.buf[w].val + (a & 3ull);
+            ok = mbar_wait(&s.bar[w], pp.uses[w] & 1u, P.wait_ns);
+            pp.uses[w]++;
+            if (a + cnt > (P.n & ~3ull)) {  // the array's last elements: plain loads (uniform branch)
+                stream_fix_tail<true>(P, sk, sv, srck, srcv, a, cnt);
+                __syncthreads();
+            }
+        } else {
+            sk = s.u.buf[w].key;
+            sv = s.u.buf[w].val;
+            for (uint32_t i = threadIdx.x; i < cnt; i += BLOCK) {
+                sk[i] = __ldcg(srck + a + i);
+                sv[i] = __ldcg(srcv + a + i);
+            }
+            __syncthreads();
+        }
+        unsigned long long x[IPT];
+        uint32_t v[IPT], b[IPT], pos[IPT], peers[IPT];
+#pragma unroll
+        for (int i = 0; i < IPT; i++) {
+            const uint32_t p = slot_index(i);
+            const bool in = p < cnt;
+            x[i] = in ? sk[p] : 0ull;
+            v[i] = in ? sv[p] : 0u;
+            b[i] = in ? map_key(mk, s.map, x[i]) : 0u;
+        }
+        rank_peers<IPT, NBITS>(b, cnt, peers);
+        rank_leaders<IPT>(b, peers, pos, s);
+        // every thread has left the previous tile: its buffer may be refilled
+        if (__syncthreads_or(!ok)) {
+            // a copy did not complete in time: give it one more bounded wait
+            // before leaving, so that no copy lands in a reused buffer
+            mbar_wait(&s.bar[w], (pp.uses[w] - 1u) & 1u, P.wait_ns);
+            err = true;
+            break;
+        }
+        if (bulk && t + 1 < nt && threadIdx.x == 0) {
+            const unsigned long long an = a + TILE;
+            stream_issue<true>(P, s, w ^ 1, srck, srcv, an, (uint32_t)min((unsigned long long)TILE, start + len - an));
+        }
+        rank_scan<true>(k, s);
+        rank_place<IPT>(b, pos, s);
+        rank_zero_warp(k, s);
+#pragma unroll
+        for (int i = 0; i < IPT; i++) {
+            if (pos[i] != INVALID) {
+                sk[pos[i]] = x[i];
+                sv[pos[i]] = v[i];
+                if (stage_b) s.bkt[pos[i]] = (uint16_t)b[i];
+            }
+        }
+        __syncthreads();
+        for (uint32_t p = threadIdx.x; p < cnt; p += BLOCK) {
+            const unsigned long long key = sk[p];
+            const uint32_t q = stage_b ? (uint32_t)s.bkt[p] : map_key(mk, s.map, key);
+            const uint32_t rel = s.gdelta[q] + p;
+            if (rel < seglen) {
+                __stcg(dstk + rel, key);
+                __stcg(dstv + rel, sv[p]);
+            } else {
+                set_error(P, ST_INTERNAL);
+            }
+        }
+        fence_proxy_async();  // this thread's smem accesses before the buffer's next bulk write
+    }
+    if (err) set_error(P, ST_TIMEOUT);
+    __syncthreads();
 }
 
 __device__ void scatter_dispatch(const Params &P, SmemTile &s, Pipe &pp, const uint64_t *srck, const uint32_t *srcv,
@@ -502,45 +545,34 @@ __device__ __noinline__ void classify_children(const Params &P, unsigned long lo
             L.leaf_len[nl++] = glen;
         }
         if (child_level > (uint32_t)MAX_LEVEL && (nm + ng) > 0) set_error(P, ST_INTERNAL);
-        // large children: descriptor + look-back rows, else demoted to medium
-        uint32_t nok = 0;
+        // large children: one descriptor and look-back rows each, allocated
+        // for the whole batch with two atomics; no room -> all medium
+        unsigned long long need = 0;
         for (uint32_t g = 0; g < ng; g++) {
             const uint32_t len = L.lg_len[g];
-            const uint32_t off_rel = L.lg_off[g];
-            const uint32_t kk = choose_k(P, len);
             const uint32_t tiles = (len + TILE - 1) / TILE;
-            const uint32_t ct = choose_chunk_tiles(P, tiles, len);
-            const uint32_t chunks = (tiles + ct - 1) / ct;
-            const unsigned long long need = 2ull * chunks * kk;
-            const uint32_t sid = atomicAdd(&P.ctl->seg_alloc, 1u);
-            unsigned long long sb = ~0ull;
-            if (sid < P.segcap) sb = atomicAdd(&P.ctl->status_alloc, need);
-            if (sid < P.segcap && sb + need <= P.statuscap) {
-                Seg *S = &P.segs[sid];
-                S->off = poff + off_rel;
-                S->mn = ~0ull;
-                S->mx = 0ull;
-                S->s1[0] = S->s1[1] = 0ull;
-                S->s2[0] = S->s2[1] = S->s2[2] = 0ull;
-                S->status_base = sb;
-                S->len = len;
-                S->k = kk;
-                S->tiles = tiles;
-                S->chunk_tiles = ct;
-                S->chunks = chunks;
-                S->level = child_level;
-                S->buf = child_buf;
-                S->kind = MAP_Z;
-                S->train_slot = INVALID;
-                L.lg_sid[nok] = sid;  // compacted in place (nok <= g)
-                L.lg_len[nok] = len;
-                L.lg_off[nok] = chunks;
-                nok++;
-            } else {
-                if (sid < P.segcap) P.segs[sid].len = 0;
-                L.med_off[nm] = off_rel;
-                L.med_len[nm++] = len;
+            const uint32_t chunks = (tiles + choose_chunk_tiles(P, tiles, len) - 1) / choose_chunk_tiles(P, tiles, len);
+            L.lg_need[g] = (uint32_t)need;
+            need += 2ull * chunks * choose_k(P, len);
+        }
+        uint32_t sid0 = 0;
+        unsigned long long sb0 = 0;
+        bool ok = ng > 0 && need < (1ull << 32);
+        if (ok) {
+            sid0 = atomicAdd(&P.ctl->seg_alloc, ng);
+            ok = sid0 + (unsigned long long)ng <= P.segcap;
+        }
+        if (ok) {
+            sb0 = atomicAdd(&P.ctl->status_alloc, need);
+            ok = sb0 + need <= P.statuscap;
+        }
+        uint32_t nok = ng;
+        if (!ok && ng > 0) {
+            for (uint32_t g = 0; g < ng; g++) {
+                L.med_off[nm] = L.lg_off[g];
+                L.med_len[nm++] = L.lg_len[g];
             }
+            nok = 0;
         }
         uint32_t base = atomicAdd(&P.ctl->item_alloc, nl + nm);
         if (base + nl + nm > P.itemcap) {
@@ -551,9 +583,12 @@ __device__ __noinline__ void classify_children(const Params &P, unsigned long lo
         s.n_med = nm;
         s.n_large_ok = nok;
         s.item_base = base;
+        s.e_base = sid0;
+        s.red64[0] = sb0;
     }
     __syncthreads();
-    const uint32_t nl = s.n_leaf, nm = s.n_med, nok = s.n_large_ok, base = s.item_base;
+    const uint32_t nl = s.n_leaf, nm = s.n_med, nok = s.n_large_ok, base = s.item_base, sid0 = s.e_base;
+    const unsigned long long sb0 = s.red64[0];
     for (uint32_t i = threadIdx.x; i < nl + nm; i += BLOCK) {
         Item it;
         const bool leaf = i < nl;
@@ -563,11 +598,32 @@ __device__ __noinline__ void classify_children(const Params &P, unsigned long lo
         it.level = (uint16_t)child_level;
         P.items[base + i] = it;
     }
-    for (uint32_t g = 0; g < nok; g++) {
-        const uint32_t sid = L.lg_sid[g];
-        const uint32_t kk = choose_k(P, L.lg_len[g]);
-        for (uint32_t q = threadIdx.x; q < kk; q += BLOCK) P.counts[(size_t)sid * NB_MAX + q] = 0;
+    for (uint32_t g = threadIdx.x; g < nok; g += BLOCK) {
+        const uint32_t len = L.lg_len[g];
+        const uint32_t tiles = (len + TILE - 1) / TILE;
+        const uint32_t ct = choose_chunk_tiles(P, tiles, len);
+        Seg *S = &P.segs[sid0 + g];
+        S->off = poff + L.lg_off[g];
+        S->mn = ~0ull;
+        S->mx = 0ull;
+        S->s1[0] = S->s1[1] = 0ull;
+        S->s2[0] = S->s2[1] = S->s2[2] = 0ull;
+        S->status_base = sb0 + L.lg_need[g];
+        S->len = len;
+        S->k = choose_k(P, len);
+        S->tiles = tiles;
+        S->chunk_tiles = ct;
+        S->chunks = (tiles + ct - 1) / ct;
+        S->level = child_level;
+        S->buf = child_buf;
+        S->kind = MAP_Z;
+        S->train_slot = INVALID;
     }
+    for (uint32_t g = 0; g < nok; g++) {
+        const uint32_t kk = choose_k(P, L.lg_len[g]);
+        for (uint32_t q = threadIdx.x; q < kk; q += BLOCK) P.counts[(size_t)(sid0 + g) * NB_MAX + q] = 0;
+    }
+    __threadfence();  // descriptors, items and counters before the entries are published
     __syncthreads();
     if (threadIdx.x == 0) {
         const uint32_t cnt = (nl > 0) + (nm > 0) + nok;
@@ -576,7 +632,11 @@ __device__ __noinline__ void classify_children(const Params &P, unsigned long lo
             uint32_t j = e;
             if (nl) q_write(P, j++, T_FINISH, base, nl);
             if (nm) q_write(P, j++, T_MPART, base + nl, nm);
-            for (uint32_t g = 0; g < nok; g++) q_write(P, j++, T_LSTATS, L.lg_sid[g], L.lg_off[g]);
+            for (uint32_t g = 0; g < nok; g++) {
+                const uint32_t tiles = (L.lg_len[g] + TILE - 1) / TILE;
+                const uint32_t ct = choose_chunk_tiles(P, tiles, L.lg_len[g]);
+                q_write(P, j++, T_LSTATS, sid0 + g, (tiles + ct - 1) / ct);
+            }
             q_release_all(P, e, cnt);
         }
     }
@@ -850,11 +910,12 @@ __device__ __noinline__ void task_lhist(const Params &P, uint32_t sid, uint32_t 
     load_seg_map(P, sid, s);
     const Chunk ch = chunk_of(P, sid, c);
     const uint32_t k = ch.k;
+    const MapK mk = map_regs(s.map);
     for (uint32_t q = threadIdx.x; q < k; q += BLOCK) s.hist[q] = 0;
     __syncthreads();
     const uint64_t *src = keys_of(P, ch.buf);
     stream_tiles<false>(P, s, pp, src, nullptr, bulk_ok(P, ch.buf), ch.start, ch.len,
-                        [&](uint32_t, uint32_t cnt, unsigned long long *sk, uint32_t *) { body_hist(s, cnt, sk); });
+                        [&](uint32_t, uint32_t cnt, unsigned long long *sk, uint32_t *) { body_hist(s, mk, cnt, sk); });
     uint32_t *status = P.status + ch.sbase;
     uint32_t *row = status + (size_t)c * k;
     uint32_t *offs = status + (size_t)ch.chunks * k + (size_t)c * k;
@@ -1019,10 +1080,11 @@ __device__ __noinline__ void task_mpart(const Params &P, const Item it, SmemTile
         return;
     }
     const uint32_t k = s.map.k;
+    const MapK mk = map_regs(s.map);
     for (uint32_t q = threadIdx.x; q < k; q += BLOCK) s.hist[q] = 0;
     __syncthreads();
     stream_tiles<false>(P, s, pp, srck, nullptr, bulk, off, len,
-                        [&](uint32_t, uint32_t cnt, unsigned long long *sk, uint32_t *) { body_hist(s, cnt, sk); });
+                        [&](uint32_t, uint32_t cnt, unsigned long long *sk, uint32_t *) { body_hist(s, mk, cnt, sk); });
     block_exclusive_scan(s.hist, s.bs, k, s.wsum);
     for (uint32_t q = threadIdx.x; q < k; q += BLOCK) s.cursor[q] = s.bs[q];
     __syncthreads();
@@ -1038,6 +1100,17 @@ __device__ __noinline__ void task_mpart(const Params &P, const Item it, SmemTile
 }
 
 // ------------------------------------------------------------ FINISH
+// Thread 0: L2 prefetch of a leaf's pairs (the span its bulk copies read).
+__device__ void prefetch_item_l2(const Params &P, const Item it)
+{
+    if (!bulk_ok(P, it.buf)) return;
+    const unsigned long long off = it.off, len = it.len;
+    const unsigned long long a0 = off & ~1ull, a1 = min((off + len + 1) & ~1ull, P.n & ~1ull);
+    const unsigned long long b0 = off & ~3ull, b1 = min((off + len + 3) & ~3ull, P.n & ~3ull);
+    if (a1 > a0) bulk_prefetch_l2(keys_of(P, it.buf) + a0, (uint32_t)(a1 - a0) * 8u);
+    if (b1 > b0) bulk_prefetch_l2(vals_of(P, it.buf) + b0, (uint32_t)(b1 - b0) * 4u);
+}
+
 __device__ bool insertion_sort_budget(unsigned long long *k, uint32_t *v, uint32_t n, uint32_t budget)
 {
     uint32_t moves = 0;
@@ -1107,76 +1180,55 @@ __device__ __forceinline__ uint32_t leaf_sub(unsigned long long key, unsigned lo
 constexpr uint32_t LEAF_M2_MAX = 2048;  // sub-buckets of the fast leaf path
 constexpr uint32_t LEAF_FAST_MAX = 32;  // largest sub-bucket the fast path ranks by counting
 
-// Fast leaf path: sub-bucket counts in cnt[0..M2) are known.  Pairs are
-// placed by sub-bucket with smem atomics (unstable), then each pair's rank
-// is counted inside its sub-bucket on (key, leaf position), a total order
-// whose sorted sequence is the stable sort; pairs move to their ranks.
-__device__ __noinline__ void finish_fast(SmemTile &s, unsigned long long *key, uint32_t *val, uint32_t len,
+// Fast leaf path.  Every thread holds its pairs (leaf positions threadIdx.x +
+// j * BLOCK) in registers and already took, with a shared-memory atomic on the
+// counter of its sub-bucket, an arrival slot a[j] inside it; cnt[0..M2) holds
+// the sub-bucket counts.  The pairs are staged by sub-bucket (arrival order,
+// not yet stable) with their leaf positions; then each staged pair counts its
+// rank inside its sub-bucket on (key, leaf position) -- a total order whose
+// sorted sequence is the stable sort -- and goes straight to that rank of the
+// output (consecutive staged pairs have nearly consecutive ranks).
+__device__ __forceinline__ void finish_fast(SmemTile &s, unsigned long long *key, uint32_t *val, uint32_t len,
                                          unsigned long long mn, uint32_t rs, uint32_t rm, uint32_t M2,
-                                         uint64_t *dk, uint32_t *dv)
+                                         const unsigned long long (&kk)[LEAF_IPT], const uint32_t (&vv)[LEAF_IPT],
+                                         const uint32_t (&a)[LEAF_IPT], uint64_t *dk, uint32_t *dv)
 {
     uint32_t *cnt = reinterpret_cast<uint32_t *>(s.wcnt);
-    uint32_t *cur = cnt + LEAF_M2_MAX;
-    uint16_t *sidx = s.bkt;                                // leaf position of each placed pair
-    uint16_t *rank = reinterpret_cast<uint16_t *>(s.hist);  // hist + cursor: LEAF_CAP u16
+    uint16_t *sidx = s.bkt;  // leaf position of each staged pair
+    if (threadIdx.x == 0) cnt[M2] = len;  // sentinel: end of the last sub-bucket
     block_exclusive_scan<LEAF_M2_MAX / BLOCK>(cnt, cnt, M2, s.wsum);
-    for (uint32_t q = threadIdx.x; q < M2; q += BLOCK) cur[q] = cnt[q];
-    unsigned long long kk[LEAF_IPT];
-    uint32_t vv[LEAF_IPT];
-#pragma unroll
-    for (int j = 0; j < LEAF_IPT; j++) {
-        const uint32_t p = threadIdx.x + j * BLOCK;
-        kk[j] = p < len ? key[p] : 0ull;
-        vv[j] = p < len ? val[p] : 0u;
-    }
-    __syncthreads();
 #pragma unroll
     for (int j = 0; j < LEAF_IPT; j++) {
         const uint32_t p = threadIdx.x + j * BLOCK;
         if (p < len) {
-            const uint32_t q = atomicAdd(&cur[leaf_sub(kk[j], mn, rs, rm)], 1u);
+            const uint32_t q = cnt[leaf_sub(kk[j], mn, rs, rm)] + a[j];
             key[q] = kk[j];
             val[q] = vv[j];
             sidx[q] = (uint16_t)p;
         }
     }
     __syncthreads();
-    for (uint32_t p = threadIdx.x; p < len; p += BLOCK) {
-        const unsigned long long xk = key[p];
-        const uint32_t me = sidx[p];
+    // the warp's lanes walk their sub-buckets in lockstep (warp-uniform trip
+    // count, clamped reads): no divergence in the counting loop
+    for (uint32_t p0 = 0; p0 < len; p0 += BLOCK) {
+        const uint32_t p = p0 + threadIdx.x;
+        const uint32_t pc = p < len ? p : len - 1;
+        const unsigned long long xk = key[pc];
+        const uint32_t me = sidx[pc];
         const uint32_t q = leaf_sub(xk, mn, rs, rm);
-        const uint32_t lo = cnt[q], hi = cur[q];
+        const uint32_t lo = cnt[q], hi = cnt[q + 1];
+        const uint32_t m = __reduce_max_sync(0xffffffffu, hi - lo);
         uint32_t r = lo;
-        for (uint32_t j = lo; j < hi; j++) {
+        for (uint32_t t = 0; t < m; t++) {
+            const uint32_t j = min(lo + t, hi - 1);
             const unsigned long long kj = key[j];
-            r += (kj < xk) || (kj == xk && sidx[j] < me);
+            const uint32_t sj = sidx[j];
+            r += (uint32_t)(lo + t < hi) & ((uint32_t)(kj < xk) | ((uint32_t)(kj == xk) & (uint32_t)(sj < me)));
         }
-        rank[p] = (uint16_t)r;
-    }
-    __syncthreads();
-    uint32_t rr[LEAF_IPT];
-#pragma unroll
-    for (int j = 0; j < LEAF_IPT; j++) {
-        const uint32_t p = threadIdx.x + j * BLOCK;
         if (p < len) {
-            kk[j] = key[p];
-            vv[j] = val[p];
-            rr[j] = rank[p];
+            __stcg(dk + r, xk);
+            __stcg(dv + r, val[p]);
         }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < LEAF_IPT; j++) {
-        const uint32_t p = threadIdx.x + j * BLOCK;
-        if (p < len) {
-            key[rr[j]] = kk[j];
-            val[rr[j]] = vv[j];
-        }
-    }
-    __syncthreads();
-    for (uint32_t p = threadIdx.x; p < len; p += BLOCK) {
-        __stcg(dk + p, key[p]);
-        __stcg(dv + p, val[p]);
     }
 }
 
@@ -1258,6 +1310,7 @@ __device__ __noinline__ void task_finish(const Params &P, const Item it, SmemTil
         const bool ok = mbar_wait(&s.bar[0], pp.uses[0] & 1u, P.wait_ns);
         pp.uses[0]++;
         if (__syncthreads_or(!ok)) {  // CTA-uniform: every thread leaves together
+            mbar_wait(&s.bar[0], (pp.uses[0] - 1u) & 1u, P.wait_ns);  // one more bounded wait
             set_error(P, ST_TIMEOUT);
             return;
         }
@@ -1275,12 +1328,23 @@ __device__ __noinline__ void task_finish(const Params &P, const Item it, SmemTil
         }
     }
     __syncthreads();
+    // this thread's pairs (leaf positions threadIdx.x + j * BLOCK) in registers
+    unsigned long long kk[LEAF_IPT];
+    uint32_t vv[LEAF_IPT];
     unsigned long long mn = ~0ull, mx = 0ull;
-    for (uint32_t p = threadIdx.x; p < len; p += BLOCK) {
-        const unsigned long long xk = key[p];
-        mn = xk < mn ? xk : mn;
-        mx = xk > mx ? xk : mx;
+#pragma unroll
+    for (int j = 0; j < LEAF_IPT; j++) {
+        const uint32_t p = threadIdx.x + j * BLOCK;
+        kk[j] = p < len ? key[p] : 0ull;
+        vv[j] = p < len ? val[p] : 0u;
+        if (p < len) {
+            mn = kk[j] < mn ? kk[j] : mn;
+            mx = kk[j] > mx ? kk[j] : mx;
+        }
     }
+    const uint32_t M2 = min(LEAF_M2_MAX, pow2ceil32(len) / 2);
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(s.wcnt);
+    for (uint32_t q = threadIdx.x; q < M2; q += BLOCK) cnt[q] = 0u;
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
         const unsigned long long a = shfl_down64(mn, o), b2 = shfl_down64(mx, o);
@@ -1304,9 +1368,13 @@ __device__ __noinline__ void task_finish(const Params &P, const Item it, SmemTil
     }
     if (mn == mx) {  // identical keys: in order already
         if (buf) {
-            for (uint32_t p = threadIdx.x; p < len; p += BLOCK) {
-                __stcg(dk + p, key[p]);
-                __stcg(dv + p, val[p]);
+#pragma unroll
+            for (int j = 0; j < LEAF_IPT; j++) {
+                const uint32_t p = threadIdx.x + j * BLOCK;
+                if (p < len) {
+                    __stcg(dk + p, kk[j]);
+                    __stcg(dv + p, vv[j]);
+                }
             }
         }
         return;
@@ -1314,29 +1382,31 @@ __device__ __noinline__ void task_finish(const Params &P, const Item it, SmemTil
     if (len <= (uint32_t)RANK_SMALL) {
         const uint32_t t = threadIdx.x;
         if (t < len) {
-            const unsigned long long kt = key[t];
+            const unsigned long long kt = kk[0];
             uint32_t r = 0;
             for (uint32_t q = 0; q < len; q++) {
                 const unsigned long long kq = key[q];
                 r += (kq < kt) || (kq == kt && q < t);
             }
             __stcg(dk + r, kt);
-            __stcg(dv + r, val[t]);
+            __stcg(dv + r, vv[0]);
         }
         return;
     }
-    const uint32_t M2 = min(LEAF_M2_MAX, pow2ceil32(len) / 2);
+    // sub-buckets by the range map (the counting map when max - min < M2);
+    // the atomic's old value is the pair's arrival slot in its sub-bucket
     uint32_t rs2, rm2;
     range_params(mx - mn, M2, &rs2, &rm2);
-    uint32_t *cnt = reinterpret_cast<uint32_t *>(s.wcnt);
-    for (uint32_t q = threadIdx.x; q < M2; q += BLOCK) cnt[q] = 0u;
-    __syncthreads();
-    for (uint32_t p = threadIdx.x; p < len; p += BLOCK) atomicAdd(&cnt[leaf_sub(key[p], mn, rs2, rm2)], 1u);
-    __syncthreads();
-    uint32_t big = 0;
-    for (uint32_t q = threadIdx.x; q < M2; q += BLOCK) big = max(big, cnt[q]);
-    if (!__syncthreads_or(big > LEAF_FAST_MAX))
-        finish_fast(s, key, val, len, mn, rs2, rm2, M2, dk, dv);
+    uint32_t a[LEAF_IPT];
+    bool big = false;
+#pragma unroll
+    for (int j = 0; j < LEAF_IPT; j++) {
+        const uint32_t p = threadIdx.x + j * BLOCK;
+        a[j] = p < len ? atomicAdd(&cnt[leaf_sub(kk[j], mn, rs2, rm2)], 1u) : 0u;
+        big = big || a[j] >= LEAF_FAST_MAX;
+    }
+    if (!__syncthreads_or(big))
+        finish_fast(s, key, val, len, mn, rs2, rm2, M2, kk, vv, a, dk, dv);
     else
         finish_stable(P, s, key, val, len, mn, mx, dk, dv);
 }
