@@ -115,11 +115,14 @@ def make_workload(n: int):
     return [("lognormal", inputs.lognormal(n, 30)), ("gmm8", inputs.gaussian_mixture(n, 31))]
 
 
-def batched_measure(z, torch, dev, nseg: int, seed: int, steps: int, warmup: int, plain_segments: int):
+def batched_measure(z, torch, dev, nseg: int, seed: int, steps: int, warmup: int, plain_segments: int,
+                    tune_cache=None, tune_budget_ms: int = 60_000):
     """zsort_segmented on a batch of nseg log-uniform (32..2^20) segments, one
-    persistent launch replayed from a CUDA graph; beside it the plain path,
-    one zsort_pairs call per segment on the same data (first plain_segments
-    segments, scaled to pairs/s)."""
+    persistent launch replayed from a CUDA graph, with the knobs chosen by the
+    library's autotuner (untimed; served from tune_cache when it has the
+    class); beside it the plain path, one zsort_pairs call per segment on the
+    same data with default options (first plain_segments segments, scaled to
+    pairs/s)."""
     keys, vals, off, _ = inputs.segmented(nseg, seed)
     n = keys.size
     kp = torch.from_numpy(keys.view(np.int64)).to(dev)
@@ -127,9 +130,16 @@ def batched_measure(z, torch, dev, nseg: int, seed: int, steps: int, warmup: int
     od = torch.from_numpy(off.view(np.int64)).to(dev)
     kb, vb = torch.empty_like(kp), torch.empty_like(vp)
     stream = torch.cuda.Stream(device=dev)
-    opts = z.default_opts(flags=z.FLAG_GRAPH)
     with torch.cuda.stream(stream):
         z.reserve(n, nseg, stream)
+        t0 = time.perf_counter()
+        cached = tune_cache is not None and os.path.exists(tune_cache)
+        opts = z.autotune(kp, vp, offsets=od, base=z.default_opts(flags=z.FLAG_GRAPH), cache_path=tune_cache,
+                          budget_ms=tune_budget_ms, reps=1, stream=stream)
+        tune_s = time.perf_counter() - t0
+        tuned = {f: getattr(opts, f) for f in ("kmax", "leaf_target", "leaf_cap", "large_min", "chunks_per_cta")}
+        tuned.update({"class": z.tune_class(kp, nseg=nseg, stream=stream), "tune_s": round(tune_s, 2),
+                      "cache": tune_cache, "cache_existed": cached})
         times = []
         for i in range(warmup + steps):
             kb.copy_(kp)
@@ -171,7 +181,7 @@ def batched_measure(z, torch, dev, nseg: int, seed: int, steps: int, warmup: int
         plain_ms = e0.elapsed_time(e1)
     ms = sum(times) / len(times)
     return {"segments": nseg, "pairs": n, "value": n / (ms / 1e3), "unit": UNIT, "ms": ms,
-            "graph": True, "bytes_per_pair": st["bytes_algorithmic"] / n,
+            "graph": True, "bytes_per_pair": st["bytes_algorithmic"] / n, "autotuned": tuned,
             "plain_per_segment_calls": {"segments": m, "pairs": b - a,
                                         "value": (b - a) / (plain_ms / 1e3), "unit": UNIT}}
 
@@ -247,6 +257,9 @@ def main():
     ap.add_argument("--workload", default="pairs", choices=["pairs", "batched"],
                     help="pairs: 2 x 2^logn arrays; batched: segmented sort of --segments arrays")
     ap.add_argument("--segments", type=int, default=20_000)
+    ap.add_argument("--tune-cache", default=os.environ.get("ZSORT_TUNE_CACHE"),
+                    help="autotuner cache file for the batched workload (default: $ZSORT_TUNE_CACHE, else none)")
+    ap.add_argument("--tune-budget-ms", type=int, default=60_000)
     ap.add_argument("--batched-side", type=int, default=2000,
                     help="segments of the batched measurement reported beside the pairs workload (0: none)")
     args = ap.parse_args()
@@ -276,7 +289,8 @@ def main():
     z.load()
 
     if args.workload == "batched":
-        res = batched_measure(z, torch, dev, args.segments, 5, args.steps, args.warmup, 2000)
+        res = batched_measure(z, torch, dev, args.segments, 5, args.steps, args.warmup, 2000,
+                              args.tune_cache, args.tune_budget_ms)
         if rank == 0:
             line = {
                 "metric": METRIC, "value": world * res["value"], "unit": UNIT, "n_gpus": world,
@@ -430,7 +444,8 @@ def main():
     if args.batched_side > 0:
         del bufs
         torch.cuda.empty_cache()
-        batched = batched_measure(z, torch, dev, args.batched_side, 5, 5, 3, min(args.batched_side, 2000))
+        batched = batched_measure(z, torch, dev, args.batched_side, 5, 5, 3, min(args.batched_side, 2000),
+                                  args.tune_cache, min(args.tune_budget_ms, 20_000))
 
     cpu = None
     if rank == 0 and not args.no_cpu:

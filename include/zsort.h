@@ -97,6 +97,13 @@ typedef struct {
     uint32_t ctas_per_sm;    /* persistent CTAs per SM, 0 = from occupancy     */
     uint32_t wait_limit_ms;  /* bound of every device-side wait (no progress)  */
     uint32_t flags;          /* ZSORT_FLAG_*                                    */
+    uint32_t leaf_cap;       /* small-bucket cutoff: buckets (and groups of
+                                consecutive buckets) of at most this many
+                                pairs are finished in shared memory,
+                                256..4096 (the CTA's 256 threads hold
+                                leaf_cap / 256 items each)                    */
+    uint32_t chunks_per_cta; /* look-back chunk tasks per CTA over one level
+                                of large partitions, 1..64                    */
 } zsort_opts;
 
 /* flags: capture the call's launch sequence (control-block reset, two set-up

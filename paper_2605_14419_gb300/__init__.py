@@ -19,7 +19,8 @@ import re
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "libzsort.so")
-_HEADER = os.path.join(os.path.dirname(_HERE), "include", "zsort.h")
+_INCLUDE = os.path.join(os.path.dirname(_HERE), "include")
+_HEADERS = [os.path.join(_INCLUDE, h) for h in ("zsort.h", "zsort_tune.h")]
 _lib = None
 
 OK = 0
@@ -27,6 +28,9 @@ ERR_INVALID, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_BAD_OFFSETS, ERR_CAPACITY, ER
     -1, -2, -3, -4, -5, -6, -7)
 MAP_ZSCORE, MAP_LEARNED = 0, 1
 KEY_TYPES = {"u64": 0, "i64": 1, "f64": 2}
+NOT_TUNED = 1
+TUNE_FORCE = 1
+TUNE_CLASS_MAX = 64
 MAX_N = 1 << 30
 MAX_SEG_TOTAL = 1 << 34
 FLAG_GRAPH = 1
@@ -56,6 +60,8 @@ class Opts(ctypes.Structure):
         ("ctas_per_sm", ctypes.c_uint32),
         ("wait_limit_ms", ctypes.c_uint32),
         ("flags", ctypes.c_uint32),
+        ("leaf_cap", ctypes.c_uint32),
+        ("chunks_per_cta", ctypes.c_uint32),
     ]
 
 
@@ -119,9 +125,11 @@ class MapInfo(ctypes.Structure):
 
 
 def header_functions() -> list[str]:
-    """Names of the functions declared in include/zsort.h."""
-    with open(_HEADER) as f:
-        text = f.read()
+    """Names of the functions declared in include/zsort.h and zsort_tune.h."""
+    text = ""
+    for h in _HEADERS:
+        with open(h) as f:
+            text += f.read()
     return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(zsort_\w+)\s*\(", text, re.M)))
 
 
@@ -154,6 +162,14 @@ def load():
         "zsort_strerror": (ctypes.c_char_p, [i32]),
         "zsort_pairs_noalloc": (i32, [vp, vp, u64, vp, vp]),
         "zsort_map_buckets": (i32, [vp, u64, ctypes.POINTER(Opts), vp, ctypes.POINTER(MapInfo), vp]),
+        "zsort_tune_class_host": (i32, [vp, u64, u64, u64, i32, ctypes.c_char_p, ctypes.c_size_t]),
+        "zsort_tune_class": (i32, [vp, u64, u64, ctypes.c_char_p, ctypes.c_size_t, vp]),
+        "zsort_tune_cache_get": (i32, [ctypes.c_char_p, ctypes.c_char_p, ctypes.POINTER(Opts),
+                                       ctypes.POINTER(ctypes.c_double)]),
+        "zsort_tune_cache_put": (i32, [ctypes.c_char_p, ctypes.c_char_p, ctypes.POINTER(Opts), ctypes.c_double]),
+        "zsort_tuned_opts": (i32, [vp, u64, u64, ctypes.POINTER(Opts), ctypes.c_char_p, ctypes.POINTER(Opts), vp]),
+        "zsort_autotune": (i32, [vp, vp, u64, vp, u64, ctypes.POINTER(Opts), ctypes.c_char_p, u32, u32, u32,
+                                 ctypes.POINTER(Opts), vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -266,3 +282,73 @@ def last_stats(stream=None) -> dict:
     s = Stats()
     _raise(load().zsort_last_stats(_stream_handle(stream), ctypes.byref(s)), "zsort_last_stats")
     return s.as_dict()
+
+
+# ------------------------------------------------------------ autotuner
+def _path(p):
+    return None if p is None else os.fsencode(p)
+
+
+def tune_class_host(sample, n: int, nseg: int = 0, sms: int = 152) -> str:
+    """Class string of a call from a host sample (numpy uint64 array)."""
+    import numpy as np
+
+    a = np.ascontiguousarray(sample, dtype=np.uint64)
+    buf = ctypes.create_string_buffer(TUNE_CLASS_MAX)
+    _raise(load().zsort_tune_class_host(a.ctypes.data if a.size else None, a.size, n, nseg, sms, buf,
+                                        TUNE_CLASS_MAX), "zsort_tune_class_host")
+    return buf.value.decode()
+
+
+def tune_class(keys, nseg: int = 0, stream=None) -> str:
+    _check_tensor(keys, 8, "keys")
+    buf = ctypes.create_string_buffer(TUNE_CLASS_MAX)
+    _raise(load().zsort_tune_class(ctypes.c_void_p(keys.data_ptr()), keys.numel(), nseg, buf, TUNE_CLASS_MAX,
+                                   _stream_handle(stream)), "zsort_tune_class")
+    return buf.value.decode()
+
+
+def tune_cache_get(path: str, cls: str, base: Opts | None = None):
+    """(Opts, ms) of a cache entry, or None if the class is not cached."""
+    o = base if base is not None else default_opts()
+    o = Opts.from_buffer_copy(o)
+    ms = ctypes.c_double(0.0)
+    rc = load().zsort_tune_cache_get(_path(path), cls.encode(), ctypes.byref(o), ctypes.byref(ms))
+    if rc == NOT_TUNED:
+        return None
+    _raise(rc, "zsort_tune_cache_get")
+    return o, ms.value
+
+
+def tune_cache_put(path: str, cls: str, opts: Opts, ms: float):
+    _raise(load().zsort_tune_cache_put(_path(path), cls.encode(), ctypes.byref(opts), ms), "zsort_tune_cache_put")
+
+
+def tuned_opts(keys, nseg: int = 0, base: Opts | None = None, cache_path: str | None = None, stream=None):
+    """(Opts, found): the base options with the cached tuned fields of the call's class."""
+    _check_tensor(keys, 8, "keys")
+    out = Opts()
+    rc = load().zsort_tuned_opts(ctypes.c_void_p(keys.data_ptr()), keys.numel(), nseg,
+                                 ctypes.byref(base) if base is not None else None, _path(cache_path),
+                                 ctypes.byref(out), _stream_handle(stream))
+    if rc not in (OK, NOT_TUNED):
+        _raise(rc, "zsort_tuned_opts")
+    return out, rc == OK
+
+
+def autotune(keys, vals, offsets=None, base: Opts | None = None, cache_path: str | None = None,
+             budget_ms: int = 0, reps: int = 3, force: bool = False, stream=None) -> Opts:
+    """Tuned options for sorting (keys, vals) -- or the segmented batch when
+    offsets is given; the tensors are not modified."""
+    _check_tensor(keys, 8, "keys")
+    _check_tensor(vals, 4, "vals")
+    if offsets is not None:
+        _check_tensor(offsets, 8, "offsets")
+    out = Opts()
+    rc = load().zsort_autotune(ctypes.c_void_p(keys.data_ptr()), ctypes.c_void_p(vals.data_ptr()), keys.numel(),
+                               ctypes.c_void_p(offsets.data_ptr()) if offsets is not None else None,
+                               max(offsets.numel() - 1, 0) if offsets is not None else 0,
+                               ctypes.byref(base) if base is not None else None, _path(cache_path), budget_ms, reps,
+                               TUNE_FORCE if force else 0, ctypes.byref(out), _stream_handle(stream))
+    _raise(rc, "zsort_autotune")
+    return out

@@ -1,6 +1,7 @@
 """Builds the CUDA library in-tree: ``paper_2605_14419_gb300/libzsort.so``.
 
-One translation unit, compiled by nvcc for sm_103a only (GB300).  Run as
+Two translation units in one nvcc call: the CUDA library (sm_103a only,
+GB300) and the host-side autotuner.  Run as
 ``python -m paper_2605_14419_gb300.build``; ``__graft_entry__.build()`` calls
 ``build()``.
 """
@@ -14,9 +15,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libzsort.so")
-SOURCES = [os.path.join(CSRC, "zsort.cu")]
+SOURCES = [os.path.join(CSRC, "zsort.cu"), os.path.join(CSRC, "zsort_tune.cpp")]
 DEPS = SOURCES + [os.path.join(CSRC, f) for f in ("zsort_device.cuh", "zsort_tasks.cuh")] + [
-    os.path.join(ROOT, "include", "zsort.h")]
+    os.path.join(ROOT, "include", h) for h in ("zsort.h", "zsort_tune.h")]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-shared"]
 

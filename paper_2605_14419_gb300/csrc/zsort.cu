@@ -127,7 +127,7 @@ __global__ void k_init_segments(Params P, const uint64_t *off, unsigned long lon
     it.len = (uint32_t)len;
     it.buf = 0;
     it.level = 0;
-    if (len <= (unsigned long long)LEAF_CAP && !P.plan_out) {
+    if (len <= (unsigned long long)P.leaf_cap && !P.plan_out) {
         uint32_t j = atomicAdd(&C->init_leaf, 1u);
         P.items[j] = it;
         return;
@@ -240,6 +240,7 @@ struct Workspace {
     cudaStream_t stream = nullptr;
     unsigned long long n_cap = 0, nseg_cap = 0;
     unsigned long long large_min = 0;
+    unsigned long long chunks_cap = 0;
     void *block = nullptr;
     size_t bytes = 0;
     Params P{};
@@ -264,17 +265,20 @@ struct Plan {
         off_items, off_counts, off_bstart, off_status, off_pwl, off_train, total;
 };
 
-Plan make_plan(unsigned long long n, unsigned long long nseg, unsigned long long large_min, int sms)
+Plan make_plan(unsigned long long n, unsigned long long nseg, unsigned long long large_min, int sms,
+               unsigned long long chunks_per_cta)
 {
     Plan p{};
     p.qcap = n / 128 + 4 * nseg + 4096;
     p.segcap = 3 * (n / (large_min + 1)) + 64;
     p.itemcap = 2 * nseg + n / 32 + 4096;
     // look-back rows: 2 x chunks x k words per large (sub)array; the chunks of
-    // one level add up to ~8 per CTA plus at most 2 per (sub)array
+    // one level add up to ~chunks_per_cta per CTA plus at most 2 per
+    // (sub)array; room for two such levels
     const unsigned long long nctas = 2ull * (unsigned long long)(sms > 0 ? sms : 160);
     p.statuscap = 2ull * NB_MAX *
-                  (std::min<unsigned long long>(16 * nctas, n / TILE + 64) + std::min<unsigned long long>(2 * p.segcap, 16384));
+                  (std::min<unsigned long long>(2 * chunks_per_cta * nctas, n / TILE + 64) +
+                   std::min<unsigned long long>(2 * p.segcap, 16384));
     p.traincap = std::min<unsigned long long>(p.segcap, 32);
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -310,7 +314,7 @@ int cuda_err(cudaError_t e)
 
 // Finds or (re)allocates the workspace of (current device, stream).
 int get_workspace(cudaStream_t stream, unsigned long long n, unsigned long long nseg,
-                  unsigned long long large_min, Workspace **out)
+                  unsigned long long large_min, unsigned long long chunks_per_cta, Workspace **out)
 {
     int dev = 0;
     cudaError_t ce = cudaGetDevice(&dev);
@@ -324,7 +328,8 @@ int get_workspace(cudaStream_t stream, unsigned long long n, unsigned long long 
         ws->stream = stream;
         g_ws.push_back(ws);
     }
-    if (!ws->block || ws->n_cap < n || ws->nseg_cap < nseg || ws->large_min != large_min) {
+    if (!ws->block || ws->n_cap < n || ws->nseg_cap < nseg || ws->large_min != large_min ||
+        ws->chunks_cap < chunks_per_cta) {
         unsigned long long ncap = std::max<unsigned long long>(n, ws->n_cap);
         unsigned long long scap = std::max<unsigned long long>(nseg, ws->nseg_cap);
         ncap = std::max<unsigned long long>(ncap, 1);
@@ -332,7 +337,8 @@ int get_workspace(cudaStream_t stream, unsigned long long n, unsigned long long 
         int sms = 0;
         ce = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (ce != cudaSuccess) return cuda_err(ce);
-        Plan p = make_plan(ncap, scap, large_min, sms);
+        const unsigned long long ccap = std::max<unsigned long long>(chunks_per_cta, ws->chunks_cap);
+        Plan p = make_plan(ncap, scap, large_min, sms, ccap);
         if (ws->block) {
             ce = cudaStreamSynchronize(stream);  // the old block may still be in use
             if (ce != cudaSuccess) return cuda_err(ce);
@@ -356,6 +362,7 @@ int get_workspace(cudaStream_t stream, unsigned long long n, unsigned long long 
         ws->n_cap = ncap;
         ws->nseg_cap = scap;
         ws->large_min = large_min;
+        ws->chunks_cap = ccap;
         char *b = static_cast<char *>(blk);
         Params &P = ws->P;
         P = Params{};
@@ -409,6 +416,8 @@ bool opts_valid(const zsort_opts &o)
     if (o.learn_min < o.sample) return false;
     if (!(o.fallback_ratio > 0.0f)) return false;
     if (o.guard_level < 1) return false;
+    if (o.leaf_cap < (uint32_t)RANK_SMALL || o.leaf_cap > (uint32_t)LEAF_CAP) return false;
+    if (o.chunks_per_cta < 1 || o.chunks_per_cta > 64) return false;
     return true;
 }
 
@@ -418,7 +427,7 @@ int launch(uint64_t *keys, uint32_t *vals, unsigned long long n, const uint64_t 
 {
     std::lock_guard<std::mutex> lock(g_mu);
     Workspace *ws = nullptr;
-    int rc = get_workspace(stream, n, nseg, o.large_min, &ws);
+    int rc = get_workspace(stream, n, nseg, o.large_min, o.chunks_per_cta, &ws);
     if (rc != ZSORT_OK) return rc;
     Params P = ws->P;
     P.ukeys = keys;
@@ -432,6 +441,8 @@ int launch(uint64_t *keys, uint32_t *vals, unsigned long long n, const uint64_t 
     P.sample = o.sample;
     P.mapper = o.mapper;
     P.guard_level = o.guard_level;
+    P.leaf_cap = o.leaf_cap;
+    P.chunks_per_cta = o.chunks_per_cta;
     P.fallback_ratio = o.fallback_ratio;
     P.seed = o.seed;
     P.wait_ns = (unsigned long long)o.wait_limit_ms * 1000000ull;
@@ -589,6 +600,8 @@ void zsort_default_opts(zsort_opts *o)
     o->guard_level = 8;
     o->ctas_per_sm = 0;
     o->wait_limit_ms = 2000;
+    o->leaf_cap = LEAF_CAP;
+    o->chunks_per_cta = 8;
 }
 
 int zsort_pairs_ex(void *keys, uint32_t key_type, uint32_t *vals, uint64_t n, const zsort_opts *opts,
@@ -655,7 +668,7 @@ int zsort_reserve(uint64_t n, uint64_t nseg, zsort_stream_t stream)
     std::lock_guard<std::mutex> lock(g_mu);
     Workspace *ws = nullptr;
     return get_workspace(reinterpret_cast<cudaStream_t>(stream), n, std::max<uint64_t>(nseg, 1),
-                         o.large_min, &ws);
+                         o.large_min, o.chunks_per_cta, &ws);
 }
 
 int zsort_release(void)
@@ -862,6 +875,8 @@ int zsort_pairs_noalloc(uint64_t *keys, uint32_t *vals, uint64_t n, int32_t *sta
     P.sample = o.sample;
     P.mapper = o.mapper;
     P.guard_level = o.guard_level;
+    P.leaf_cap = o.leaf_cap;
+    P.chunks_per_cta = o.chunks_per_cta;
     P.fallback_ratio = o.fallback_ratio;
     P.seed = o.seed;
     P.wait_ns = (unsigned long long)o.wait_limit_ms * 1000000ull;

@@ -132,6 +132,7 @@ struct Params {
     uint32_t traincap;
     // options
     uint32_t kmax, leaf_target, large_min, learn_min, sample, mapper, guard_level;
+    uint32_t leaf_cap, chunks_per_cta;
     float fallback_ratio;
     unsigned long long seed;
     unsigned long long wait_ns;
@@ -726,13 +727,37 @@ __device__ __forceinline__ void mbar_expect_arrive(unsigned long long *bar, uint
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
 }
+// L2 policy for data read once (streamed tiles, leaves): evicted first, so
+// that the stream does not push out the partly written output lines (the
+// write fronts of the scatter), which would then be written to HBM in parts.
+__device__ __forceinline__ unsigned long long policy_evict_first()
+{
+    unsigned long long pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ unsigned long long policy_evict_last()
+{
+    unsigned long long pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, unsigned long long *bar)
 {
     asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
             smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy_evict_first())
         : "memory");
+}
+// Scatter stores with an L2 policy (the write fronts).
+__device__ __forceinline__ void st_front(uint64_t *p, unsigned long long v, unsigned long long pol)
+{
+    asm volatile("st.global.L2::cache_hint.u64 [%0], %1, %2;" ::"l"(p), "l"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void st_front(uint32_t *p, uint32_t v, unsigned long long pol)
+{
+    asm volatile("st.global.L2::cache_hint.u32 [%0], %1, %2;" ::"l"(p), "r"(v), "l"(pol) : "memory");
 }
 // Hint: bring [src, src + bytes) into L2 (16-byte aligned address and size).
 __device__ __forceinline__ void bulk_prefetch_l2(const void *src, uint32_t bytes)

@@ -153,12 +153,14 @@ __device__ __forceinline__ uint32_t choose_k(const Params &P, uint32_t len)
 }
 
 // Tiles per chunk task of a large (sub)array of len elements: chunks in
-// proportion to its share of the call's n, about eight per CTA of the grid
-// over a whole level (so one level needs ~8 * nctas look-back rows in all;
-// eight keep the tail of a phase short), at least four tiles each.
+// proportion to its share of the call's n, about chunks_per_cta (default 8)
+// per CTA of the grid over a whole level (so one level needs about
+// chunks_per_cta * nctas look-back rows in all; more chunks shorten the tail
+// of a phase), at least four tiles each.
 __device__ __forceinline__ uint32_t choose_chunk_tiles(const Params &P, uint32_t tiles, uint32_t len)
 {
-    const unsigned long long want = ((unsigned long long)8 * P.nctas * len + P.n - 1) / P.n;
+    const unsigned long long want =
+        ((unsigned long long)P.chunks_per_cta * P.nctas * len + P.n - 1) / P.n;
     const uint32_t target = (uint32_t)(want < 1 ? 1 : want);
     const uint32_t ct = (tiles + target - 1) / target;
     return ct < 4u ? 4u : ct;
@@ -408,6 +410,9 @@ __device__ __noinline__ void scatter_stream(const Params &P, SmemTile &s, Pipe &
     const MapK mk = map_regs(s.map);
     const uint32_t k = mk.k;
     const bool stage_b = mk.kind == MAP_PWL;
+    // the runs written per tile end inside lines that the next tile (or the
+    // neighbouring chunk) completes: keep those lines in L2 until then
+    const unsigned long long pol_front = policy_evict_last();
     rank_zero_warp(k, s);
     if (bulk && threadIdx.x == 0)
         stream_issue<true>(P, s, 0, srck, srcv, start, (uint32_t)min(len, (unsigned long long)TILE));
@@ -478,8 +483,8 @@ __device__ __noinline__ void scatter_stream(const Params &P, SmemTile &s, Pipe &
             const uint32_t q = stage_b ? (uint32_t)s.bkt[p] : map_key(mk, s.map, key);
             const uint32_t rel = s.gdelta[q] + p;
             if (rel < seglen) {
-                __stcg(dstk + rel, key);
-                __stcg(dstv + rel, sv[p]);
+                st_front(dstk + rel, key, pol_front);
+                st_front(dstv + rel, sv[p], pol_front);
             } else {
                 set_error(P, ST_INTERNAL);
             }
@@ -505,7 +510,7 @@ __device__ void scatter_dispatch(const Params &P, SmemTile &s, Pipe &pp, const u
 // ------------------------------------------------------------ children
 // After a partition of the (sub)array at absolute offset poff: bucket counts
 // in s.hist[0..k), starts (relative) in s.bs[0..k).  Consecutive small
-// buckets are grouped into leaves of at most LEAF_CAP elements (sorting a
+// buckets are grouped into leaves of at most leaf_cap (<= LEAF_CAP) elements (sorting a
 // group of whole, ordered buckets gives the same result as sorting each);
 // larger buckets become medium or large (sub)arrays of the next level.
 __device__ __noinline__ void classify_children(const Params &P, unsigned long long poff, uint32_t k,
@@ -517,7 +522,7 @@ __device__ __noinline__ void classify_children(const Params &P, unsigned long lo
         for (uint32_t b = 0; b < k; b++) {
             uint32_t c = s.hist[b];
             if (c == 0) continue;
-            if (c > (uint32_t)LEAF_CAP) {
+            if (c > P.leaf_cap) {
                 if (glen) {
                     L.leaf_off[nl] = gstart;
                     L.leaf_len[nl++] = glen;
@@ -531,7 +536,7 @@ __device__ __noinline__ void classify_children(const Params &P, unsigned long lo
                     L.lg_len[ng++] = c;
                 }
             } else {
-                if (glen + c > (uint32_t)LEAF_CAP) {
+                if (glen + c > P.leaf_cap) {
                     L.leaf_off[nl] = gstart;
                     L.leaf_len[nl++] = glen;
                     glen = 0;
