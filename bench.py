@@ -43,6 +43,40 @@ UNIT = "pairs/s"
 BYTES_PER_PAIR = 12
 
 
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_2605_14419_gb300", "csrc", f)
+                  for f in ("zsort.cu", "zsort_device.cuh", "zsort_tasks.cuh")]
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "k_persistent_bench_2p26.md")
+
+
+def kernel_source_hash() -> str:
+    """sha256 over the persistent kernel's sources (the code the DRAM counters describe)."""
+    import hashlib
+
+    h = hashlib.sha256()
+    for path in KERNEL_SOURCES:
+        with open(path, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def measured_traffic_per_pair():
+    """DRAM bytes per pair of k_persistent from the committed ncu summary, or
+    None when the kernel sources changed since those counters were taken."""
+    try:
+        with open(TRAFFIC_PROFILE) as f:
+            text = f.read()
+    except OSError:
+        return None, "no profile"
+    fields = dict(line.split(":", 1) for line in text.splitlines() if line.startswith(("source_sha256:",
+                                                                                          "dram_bytes_per_pair:")))
+    if fields.get("source_sha256", "").strip() != kernel_source_hash():
+        return None, "kernel changed since the ncu capture"
+    try:
+        return float(fields["dram_bytes_per_pair"]), "ncu capture at n=2^26, scaled by pairs"
+    except (KeyError, ValueError):
+        return None, "no figure"
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -376,7 +410,8 @@ def main():
         t = torch.tensor([total_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    pairs_per_step = n * len(bufs)
+    n_arrays = len(bufs)
+    pairs_per_step = n * n_arrays
     value = world * pairs_per_step * args.steps / (total_ms / 1e3)
     kernel_ms = [a[0] for step in res for a in step]
     kernel_bytes = [a[1] for step in res for a in step]
@@ -384,6 +419,7 @@ def main():
     avg_bytes = sum(kernel_bytes) / len(kernel_bytes)
     peak, peak_kind = load_peaks()
     achieved = avg_bytes / (avg_ms / 1e3) / 1e9
+    traffic_pp, traffic_note = measured_traffic_per_pair()
     last_stats = [a[2] for a in res[-1]]
     # correctness of the last timed outputs (cheap device-side checks)
     for (name, kd, _), (kb, vb) in zip(pristine, bufs):
@@ -467,13 +503,15 @@ def main():
             "parallelism": "replicas" if world > 1 else "single GPU",
         },
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                     "frac": achieved / peak,
+                     "traffic": None if traffic_pp is None else traffic_pp * n, "traffic_note": traffic_note,
+                     "peak_kind": peak_kind,
                      "kernel": "k_persistent (whole zsort_pairs call)",
                      "algorithmic_bytes_per_launch": avg_bytes, "avg_launch_ms": avg_ms},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "clocks": clk,
-        "gpu_launches": 3 * len(bufs) * args.steps,
+        "gpu_launches": 3 * n_arrays * args.steps,
         "per_array": [{"array": name, "ms": round(sum(step[i][0] for step in res) / len(res), 3),
                        "bytes_per_pair": round(last_stats[i]["bytes_algorithmic"] / n, 2),
                        "max_level": last_stats[i]["max_level"],
