@@ -54,7 +54,8 @@ __global__ void __launch_bounds__(BLOCK, 2) k_persistent(const __grid_constant__
             const uint32_t tile = tile0 + j;
             switch (type) {
             case T_LSTATS: task_lstats(P, arg, tile, s, pp); break;
-            case T_LTRAIN: task_ltrain(P, arg, s); break;
+            case T_LSAMPLE: task_lsample(P, arg, s); break;
+            case T_LFIT: task_lfit(P, arg, s); break;
             case T_LHIST: task_lhist(P, arg, tile, s, pp); break;
             case T_LSCATTER: task_lscatter(P, arg, tile, s, pp); break;
             case T_MPART: task_mpart(P, load_item(P, arg + tile), s, pp); break;
@@ -71,8 +72,9 @@ __global__ void __launch_bounds__(BLOCK, 2) k_persistent(const __grid_constant__
         }
         if (threadIdx.x == 0) {
             unsigned long long t1 = globaltimer();
-            atomicAdd(&P.ctl->task_ns[type & 7], t1 - t_task0);
-            atomicAdd(&P.ctl->task_cnt[type & 7], (unsigned long long)count);
+            const uint32_t ti = type == T_LFIT ? (uint32_t)T_LSAMPLE : (type & 7u);  // both: learned map
+            atomicAdd(&P.ctl->task_ns[ti], t1 - t_task0);
+            atomicAdd(&P.ctl->task_cnt[ti], (unsigned long long)count);
             __threadfence();
             uint32_t old = atomicAdd(&P.tdone[e], count);
             s.flag2 = (old + count == ntiles) ? 1u : 0u;
@@ -86,7 +88,7 @@ __global__ void __launch_bounds__(BLOCK, 2) k_persistent(const __grid_constant__
             case T_LSTATS: lstats_done(P, arg, s); break;
             case T_LHIST: lhist_done(P, arg, s); break;
             case T_LSCATTER: lscatter_done(P, arg, s); break;
-            default: break;  // LTRAIN publishes its successor itself
+            default: break;  // LSAMPLE and LFIT publish their successors themselves
             }
             __syncthreads();
             if (threadIdx.x == 0) {
@@ -157,7 +159,9 @@ __global__ void k_init_segments(Params P, const uint64_t *off, unsigned long lon
             S->level = 0;
             S->buf = 0;
             S->kind = MAP_Z;
-            S->train_slot = INVALID;
+            S->train_slot = take_train_slot(P, (uint32_t)len, kk, 0);
+            S->join = 2;
+            S->max_learned = S->max_z = 0;
             for (uint32_t q = 0; q < kk; q++) P.counts[(size_t)sid * NB_MAX + q] = 0;
             return;
         }
@@ -192,6 +196,14 @@ __global__ void k_init_publish(Params P, unsigned long long nseg)
             C->error = (unsigned int)ST_CAPACITY;
             C->pending = 0;
             return;
+        }
+        if (P.segs[sid].train_slot != INVALID) {  // the sample runs beside the statistics
+            if (e + 1 >= P.qcap) {
+                C->error = (unsigned int)ST_CAPACITY;
+                C->pending = 0;
+                return;
+            }
+            q_write(P, e++, T_LSAMPLE, sid, 1);
         }
         q_write(P, e++, T_LSTATS, sid, P.segs[sid].chunks);
     }
@@ -300,7 +312,7 @@ Plan make_plan(unsigned long long n, unsigned long long nseg, unsigned long long
     p.off_bstart = take(p.segcap * NB_MAX * 4);
     p.off_status = take(p.statuscap * 4);
     p.off_pwl = take(p.segcap * PWL_STRIDE * 4);
-    p.off_train = take(p.traincap * 2 * SAMPLE_MAX * 4);
+    p.off_train = take(p.traincap * 2 * SAMPLE_MAX * 8);
     p.total = o;
     return p;
 }
@@ -384,7 +396,7 @@ int get_workspace(cudaStream_t stream, unsigned long long n, unsigned long long 
         P.status = reinterpret_cast<uint32_t *>(b + p.off_status);
         P.statuscap = p.statuscap;
         P.pwl = reinterpret_cast<float *>(b + p.off_pwl);
-        P.trainbuf = reinterpret_cast<uint32_t *>(b + p.off_train);
+        P.trainbuf = reinterpret_cast<unsigned long long *>(b + p.off_train);
         P.traincap = (uint32_t)p.traincap;
         ws->epoch = 0;
     }
@@ -554,7 +566,7 @@ constexpr NaLayout na_layout()
     L.bstart = o; o = na_align(o + L.segcap * NB_MAX * 4);
     L.status = o; o = na_align(o + L.statuscap * 4);
     L.pwl = o; o = na_align(o + L.segcap * PWL_STRIDE * 4);
-    L.train = o; o = na_align(o + L.traincap * 2 * SAMPLE_MAX * 4);
+    L.train = o; o = na_align(o + L.traincap * 2 * SAMPLE_MAX * 8);
     L.total = o;
     return L;
 }
@@ -794,7 +806,7 @@ int zsort_map_buckets(const uint64_t *keys, uint64_t n, const zsort_opts *opts, 
     info->escale = S.escale;
     info->learned_max_load = S.max_learned;
     info->zscore_max_load = S.max_z;
-    if (S.train_slot != INVALID) {
+    if (S.train_slot != INVALID && S.max_learned > 0) {  // the fit ran (it sets the loads)
         float t[PWL_STRIDE];
         ce = cudaMemcpy(t, ws->P.pwl, sizeof(t), cudaMemcpyDeviceToHost);
         if (ce != cudaSuccess) return cuda_err(ce);
@@ -866,7 +878,7 @@ int zsort_pairs_noalloc(uint64_t *keys, uint32_t *vals, uint64_t n, int32_t *sta
     P.status = reinterpret_cast<uint32_t *>(b + NA.status);
     P.statuscap = NA.statuscap;
     P.pwl = reinterpret_cast<float *>(b + NA.pwl);
-    P.trainbuf = reinterpret_cast<uint32_t *>(b + NA.train);
+    P.trainbuf = reinterpret_cast<unsigned long long *>(b + NA.train);
     P.traincap = (uint32_t)NA.traincap;
     P.kmax = o.kmax;
     P.leaf_target = o.leaf_target;

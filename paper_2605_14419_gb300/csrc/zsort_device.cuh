@@ -44,13 +44,16 @@ enum MapKind : uint32_t { MAP_Z = 0, MAP_PWL = 1, MAP_RANGE = 2 };
 enum TaskType : uint32_t {
     T_NONE = 0,
     T_LSTATS = 1,    // large segment: statistics tile
-    T_LTRAIN = 2,    // large segment: learned-map training (one CTA)
+    T_LSAMPLE = 2,   // large segment: learned-map sample, drawn and sorted (one CTA,
+                     // runs beside the statistics tiles)
     T_LHIST = 3,     // large segment: histogram tile
     T_LSCATTER = 4,  // large segment: look-back stable scatter tile
     T_MPART = 5,     // medium segment: whole partition pass by one CTA
     T_FINISH = 6,    // leaf (group of small buckets): shared-memory sort
     T_COPY = 7,      // all-equal large segment living in scratch: copy back
-    T_DUMP = 8       // map inspection: bucket of every key of a chunk
+    T_DUMP = 8,      // map inspection: bucket of every key of a chunk
+    T_LFIT = 9       // large segment: learned-map breakpoints and load test (one CTA,
+                     // after both the statistics and the sample)
 };
 
 // ---------------------------------------------------------------- records
@@ -72,7 +75,10 @@ struct Seg {
     uint32_t max_learned, max_z; // load test: largest sample bucket per map
     uint32_t chunk_tiles;        // tiles per chunk task
     uint32_t chunks;             // chunk tasks per phase
-    uint32_t pad[3];
+    uint32_t join;               // learned map: statistics and sample still running (2, 1, 0)
+    uint32_t next_type, next_nt; // learned map: the task the last of the two publishes
+    uint32_t sort_sel;           // learned map: sorted sample in buffer 0 or 1 of the slot
+    unsigned long long smin;     // learned map: smallest sampled key
 };
 
 // A leaf group or a medium segment.
@@ -128,7 +134,7 @@ struct Params {
     uint32_t *plan_out;          // map inspection: bucket of every key (else null)
     uint32_t user_aligned;       // caller's keys and vals 16-byte aligned: bulk copies allowed
     float *pwl;         // segcap * PWL_STRIDE: breakpoints q[0..P], reciprocals r[0..P)
-    uint32_t *trainbuf; // traincap * 2 * SAMPLE_MAX
+    unsigned long long *trainbuf; // traincap * 2 * SAMPLE_MAX sampled keys (ping-pong)
     uint32_t traincap;
     // options
     uint32_t kmax, leaf_target, large_min, learn_min, sample, mapper, guard_level;
@@ -459,7 +465,7 @@ __device__ __forceinline__ void range_params(unsigned long long range, uint32_t 
 struct ChildList {
     uint32_t leaf_off[NB_MAX], leaf_len[NB_MAX];
     uint32_t med_off[NB_MAX], med_len[NB_MAX];
-    uint32_t lg_off[NB_MAX], lg_len[NB_MAX], lg_need[NB_MAX];
+    uint32_t lg_off[NB_MAX], lg_len[NB_MAX], lg_need[NB_MAX], lg_slot[NB_MAX];
 };
 
 struct TileBuf {
@@ -494,6 +500,7 @@ struct SmemTile {
     unsigned long long red64[WARPS * 2];
 };
 static_assert(sizeof(LeafBuf) <= sizeof(TileBuf) * 2, "leaf fits the tile buffers");
+static_assert(sizeof(ChildList) <= sizeof(TileBuf) * 2, "child lists fit the tile buffers");
 
 // ------------------------------------------------------------ block scan
 // Exclusive scan of in[0..nb) into out (may alias); returns the total.

@@ -152,6 +152,22 @@ __device__ __forceinline__ uint32_t choose_k(const Params &P, uint32_t len)
     return k > P.kmax ? P.kmax : k;
 }
 
+// A large (sub)array of len elements with k buckets at depth level learns
+// its map (the statistics decide later whether Eq. 1 applies at all).
+__device__ __forceinline__ bool wants_learned_map(const Params &P, uint32_t len, uint32_t k, uint32_t level)
+{
+    return P.mapper == 1 && len >= P.learn_min && P.sample <= len && k >= (uint32_t)PWL_P && level < P.guard_level;
+}
+
+// Takes a training slot for a new large (sub)array (any thread): INVALID if
+// none is left, then the (sub)array keeps Eq. 1.
+__device__ __forceinline__ uint32_t take_train_slot(const Params &P, uint32_t len, uint32_t k, uint32_t level)
+{
+    if (!wants_learned_map(P, len, k, level)) return INVALID;
+    const uint32_t slot = atomicAdd(&P.ctl->train_alloc, 1u);
+    return slot < P.traincap ? slot : INVALID;
+}
+
 // Tiles per chunk task of a large (sub)array of len elements: chunks in
 // proportion to its share of the call's n, about chunks_per_cta (default 8)
 // per CTA of the grid over a whole level (so one level needs about
@@ -622,7 +638,11 @@ __device__ __noinline__ void classify_children(const Params &P, unsigned long lo
         S->level = child_level;
         S->buf = child_buf;
         S->kind = MAP_Z;
-        S->train_slot = INVALID;
+        const uint32_t slot = take_train_slot(P, len, S->k, child_level);
+        S->train_slot = slot;
+        S->join = 2;
+        S->max_learned = S->max_z = 0;
+        L.lg_slot[g] = slot;
     }
     for (uint32_t g = 0; g < nok; g++) {
         const uint32_t kk = choose_k(P, L.lg_len[g]);
@@ -631,10 +651,16 @@ __device__ __noinline__ void classify_children(const Params &P, unsigned long lo
     __threadfence();  // descriptors, items and counters before the entries are published
     __syncthreads();
     if (threadIdx.x == 0) {
-        const uint32_t cnt = (nl > 0) + (nm > 0) + nok;
+        uint32_t nsample = 0;
+        for (uint32_t g = 0; g < nok; g++) nsample += L.lg_slot[g] != INVALID;
+        const uint32_t cnt = (nl > 0) + (nm > 0) + nok + nsample;
         const uint32_t e = q_reserve(P, cnt);
         if (e != INVALID && cnt) {
             uint32_t j = e;
+            // the learned-map samples first: each is one CTA's long task that
+            // runs beside its (sub)array's statistics tiles
+            for (uint32_t g = 0; g < nok; g++)
+                if (L.lg_slot[g] != INVALID) q_write(P, j++, T_LSAMPLE, sid0 + g, 1);
             if (nl) q_write(P, j++, T_FINISH, base, nl);
             if (nm) q_write(P, j++, T_MPART, base + nl, nm);
             for (uint32_t g = 0; g < nok; g++) {
@@ -697,6 +723,30 @@ __device__ __noinline__ void task_lstats(const Params &P, uint32_t sid, uint32_t
     }
 }
 
+// Thread 0: publishes one entry (nothing for type T_NONE).
+__device__ void publish1(const Params &P, uint32_t type, uint32_t arg, uint32_t nt)
+{
+    if (type == T_NONE) return;
+    const uint32_t e = q_reserve(P, 1);
+    if (e != INVALID) {
+        q_write(P, e, type, arg, nt);
+        q_release_all(P, e, 1);
+    }
+}
+
+// Thread 0, for a (sub)array with a training slot: the statistics and the
+// sample task each call this once when done; the second one publishes the
+// successor that the statistics chose (written before the first call).
+__device__ void learned_join(const Params &P, uint32_t sid)
+{
+    Seg *S = &P.segs[sid];
+    __threadfence();
+    if (atomicSub(&S->join, 1u) == 1u) {
+        __threadfence();
+        publish1(P, __ldcg(&S->next_type), sid, __ldcg(&S->next_nt));
+    }
+}
+
 __device__ __noinline__ void lstats_done(const Params &P, uint32_t sid, SmemTile &s)
 {
     if (threadIdx.x == 0) {
@@ -704,6 +754,8 @@ __device__ __noinline__ void lstats_done(const Params &P, uint32_t sid, SmemTile
         const unsigned long long mn = __ldcg(&S->mn), mx = __ldcg(&S->mx);
         const uint32_t len = __ldcg(&S->len), level = __ldcg(&S->level);
         const uint32_t sbuf = __ldcg(&S->buf), sk = __ldcg(&S->k), chunks = __ldcg(&S->chunks);
+        const uint32_t slot = __ldcg(&S->train_slot);
+        uint32_t next = T_NONE, nt = 0;
         if (mn == mx && P.plan_out) {  // inspection of identical keys: all in bucket 0
             S->kind = MAP_RANGE;
             S->rshift = 0;
@@ -714,18 +766,12 @@ __device__ __noinline__ void lstats_done(const Params &P, uint32_t sid, SmemTile
                 m0.kind = MAP_RANGE;
                 record_top(P, m0, mn, mx, 0.0, 0.0);
             }
-            uint32_t e = q_reserve(P, 1);
-            if (e != INVALID) {
-                q_write(P, e, T_DUMP, sid, chunks);
-                q_release_all(P, e, 1);
-            }
+            next = T_DUMP;
+            nt = chunks;
         } else if (mn == mx) {  // a set of identical keys is sorted (Alg. 1 early exit)
             if (sbuf) {
-                uint32_t e = q_reserve(P, 1);
-                if (e != INVALID) {
-                    q_write(P, e, T_COPY, sid, (len + LEAF_CAP - 1) / LEAF_CAP);
-                    q_release_all(P, e, 1);
-                }
+                next = T_COPY;
+                nt = (len + LEAF_CAP - 1) / LEAF_CAP;
                 atomicAdd(&P.ctl->n_copies, 1ull);
             }
         } else {
@@ -743,79 +789,174 @@ __device__ __noinline__ void lstats_done(const Params &P, uint32_t sid, SmemTile
             S->rshift = m.rshift;
             S->rmult = m.rmult;
             if (level == 0 && sid == 0) record_top(P, m, mn, mx, mean_d, sd);
-            uint32_t next = P.plan_out ? T_DUMP : T_LHIST, nt = chunks;
-            if (m.kind == MAP_Z && P.mapper == 1 && len >= P.learn_min && P.sample <= len &&
-                sk >= (uint32_t)PWL_P) {
-                uint32_t slot = atomicAdd(&P.ctl->train_alloc, 1u);
-                if (slot < P.traincap) {
-                    S->train_slot = slot;
-                    next = T_LTRAIN;
-                    nt = 1;
-                }
+            next = P.plan_out ? T_DUMP : T_LHIST;
+            nt = chunks;
+            if (m.kind == MAP_Z && slot != INVALID) {
+                next = T_LFIT;
+                nt = 1;
             }
-            uint32_t e = q_reserve(P, 1);
-            if (e != INVALID) {
-                q_write(P, e, next, sid, nt);
-                q_release_all(P, e, 1);
-            }
+        }
+        if (slot != INVALID) {
+            S->next_type = next;
+            S->next_nt = nt;
+            learned_join(P, sid);
+        } else {
+            publish1(P, next, sid, nt);
         }
     }
 }
 
-// ------------------------------------------------------------ LTRAIN
-// One stable LSD pass (8-bit digit at `shift`) of m uint32 values, src -> dst,
-// by one CTA: histogram, scan, then tile by tile in input order.
-__device__ void cta_lsd_pass(const uint32_t *src, uint32_t *dst, uint32_t m, uint32_t shift, SmemTile &s)
+// ------------------------------------------------------------ LSAMPLE / LFIT
+// Exact LSD radix sort of m 64-bit keys by key - base (8-bit digits, `passes`
+// of them) by one CTA, A and B ping-pong in global memory (L2 resident);
+// returns 1 if the result is in B.  One read pass builds the histograms of
+// all digits; a digit that every key shares is skipped (its pass would be
+// the identity).  Each pass streams tiles of 2048 keys in input order, the
+// next tile's loads in flight while the current one is ranked (ballots,
+// stable), and every key goes straight to its bucket's running cursor.
+__device__ uint32_t cta_lsd_sort64(unsigned long long *A, unsigned long long *B, uint32_t m,
+                                   unsigned long long base, uint32_t passes, SmemTile &s)
 {
-    for (int q = threadIdx.x; q < 256; q += BLOCK) s.hist[q] = 0;
+    uint32_t *h8 = reinterpret_cast<uint32_t *>(&s.u);  // [8][256] digit histograms
+    for (uint32_t q = threadIdx.x; q < 8 * 256; q += BLOCK) h8[q] = 0;
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < m; i += BLOCK) atomicAdd(&s.hist[(__ldcg(src + i) >> shift) & 255u], 1u);
-    __syncthreads();
-    block_exclusive_scan(s.hist, s.cursor, 256, s.wsum);
-    for (uint32_t t0 = 0; t0 < m; t0 += TILE) {
-        const uint32_t cnt = min((uint32_t)TILE, m - t0);
-        uint32_t v[IPT], b[IPT], pos[IPT];
+    for (uint32_t i0 = 0; i0 < m; i0 += TILE) {
+        unsigned long long x[IPT];
 #pragma unroll
         for (int i = 0; i < IPT; i++) {
-            uint32_t p = slot_index(i);
-            v[i] = p < cnt ? __ldcg(src + t0 + p) : 0u;
-            b[i] = (v[i] >> shift) & 255u;
+            const uint32_t p = i0 + threadIdx.x + i * BLOCK;
+            x[i] = p < m ? __ldcg(A + p) - base : 0ull;
         }
-        tile_rank<IPT, 8>(b, pos, 256, cnt, s);
 #pragma unroll
         for (int i = 0; i < IPT; i++)
-            if (pos[i] != INVALID) __stcg(dst + s.cursor[b[i]] + pos[i] - s.tstart[b[i]], v[i]);
+            if (i0 + threadIdx.x + i * BLOCK < m)
+                for (uint32_t d = 0; d < passes; d++) atomicAdd(&h8[d * 256 + ((x[i] >> (8 * d)) & 255u)], 1u);
+    }
+    __syncthreads();
+    uint32_t sel = 0;
+    const unsigned long long *src = A;
+    unsigned long long *dst = B;
+    for (uint32_t d = 0; d < passes; d++) {
+        // skip a digit shared by every key
+        const uint32_t c = h8[d * 256 + threadIdx.x];
+        if (__syncthreads_or(c == m)) continue;
+        block_exclusive_scan(h8 + d * 256, s.cursor, 256, s.wsum);
+        rank_zero_warp(256, s);
+        const uint32_t nt = (m + TILE - 1) / TILE;
+        unsigned long long nx[IPT];
+#pragma unroll
+        for (int i = 0; i < IPT; i++) {
+            const uint32_t p = slot_index(i);
+            nx[i] = p < m ? __ldcg(src + p) : 0ull;
+        }
+        for (uint32_t t = 0; t < nt; t++) {
+            const uint32_t t0 = t * TILE, cnt = min((uint32_t)TILE, m - t0);
+            unsigned long long v[IPT];
+            uint32_t b[IPT], pos[IPT], peers[IPT];
+#pragma unroll
+            for (int i = 0; i < IPT; i++) {
+                v[i] = nx[i];
+                b[i] = (uint32_t)((v[i] - base) >> (8 * d)) & 255u;
+            }
+            if (t + 1 < nt) {
+#pragma unroll
+                for (int i = 0; i < IPT; i++) {
+                    const uint32_t p = t0 + TILE + slot_index(i);
+                    nx[i] = p < m ? __ldcg(src + p) : 0ull;
+                }
+            }
+            rank_peers<IPT, 8>(b, cnt, peers);
+            rank_leaders<IPT>(b, peers, pos, s);
+            __syncthreads();
+            rank_scan<true>(256, s);
+            rank_place<IPT>(b, pos, s);
+            rank_zero_warp(256, s);
+#pragma unroll
+            for (int i = 0; i < IPT; i++)
+                if (pos[i] != INVALID) __stcg(dst + s.gdelta[b[i]] + pos[i], v[i]);
+        }
         __syncthreads();
-        for (int q = threadIdx.x; q < 256; q += BLOCK) s.cursor[q] += s.tcount[q];
-        __syncthreads();
+        sel ^= 1u;
+        const unsigned long long *t2 = dst;
+        dst = const_cast<unsigned long long *>(src);
+        src = t2;
+    }
+    return sel;
+}
+
+// Learned map, first half (beside the statistics tiles): the sample of
+// P.sample keys at the stratified positions, then its exact sort.  The keys
+// are sorted as they are (key - smallest sampled key, over the bytes that
+// vary): the normalisation u = fl32(key - min) * 2^-E is monotone, so the
+// sorted keys give the sorted normalised sample once min and max are known.
+__device__ __noinline__ void task_lsample(const Params &P, uint32_t sid, SmemTile &s)
+{
+    Seg *S = &P.segs[sid];
+    const unsigned long long off = __ldcg(&S->off);
+    const uint32_t len = __ldcg(&S->len), buf = __ldcg(&S->buf), slot = __ldcg(&S->train_slot);
+    const uint32_t m = P.sample;
+    unsigned long long *A = P.trainbuf + (size_t)slot * 2 * SAMPLE_MAX;
+    unsigned long long *B = A + SAMPLE_MAX;
+    const uint64_t *src = keys_of(P, buf) + off;
+    unsigned long long mn = ~0ull, mx = 0ull;
+    constexpr int U = 8;  // independent loads in flight per thread
+    for (uint32_t i0 = 0; i0 < m; i0 += BLOCK * U) {
+        unsigned long long x[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const uint32_t i = i0 + threadIdx.x + u * BLOCK;
+            x[u] = i < m ? __ldcg(src + sample_pos(P.seed, len, m, i)) : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const uint32_t i = i0 + threadIdx.x + u * BLOCK;
+            if (i < m) {
+                __stcg(A + i, x[u]);
+                mn = x[u] < mn ? x[u] : mn;
+                mx = x[u] > mx ? x[u] : mx;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const unsigned long long a = shfl_down64(mn, o), b2 = shfl_down64(mx, o);
+        mn = a < mn ? a : mn;
+        mx = b2 > mx ? b2 : mx;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        s.red64[threadIdx.x >> 5] = mn;
+        s.red64[WARPS + (threadIdx.x >> 5)] = mx;
+    }
+    __syncthreads();
+    mn = s.red64[0];
+    mx = s.red64[WARPS];
+    for (int w = 1; w < WARPS; w++) {
+        mn = s.red64[w] < mn ? s.red64[w] : mn;
+        mx = s.red64[WARPS + w] > mx ? s.red64[WARPS + w] : mx;
+    }
+    __syncthreads();
+    const uint32_t sel = cta_lsd_sort64(A, B, m, mn, (bitlen64(mx - mn) + 7) / 8, s);
+    __threadfence();  // the sorted sample before the join publishes the fit
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        S->smin = mn;
+        S->sort_sel = sel;
+        learned_join(P, sid);
     }
 }
 
-// Learned-map training: sample, exact sort of the normalised sample,
-// breakpoints at the 1/256 quantiles and their reciprocal widths, then the
-// load test that keeps Eq. 1 as the fallback.
-__device__ __noinline__ void task_ltrain(const Params &P, uint32_t sid, SmemTile &s)
+// Learned map, second half (after the statistics and the sample): breakpoints
+// at the 1/256 quantiles of the normalised sample and their reciprocal
+// widths, then the load test that keeps Eq. 1 as the fallback.
+__device__ __noinline__ void task_lfit(const Params &P, uint32_t sid, SmemTile &s)
 {
     Seg *S = &P.segs[sid];
-    const unsigned long long off = __ldcg(&S->off), mn = __ldcg(&S->mn), mx = __ldcg(&S->mx);
-    const uint32_t len = __ldcg(&S->len), buf = __ldcg(&S->buf), k = __ldcg(&S->k);
-    const uint32_t slot = __ldcg(&S->train_slot), chunks = __ldcg(&S->chunks);
+    const unsigned long long mn = __ldcg(&S->mn), mx = __ldcg(&S->mx);
+    const uint32_t k = __ldcg(&S->k), slot = __ldcg(&S->train_slot), chunks = __ldcg(&S->chunks);
     const float escale = __ldcg(&S->escale), zc = __ldcg(&S->zc);
     const uint32_t zsh = __ldcg(&S->zsh);
     const uint32_t m = P.sample;
-    uint32_t *A = P.trainbuf + (size_t)slot * 2 * SAMPLE_MAX;
-    uint32_t *B = A + SAMPLE_MAX;
-    const uint64_t *src = keys_of(P, buf) + off;
-    for (uint32_t i = threadIdx.x; i < m; i += BLOCK) {
-        const unsigned long long key = __ldcg(src + sample_pos(P.seed, len, m, i));
-        __stcg(A + i, __float_as_uint(__fmul_rn(u64_to_f32_rn(key - mn), escale)));
-    }
-    __syncthreads();
-    // non-negative floats order as their bit patterns
-    cta_lsd_pass(A, B, m, 0, s);
-    cta_lsd_pass(B, A, m, 8, s);
-    cta_lsd_pass(A, B, m, 16, s);
-    cta_lsd_pass(B, A, m, 24, s);
+    const unsigned long long *X = P.trainbuf + (size_t)slot * 2 * SAMPLE_MAX + (__ldcg(&S->sort_sel) ? SAMPLE_MAX : 0);
     if (threadIdx.x == 0) {
         s.map.mn = mn;
         s.map.kind = MAP_PWL;
@@ -833,7 +974,7 @@ __device__ __noinline__ void task_ltrain(const Params &P, uint32_t sid, SmemTile
         else if (j == PWL_P)
             q = __fmul_rn(u64_to_f32_rn(mx - mn), escale);
         else
-            q = __uint_as_float(__ldcg(A + (size_t)j * m / PWL_P));
+            q = __fmul_rn(u64_to_f32_rn(__ldcg(X + (size_t)j * m / PWL_P) - mn), escale);
         s.map.q[j] = q;
         t[j] = q;
     }
@@ -851,11 +992,22 @@ __device__ __noinline__ void task_ltrain(const Params &P, uint32_t sid, SmemTile
     build_pwl_bins(s.map);
     __syncthreads();
     // load test on the sample: largest learned bucket vs largest Eq. 1 bucket
-    for (uint32_t i = threadIdx.x; i < m; i += BLOCK) {
-        const unsigned long long d = __ldcg(src + sample_pos(P.seed, len, m, i)) - mn;
-        atomicAdd(&s.hist[pwl_bucket_u(s.map, __fmul_rn(u64_to_f32_rn(d), escale))], 1u);
-        const uint32_t bz = __float2uint_rz(__fmul_rn(__uint2float_rz((uint32_t)(d >> zsh)), zc));
-        atomicAdd(&s.cursor[bz < k ? bz : k - 1], 1u);
+    for (uint32_t i0 = 0; i0 < m; i0 += BLOCK * IPT) {
+        unsigned long long x[IPT];
+#pragma unroll
+        for (int u = 0; u < IPT; u++) {
+            const uint32_t i = i0 + threadIdx.x + u * BLOCK;
+            x[u] = i < m ? __ldcg(X + i) : mn;
+        }
+#pragma unroll
+        for (int u = 0; u < IPT; u++) {
+            if (i0 + threadIdx.x + u * BLOCK < m) {
+                const unsigned long long d = x[u] - mn;
+                atomicAdd(&s.hist[pwl_bucket_u(s.map, __fmul_rn(u64_to_f32_rn(d), escale))], 1u);
+                const uint32_t bz = __float2uint_rz(__fmul_rn(__uint2float_rz((uint32_t)(d >> zsh)), zc));
+                atomicAdd(&s.cursor[bz < k ? bz : k - 1], 1u);
+            }
+        }
     }
     __syncthreads();
     uint32_t ml = 0, mz = 0;
@@ -869,6 +1021,7 @@ __device__ __noinline__ void task_ltrain(const Params &P, uint32_t sid, SmemTile
         s.red64[threadIdx.x >> 5] = ml;
         s.red64[WARPS + (threadIdx.x >> 5)] = mz;
     }
+    __threadfence();  // the map tables before the histogram tasks are published
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int w = 1; w < WARPS; w++) {
@@ -881,11 +1034,7 @@ __device__ __noinline__ void task_ltrain(const Params &P, uint32_t sid, SmemTile
         S->max_z = mz;
         atomicAdd(ok ? &P.ctl->n_learn_ok : &P.ctl->n_learn_rej, 1ull);
         if (__ldcg(&S->level) == 0 && sid == 0) P.ctl->top_map = ok ? MAP_PWL : MAP_Z;
-        uint32_t e = q_reserve(P, 1);
-        if (e != INVALID) {
-            q_write(P, e, P.plan_out ? T_DUMP : T_LHIST, sid, chunks);
-            q_release_all(P, e, 1);
-        }
+        publish1(P, P.plan_out ? T_DUMP : T_LHIST, sid, chunks);
     }
 }
 
