@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(BLOCK, 2) k_persistent(const __grid_constant__
             const uint32_t tile = tile0 + j;
             switch (type) {
             case T_LSTATS: task_lstats(P, arg, tile, s, pp); break;
-            case T_LSAMPLE: task_lsample(P, arg, s); break;
+            case T_LSAMPLE: task_lsample(P, arg, tile, s); break;
             case T_LFIT: task_lfit(P, arg, s); break;
             case T_LHIST: task_lhist(P, arg, tile, s, pp); break;
             case T_LSCATTER: task_lscatter(P, arg, tile, s, pp); break;
@@ -160,7 +160,7 @@ __global__ void k_init_segments(Params P, const uint64_t *off, unsigned long lon
             S->buf = 0;
             S->kind = MAP_Z;
             S->train_slot = take_train_slot(P, (uint32_t)len, kk, 0);
-            S->join = 2;
+            S->join = SAMPLE_RUNS + 1;
             S->max_learned = S->max_z = 0;
             for (uint32_t q = 0; q < kk; q++) P.counts[(size_t)sid * NB_MAX + q] = 0;
             return;
@@ -203,7 +203,7 @@ __global__ void k_init_publish(Params P, unsigned long long nseg)
                 C->pending = 0;
                 return;
             }
-            q_write(P, e++, T_LSAMPLE, sid, 1);
+            q_write(P, e++, T_LSAMPLE, sid, SAMPLE_RUNS);
         }
         q_write(P, e++, T_LSTATS, sid, P.segs[sid].chunks);
     }

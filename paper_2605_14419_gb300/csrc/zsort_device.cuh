@@ -27,6 +27,7 @@ constexpr int NB_MAX = 1024;              // buckets per partition pass
 constexpr int RANK_SMALL = BLOCK;         // leaves this small are ranked by counting
 constexpr int PWL_P = 256;                // pieces of the learned map
 constexpr int SAMPLE_MAX = 65536;         // largest training sample
+constexpr int SAMPLE_RUNS = 8;            // the sample is sorted as this many runs, one CTA each
 constexpr int MIN_K = 16;                 // fewest buckets of a partition pass
 constexpr int MAX_LEVEL = 48;             // hard bound on the partition depth
 constexpr uint32_t INVALID = 0xFFFFFFFFu;
@@ -44,8 +45,8 @@ enum MapKind : uint32_t { MAP_Z = 0, MAP_PWL = 1, MAP_RANGE = 2 };
 enum TaskType : uint32_t {
     T_NONE = 0,
     T_LSTATS = 1,    // large segment: statistics tile
-    T_LSAMPLE = 2,   // large segment: learned-map sample, drawn and sorted (one CTA,
-                     // runs beside the statistics tiles)
+    T_LSAMPLE = 2,   // large segment: learned-map sample, drawn and sorted as
+                     // SAMPLE_RUNS runs (one CTA each, beside the statistics tiles)
     T_LHIST = 3,     // large segment: histogram tile
     T_LSCATTER = 4,  // large segment: look-back stable scatter tile
     T_MPART = 5,     // medium segment: whole partition pass by one CTA
@@ -75,10 +76,9 @@ struct Seg {
     uint32_t max_learned, max_z; // load test: largest sample bucket per map
     uint32_t chunk_tiles;        // tiles per chunk task
     uint32_t chunks;             // chunk tasks per phase
-    uint32_t join;               // learned map: statistics and sample still running (2, 1, 0)
+    uint32_t join;               // learned map: statistics + sample runs still running
     uint32_t next_type, next_nt; // learned map: the task the last of the two publishes
-    uint32_t sort_sel;           // learned map: sorted sample in buffer 0 or 1 of the slot
-    unsigned long long smin;     // learned map: smallest sampled key
+    uint32_t pad1;
 };
 
 // A leaf group or a medium segment.

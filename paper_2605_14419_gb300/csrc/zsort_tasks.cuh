@@ -640,7 +640,7 @@ __device__ __noinline__ void classify_children(const Params &P, unsigned long lo
         S->kind = MAP_Z;
         const uint32_t slot = take_train_slot(P, len, S->k, child_level);
         S->train_slot = slot;
-        S->join = 2;
+        S->join = SAMPLE_RUNS + 1;
         S->max_learned = S->max_z = 0;
         L.lg_slot[g] = slot;
     }
@@ -660,7 +660,7 @@ __device__ __noinline__ void classify_children(const Params &P, unsigned long lo
             // the learned-map samples first: each is one CTA's long task that
             // runs beside its (sub)array's statistics tiles
             for (uint32_t g = 0; g < nok; g++)
-                if (L.lg_slot[g] != INVALID) q_write(P, j++, T_LSAMPLE, sid0 + g, 1);
+                if (L.lg_slot[g] != INVALID) q_write(P, j++, T_LSAMPLE, sid0 + g, SAMPLE_RUNS);
             if (nl) q_write(P, j++, T_FINISH, base, nl);
             if (nm) q_write(P, j++, T_MPART, base + nl, nm);
             for (uint32_t g = 0; g < nok; g++) {
@@ -734,9 +734,9 @@ __device__ void publish1(const Params &P, uint32_t type, uint32_t arg, uint32_t 
     }
 }
 
-// Thread 0, for a (sub)array with a training slot: the statistics and the
-// sample task each call this once when done; the second one publishes the
-// successor that the statistics chose (written before the first call).
+// Thread 0, for a (sub)array with a training slot: the statistics and each
+// sample run call this once when done; the last one publishes the successor
+// that the statistics chose (written before their call).
 __device__ void learned_join(const Params &P, uint32_t sid)
 {
     Seg *S = &P.segs[sid];
@@ -884,33 +884,37 @@ __device__ uint32_t cta_lsd_sort64(unsigned long long *A, unsigned long long *B,
     return sel;
 }
 
-// Learned map, first half (beside the statistics tiles): the sample of
-// P.sample keys at the stratified positions, then its exact sort.  The keys
-// are sorted as they are (key - smallest sampled key, over the bytes that
-// vary): the normalisation u = fl32(key - min) * 2^-E is monotone, so the
-// sorted keys give the sorted normalised sample once min and max are known.
-__device__ __noinline__ void task_lsample(const Params &P, uint32_t sid, SmemTile &s)
+// Learned map, first half (beside the statistics tiles): run `run` of the
+// sample, i.e. sample indices [run * m / R, (run + 1) * m / R) at the
+// stratified positions, drawn and sorted exactly by one CTA (in place in
+// buffer A of the slot).  The keys are sorted as they are: the
+// normalisation u = fl32(key - min) * 2^-E is monotone, so the sorted keys
+// give the sorted normalised sample once min and max are known.
+__device__ __noinline__ void task_lsample(const Params &P, uint32_t sid, uint32_t run, SmemTile &s)
 {
     Seg *S = &P.segs[sid];
     const unsigned long long off = __ldcg(&S->off);
     const uint32_t len = __ldcg(&S->len), buf = __ldcg(&S->buf), slot = __ldcg(&S->train_slot);
     const uint32_t m = P.sample;
-    unsigned long long *A = P.trainbuf + (size_t)slot * 2 * SAMPLE_MAX;
+    const uint32_t lo = (uint32_t)((unsigned long long)run * m / SAMPLE_RUNS);
+    const uint32_t hi = (uint32_t)((unsigned long long)(run + 1) * m / SAMPLE_RUNS);
+    const uint32_t mr = hi - lo;
+    unsigned long long *A = P.trainbuf + (size_t)slot * 2 * SAMPLE_MAX + lo;
     unsigned long long *B = A + SAMPLE_MAX;
     const uint64_t *src = keys_of(P, buf) + off;
     unsigned long long mn = ~0ull, mx = 0ull;
     constexpr int U = 8;  // independent loads in flight per thread
-    for (uint32_t i0 = 0; i0 < m; i0 += BLOCK * U) {
+    for (uint32_t i0 = 0; i0 < mr; i0 += BLOCK * U) {
         unsigned long long x[U];
 #pragma unroll
         for (int u = 0; u < U; u++) {
             const uint32_t i = i0 + threadIdx.x + u * BLOCK;
-            x[u] = i < m ? __ldcg(src + sample_pos(P.seed, len, m, i)) : 0ull;
+            x[u] = i < mr ? __ldcg(src + sample_pos(P.seed, len, m, lo + i)) : 0ull;
         }
 #pragma unroll
         for (int u = 0; u < U; u++) {
             const uint32_t i = i0 + threadIdx.x + u * BLOCK;
-            if (i < m) {
+            if (i < mr) {
                 __stcg(A + i, x[u]);
                 mn = x[u] < mn ? x[u] : mn;
                 mx = x[u] > mx ? x[u] : mx;
@@ -935,14 +939,74 @@ __device__ __noinline__ void task_lsample(const Params &P, uint32_t sid, SmemTil
         mx = s.red64[WARPS + w] > mx ? s.red64[WARPS + w] : mx;
     }
     __syncthreads();
-    const uint32_t sel = cta_lsd_sort64(A, B, m, mn, (bitlen64(mx - mn) + 7) / 8, s);
-    __threadfence();  // the sorted sample before the join publishes the fit
+    if (mr > 0 && cta_lsd_sort64(A, B, mr, mn, (bitlen64(mx - mn) + 7) / 8, s))
+        for (uint32_t i = threadIdx.x; i < mr; i += BLOCK) __stcg(A + i, __ldcg(B + i));
+    __threadfence();  // the sorted run before the join publishes the fit
     __syncthreads();
-    if (threadIdx.x == 0) {
-        S->smin = mn;
-        S->sort_sel = sel;
-        learned_join(P, sid);
+    if (threadIdx.x == 0) learned_join(P, sid);
+}
+
+// The r-th smallest (0-based) of the sample held as SAMPLE_RUNS sorted runs
+// in X: the smallest value v with at least r + 1 sample keys <= v, by a
+// binary search over values between the sample's min and max.  Each run
+// keeps the index window that holds the count of its keys <= v for every v
+// still in the search interval, so its searches shrink as the interval does;
+// the runs' searches advance in lockstep (their loads are independent).
+__device__ unsigned long long sample_select(const unsigned long long *X, uint32_t m, uint32_t r)
+{
+    uint32_t wl[SAMPLE_RUNS], wh[SAMPLE_RUNS];
+    unsigned long long lo = ~0ull, hi = 0ull;
+#pragma unroll
+    for (int t = 0; t < SAMPLE_RUNS; t++) {
+        wl[t] = (uint32_t)((unsigned long long)t * m / SAMPLE_RUNS);
+        wh[t] = (uint32_t)((unsigned long long)(t + 1) * m / SAMPLE_RUNS);
+        if (wh[t] > wl[t]) {
+            lo = min(lo, __ldcg(X + wl[t]));
+            hi = max(hi, __ldcg(X + wh[t] - 1));
+        }
     }
+    while (lo < hi) {
+        const unsigned long long mid = lo + ((hi - lo) >> 1);
+        // per run: the first index in [wl, wh) whose key is > mid (wh if none)
+        uint32_t a[SAMPLE_RUNS], b[SAMPLE_RUNS];
+        bool active = false;
+#pragma unroll
+        for (int t = 0; t < SAMPLE_RUNS; t++) {
+            a[t] = wl[t];
+            b[t] = wh[t];
+            active = active || a[t] < b[t];
+        }
+        while (active) {
+            unsigned long long v[SAMPLE_RUNS];
+#pragma unroll
+            for (int t = 0; t < SAMPLE_RUNS; t++) v[t] = a[t] < b[t] ? __ldcg(X + ((a[t] + b[t]) >> 1)) : 0ull;
+            active = false;
+#pragma unroll
+            for (int t = 0; t < SAMPLE_RUNS; t++) {
+                if (a[t] < b[t]) {
+                    const uint32_t h = (a[t] + b[t]) >> 1;
+                    if (v[t] <= mid)
+                        a[t] = h + 1;
+                    else
+                        b[t] = h;
+                }
+                active = active || a[t] < b[t];
+            }
+        }
+        uint32_t c = 0;
+#pragma unroll
+        for (int t = 0; t < SAMPLE_RUNS; t++) c += a[t] - (uint32_t)((unsigned long long)t * m / SAMPLE_RUNS);
+        if (c >= r + 1) {
+            hi = mid;
+#pragma unroll
+            for (int t = 0; t < SAMPLE_RUNS; t++) wh[t] = a[t];
+        } else {
+            lo = mid + 1;
+#pragma unroll
+            for (int t = 0; t < SAMPLE_RUNS; t++) wl[t] = a[t];
+        }
+    }
+    return lo;
 }
 
 // Learned map, second half (after the statistics and the sample): breakpoints
@@ -956,7 +1020,7 @@ __device__ __noinline__ void task_lfit(const Params &P, uint32_t sid, SmemTile &
     const float escale = __ldcg(&S->escale), zc = __ldcg(&S->zc);
     const uint32_t zsh = __ldcg(&S->zsh);
     const uint32_t m = P.sample;
-    const unsigned long long *X = P.trainbuf + (size_t)slot * 2 * SAMPLE_MAX + (__ldcg(&S->sort_sel) ? SAMPLE_MAX : 0);
+    const unsigned long long *X = P.trainbuf + (size_t)slot * 2 * SAMPLE_MAX;  // sorted runs
     if (threadIdx.x == 0) {
         s.map.mn = mn;
         s.map.kind = MAP_PWL;
@@ -974,7 +1038,7 @@ __device__ __noinline__ void task_lfit(const Params &P, uint32_t sid, SmemTile &
         else if (j == PWL_P)
             q = __fmul_rn(u64_to_f32_rn(mx - mn), escale);
         else
-            q = __fmul_rn(u64_to_f32_rn(__ldcg(X + (size_t)j * m / PWL_P) - mn), escale);
+            q = __fmul_rn(u64_to_f32_rn(sample_select(X, m, (uint32_t)((size_t)j * m / PWL_P)) - mn), escale);
         s.map.q[j] = q;
         t[j] = q;
     }
