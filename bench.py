@@ -358,14 +358,15 @@ def main():
             kb.copy_(kd)
             vb.copy_(vd)
 
-    def timed_sorts(opts):
-        """Sorts both arrays; returns per-array (ms, bytes, stats)."""
+    def timed_sorts(opts, keys_only=False):
+        """Sorts both arrays (keys_only: the keys alone, vals = NULL); returns
+        per-array (ms, bytes, stats)."""
         out = []
         for kb, vb in bufs:
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            z.sort_pairs(kb, vb, opts=opts, check=False)
+            z.sort_pairs(kb, None if keys_only else vb, opts=opts, check=False)
             e1.record(stream)
             rc = z.sync_status(stream)
             if rc != 0:
@@ -374,15 +375,15 @@ def main():
             out.append((e0.elapsed_time(e1), st["bytes_algorithmic"], st))
         return out
 
-    def run(opts, steps, warmup):
+    def run(opts, steps, warmup, keys_only=False):
         for _ in range(warmup):
             restore()
-            timed_sorts(opts)
+            timed_sorts(opts, keys_only)
         res = []
         for _ in range(steps):
             restore()
             torch.cuda.synchronize()
-            res.append(timed_sorts(opts))
+            res.append(timed_sorts(opts, keys_only))
         return res
 
     opts = z.default_opts(mapper=mapper)
@@ -437,6 +438,19 @@ def main():
                  "bytes_per_pair": sum(a[1] for step in pres for a in step) / (n * len(bufs) * len(pres)),
                  "per_array_ms": [round(sum(step[i][0] for step in pres) / len(pres), 3)
                                   for i in range(len(bufs))]}
+
+    keys_only = None
+    if not args.no_plain:
+        kres = run(opts, max(3, args.steps // 2), 1, keys_only=True)
+        kms = sum(sum(a[0] for a in step) for step in kres)
+        for (name, kd, _), (kb, _vb) in zip(pristine, bufs):
+            s_ = kb ^ torch.tensor(-(2 ** 63), dtype=torch.int64, device=dev)
+            assert bool((s_[1:] >= s_[:-1]).all()), f"{name}: keys-only output not sorted"
+        keys_only = {"value": pairs_per_step * len(kres) / (kms / 1e3), "unit": "keys/s",
+                     "mode": "vals = NULL (the paper's key-only workload), same arrays and mapper",
+                     "bytes_per_key": sum(a[1] for step in kres for a in step) / (n * len(bufs) * len(kres)),
+                     "per_array_ms": [round(sum(step[i][0] for step in kres) / len(kres), 3)
+                                      for i in range(len(bufs))]}
 
     e2e = None
     if not args.no_e2e:
@@ -520,6 +534,7 @@ def main():
                        "learned_accepted": last_stats[i]["learned_accepted"]}
                       for i, (name, _, _) in enumerate(pristine)],
         "plain_zscore": plain,
+        "keys_only": keys_only,
         "batched": batched,
     }
     print(json.dumps(line), flush=True)

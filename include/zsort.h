@@ -147,8 +147,14 @@ typedef struct {
 void zsort_default_opts(zsort_opts *o);
 
 /* Sorts n (uint64 key, uint32 payload) pairs in place, stably (see above).
- * n <= ZSORT_MAX_N.  Uses the default options. */
+ * n <= ZSORT_MAX_N.  Uses the default options.  vals may be NULL: then the
+ * keys are sorted alone (key-only mode, the paper's own workload; each pass
+ * moves 8 bytes per element instead of 12).  Every entry point below that
+ * takes vals accepts NULL the same way. */
 int zsort_pairs(uint64_t *keys, uint32_t *vals, uint64_t n, zsort_stream_t stream);
+
+/* Key-only sort of n uint64 keys in place: zsort_pairs(keys, NULL, n, stream). */
+int zsort_keys(uint64_t *keys, uint64_t n, zsort_stream_t stream);
 
 /* The same for int64 keys (two's complement order) and float64 keys (IEEE
  * totalOrder, so -0.0 sorts before +0.0).  The keys are encoded to uint64 in

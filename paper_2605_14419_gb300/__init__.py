@@ -150,6 +150,7 @@ def load():
     sig = {
         "zsort_default_opts": (None, [ctypes.POINTER(Opts)]),
         "zsort_pairs": (i32, [vp, vp, u64, vp]),
+        "zsort_keys": (i32, [vp, u64, vp]),
         "zsort_pairs_i64": (i32, [vp, vp, u64, vp]),
         "zsort_pairs_f64": (i32, [vp, vp, u64, vp]),
         "zsort_pairs_ex": (i32, [vp, u32, vp, u64, ctypes.POINTER(Opts), vp]),
@@ -216,16 +217,18 @@ def _raise(rc: int, where: str):
 
 def sort_pairs(keys, vals, key_type: str = "u64", opts: Opts | None = None, stream=None,
                check: bool = True):
-    """Sorts (keys, vals) in place, stably by key.  With check=True the stream
-    is synchronised and the device status raised as ZsortError."""
+    """Sorts (keys, vals) in place, stably by key; vals=None sorts the keys
+    alone (key-only mode).  With check=True the stream is synchronised and
+    the device status raised as ZsortError."""
     _check_tensor(keys, 8, "keys")
-    _check_tensor(vals, 4, "vals")
-    if keys.numel() != vals.numel():
-        raise ValueError("keys and vals differ in length")
+    if vals is not None:
+        _check_tensor(vals, 4, "vals")
+        if keys.numel() != vals.numel():
+            raise ValueError("keys and vals differ in length")
     lib = load()
     st = _stream_handle(stream)
     rc = lib.zsort_pairs_ex(ctypes.c_void_p(keys.data_ptr()), KEY_TYPES[key_type],
-                            ctypes.c_void_p(vals.data_ptr()), keys.numel(),
+                            ctypes.c_void_p(vals.data_ptr()) if vals is not None else None, keys.numel(),
                             ctypes.byref(opts) if opts is not None else None, st)
     _raise(rc, "zsort_pairs_ex")
     if check:
@@ -233,15 +236,23 @@ def sort_pairs(keys, vals, key_type: str = "u64", opts: Opts | None = None, stre
     return keys, vals
 
 
+def sort_keys(keys, key_type: str = "u64", opts: Opts | None = None, stream=None, check: bool = True):
+    """Key-only sort of keys in place."""
+    return sort_pairs(keys, None, key_type=key_type, opts=opts, stream=stream, check=check)[0]
+
+
 def sort_segmented(keys, vals, offsets, opts: Opts | None = None, stream=None, check: bool = True):
-    """Sorts each segment [offsets[i], offsets[i+1]) of (keys, vals) in place.
-    offsets: CUDA int64/uint64 tensor of nseg + 1 entries."""
+    """Sorts each segment [offsets[i], offsets[i+1]) of (keys, vals) in place
+    (vals=None: keys only).  offsets: CUDA int64/uint64 tensor of nseg + 1
+    entries."""
     _check_tensor(keys, 8, "keys")
-    _check_tensor(vals, 4, "vals")
+    if vals is not None:
+        _check_tensor(vals, 4, "vals")
     _check_tensor(offsets, 8, "offsets")
     lib = load()
     st = _stream_handle(stream)
-    rc = lib.zsort_segmented_ex(ctypes.c_void_p(keys.data_ptr()), ctypes.c_void_p(vals.data_ptr()),
+    rc = lib.zsort_segmented_ex(ctypes.c_void_p(keys.data_ptr()),
+                                ctypes.c_void_p(vals.data_ptr()) if vals is not None else None,
                                 keys.numel(), ctypes.c_void_p(offsets.data_ptr()),
                                 max(offsets.numel() - 1, 0),
                                 ctypes.byref(opts) if opts is not None else None, st)

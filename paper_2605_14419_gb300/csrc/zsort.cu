@@ -459,6 +459,7 @@ int launch(uint64_t *keys, uint32_t *vals, unsigned long long n, const uint64_t 
     P.seed = o.seed;
     P.wait_ns = (unsigned long long)o.wait_limit_ms * 1000000ull;
     P.user_aligned = ((reinterpret_cast<uintptr_t>(keys) | reinterpret_cast<uintptr_t>(vals)) & 15u) == 0;
+    P.kv = vals != nullptr;  // null vals: keys only
     int per_sm = o.ctas_per_sm ? (int)std::min<uint32_t>(o.ctas_per_sm, (uint32_t)ws->occ) : ws->occ;
     P.nctas = (uint32_t)(ws->sms * per_sm);
     P.plan_out = plan_out;
@@ -627,13 +628,18 @@ int zsort_pairs_ex(void *keys, uint32_t key_type, uint32_t *vals, uint64_t n, co
     if (!opts_valid(o)) return ZSORT_ERR_INVALID;
     if (key_type > ZSORT_KEY_F64 || n > ZSORT_MAX_N) return ZSORT_ERR_INVALID;
     if (n <= 1) return ZSORT_OK;
-    if (!keys || !vals) return ZSORT_ERR_INVALID;
+    if (!keys) return ZSORT_ERR_INVALID;  // vals may be null: keys only
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     int rc = encode(keys, n, key_type, 0, st);
     if (rc != ZSORT_OK) return rc;
     rc = launch(static_cast<uint64_t *>(keys), vals, n, nullptr, 1, o, st);
     if (rc != ZSORT_OK) return rc;
     return encode(keys, n, key_type, 1, st);
+}
+
+int zsort_keys(uint64_t *keys, uint64_t n, zsort_stream_t stream)
+{
+    return zsort_pairs_ex(keys, ZSORT_KEY_U64, nullptr, n, nullptr, stream);
 }
 
 int zsort_pairs(uint64_t *keys, uint32_t *vals, uint64_t n, zsort_stream_t stream)
@@ -662,7 +668,7 @@ int zsort_segmented_ex(uint64_t *keys, uint32_t *vals, uint64_t n, const uint64_
     if (!opts_valid(o)) return ZSORT_ERR_INVALID;
     if (n > ZSORT_MAX_SEG_TOTAL || nseg > (1ull << 31)) return ZSORT_ERR_INVALID;
     if (nseg == 0) return ZSORT_OK;
-    if (!seg_offsets || (n > 0 && (!keys || !vals))) return ZSORT_ERR_INVALID;
+    if (!seg_offsets || (n > 0 && !keys)) return ZSORT_ERR_INVALID;
     return launch(keys, vals, n, seg_offsets, nseg, o, reinterpret_cast<cudaStream_t>(stream));
 }
 
@@ -774,9 +780,8 @@ int zsort_map_buckets(const uint64_t *keys, uint64_t n, const zsort_opts *opts, 
     if (!opts_valid(o)) return ZSORT_ERR_INVALID;
     if (n < 2 || n > ZSORT_MAX_N || !keys || !buckets || !info) return ZSORT_ERR_INVALID;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    // the executor reads keys only in inspection mode; vals are never touched
-    int rc = launch(const_cast<uint64_t *>(keys), reinterpret_cast<uint32_t *>(buckets), n, nullptr, 1, o, st,
-                    buckets);
+    // inspection mode reads the keys only (no payload) and writes buckets
+    int rc = launch(const_cast<uint64_t *>(keys), nullptr, n, nullptr, 1, o, st, buckets);
     if (rc != ZSORT_OK) return rc;
     cudaError_t ce = cudaStreamSynchronize(st);
     if (ce != cudaSuccess) return cuda_err(ce);
@@ -831,7 +836,7 @@ int zsort_pairs_noalloc(uint64_t *keys, uint32_t *vals, uint64_t n, int32_t *sta
         }
         return ZSORT_OK;
     }
-    if (!keys || !vals) return ZSORT_ERR_INVALID;
+    if (!keys) return ZSORT_ERR_INVALID;  // vals may be null: keys only
     int dev = 0;
     cudaError_t ce = cudaGetDevice(&dev);
     if (ce != cudaSuccess) return cuda_err(ce);
@@ -893,6 +898,7 @@ int zsort_pairs_noalloc(uint64_t *keys, uint32_t *vals, uint64_t n, int32_t *sta
     P.seed = o.seed;
     P.wait_ns = (unsigned long long)o.wait_limit_ms * 1000000ull;
     P.user_aligned = ((reinterpret_cast<uintptr_t>(keys) | reinterpret_cast<uintptr_t>(vals)) & 15u) == 0;
+    P.kv = vals != nullptr;  // null vals: keys only
     P.nctas = (uint32_t)(D.sms * D.occ);
     ce = cudaMemsetAsync(P.ctl, 0, sizeof(Ctl), st);  // the control block must start at zero
     if (ce != cudaSuccess) return cuda_err(ce);

@@ -130,6 +130,12 @@ __device__ __forceinline__ Item load_item(const Params &P, uint32_t idx)
     return it;
 }
 
+// Bytes of one element: key and payload, or the key alone.
+__device__ __forceinline__ unsigned long long elem_bytes(const Params &P)
+{
+    return P.kv ? 12ull : 8ull;
+}
+
 __device__ __forceinline__ uint64_t *keys_of(const Params &P, uint32_t buf)
 {
     return buf ? P.skeys : P.ukeys;
@@ -296,7 +302,7 @@ __device__ void stream_issue(const Params &P, SmemTile &s, int w, const uint64_t
     const uint32_t bk = a1 > a0 ? (uint32_t)(a1 - a0) * 8u : 0u;
     uint32_t bv = 0;
     unsigned long long b0 = 0;
-    if (VALS) {
+    if (VALS && P.kv) {
         b0 = a & ~3ull;
         const unsigned long long b1 = min((a + cnt + 3) & ~3ull, P.n & ~3ull);
         bv = b1 > b0 ? (uint32_t)(b1 - b0) * 4u : 0u;
@@ -313,7 +319,7 @@ __device__ void stream_fix_tail(const Params &P, unsigned long long *sk, uint32_
     const unsigned long long end = a + cnt;
     const unsigned long long ka = max(a, P.n & ~1ull);
     for (unsigned long long e = ka + threadIdx.x; e < end; e += BLOCK) sk[e - a] = __ldcg(keys + e);
-    if (VALS) {
+    if (VALS && P.kv) {
         const unsigned long long va = max(a, P.n & ~3ull);
         for (unsigned long long e = va + threadIdx.x; e < end; e += BLOCK) sv[e - a] = __ldcg(vals + e);
     }
@@ -359,7 +365,7 @@ __device__ bool stream_tiles(const Params &P, SmemTile &s, Pipe &pp, const uint6
             sv = s.u.buf[w].val;
             for (uint32_t i = threadIdx.x; i < cnt; i += BLOCK) {
                 sk[i] = __ldcg(keys + a + i);
-                if (VALS) sv[i] = __ldcg(vals + a + i);
+                if (VALS && P.kv) sv[i] = __ldcg(vals + a + i);
             }
         }
         __syncthreads();
@@ -426,6 +432,7 @@ __device__ __noinline__ void scatter_stream(const Params &P, SmemTile &s, Pipe &
     const MapK mk = map_regs(s.map);
     const uint32_t k = mk.k;
     const bool stage_b = mk.kind == MAP_PWL;
+    const bool kv = P.kv != 0;
     // the runs written per tile end inside lines that the next tile (or the
     // neighbouring chunk) completes: keep those lines in L2 until then
     const unsigned long long pol_front = policy_evict_last();
@@ -454,7 +461,7 @@ __device__ __noinline__ void scatter_stream(const Params &P, SmemTile &s, Pipe &
             sv = s.u.buf[w].val;
             for (uint32_t i = threadIdx.x; i < cnt; i += BLOCK) {
                 sk[i] = __ldcg(srck + a + i);
-                sv[i] = __ldcg(srcv + a + i);
+                if (kv) sv[i] = __ldcg(srcv + a + i);
             }
             __syncthreads();
         }
@@ -465,7 +472,7 @@ __device__ __noinline__ void scatter_stream(const Params &P, SmemTile &s, Pipe &
             const uint32_t p = slot_index(i);
             const bool in = p < cnt;
             x[i] = in ? sk[p] : 0ull;
-            v[i] = in ? sv[p] : 0u;
+            v[i] = in && kv ? sv[p] : 0u;
             b[i] = in ? map_key(mk, s.map, x[i]) : 0u;
         }
         rank_peers<IPT, NBITS>(b, cnt, peers);
@@ -489,7 +496,7 @@ __device__ __noinline__ void scatter_stream(const Params &P, SmemTile &s, Pipe &
         for (int i = 0; i < IPT; i++) {
             if (pos[i] != INVALID) {
                 sk[pos[i]] = x[i];
-                sv[pos[i]] = v[i];
+                if (kv) sv[pos[i]] = v[i];
                 if (stage_b) s.bkt[pos[i]] = (uint16_t)b[i];
             }
         }
@@ -500,7 +507,7 @@ __device__ __noinline__ void scatter_stream(const Params &P, SmemTile &s, Pipe &
             const uint32_t rel = s.gdelta[q] + p;
             if (rel < seglen) {
                 st_front(dstk + rel, key, pol_front);
-                st_front(dstv + rel, sv[p], pol_front);
+                if (kv) st_front(dstv + rel, sv[p], pol_front);
             } else {
                 set_error(P, ST_INTERNAL);
             }
@@ -1234,7 +1241,7 @@ __device__ __noinline__ void task_lscatter(const Params &P, uint32_t sid, uint32
     uint32_t *dstv = vals_of(P, ch.buf ^ 1u) + ch.off;
     scatter_dispatch(P, s, pp, keys_of(P, ch.buf), vals_of(P, ch.buf), bulk_ok(P, ch.buf), ch.start, ch.len, dstk,
                      dstv, ch.seglen, k);
-    if (threadIdx.x == 0) atomicAdd(&P.ctl->bytes, 24ull * ch.len);
+    if (threadIdx.x == 0) atomicAdd(&P.ctl->bytes, 2ull * elem_bytes(P) * ch.len);
 }
 
 __device__ __noinline__ void lscatter_done(const Params &P, uint32_t sid, SmemTile &s)
@@ -1286,11 +1293,11 @@ __device__ __noinline__ void task_mpart(const Params &P, const Item it, SmemTile
         if (buf) {
             for (uint32_t p = threadIdx.x; p < len; p += BLOCK) {
                 __stcg(P.ukeys + off + p, __ldcg(srck + off + p));
-                __stcg(P.uvals + off + p, __ldcg(srcv + off + p));
+                if (P.kv) __stcg(P.uvals + off + p, __ldcg(srcv + off + p));
             }
             if (threadIdx.x == 0) {
                 atomicAdd(&P.ctl->n_copies, 1ull);
-                atomicAdd(&P.ctl->bytes, 32ull * len);
+                atomicAdd(&P.ctl->bytes, (8ull + 2ull * elem_bytes(P)) * len);
             }
         } else if (threadIdx.x == 0) {
             atomicAdd(&P.ctl->bytes, 8ull * len);
@@ -1311,7 +1318,7 @@ __device__ __noinline__ void task_mpart(const Params &P, const Item it, SmemTile
     scatter_dispatch(P, s, pp, srck, srcv, bulk, off, len, dstk, dstv, len, k);
     if (threadIdx.x == 0) {
         atomicAdd(&P.ctl->n_small, 1ull);
-        atomicAdd(&P.ctl->bytes, 40ull * len);
+        atomicAdd(&P.ctl->bytes, (16ull + 2ull * elem_bytes(P)) * len);
         note_level(P, level);
     }
     classify_children(P, off, k, buf ^ 1u, level + 1, s);
@@ -1326,7 +1333,7 @@ __device__ void prefetch_item_l2(const Params &P, const Item it)
     const unsigned long long a0 = off & ~1ull, a1 = min((off + len + 1) & ~1ull, P.n & ~1ull);
     const unsigned long long b0 = off & ~3ull, b1 = min((off + len + 3) & ~3ull, P.n & ~3ull);
     if (a1 > a0) bulk_prefetch_l2(keys_of(P, it.buf) + a0, (uint32_t)(a1 - a0) * 8u);
-    if (b1 > b0) bulk_prefetch_l2(vals_of(P, it.buf) + b0, (uint32_t)(b1 - b0) * 4u);
+    if (P.kv && b1 > b0) bulk_prefetch_l2(vals_of(P, it.buf) + b0, (uint32_t)(b1 - b0) * 4u);
 }
 
 __device__ bool insertion_sort_budget(unsigned long long *k, uint32_t *v, uint32_t n, uint32_t budget)
@@ -1445,7 +1452,7 @@ __device__ __forceinline__ void finish_fast(SmemTile &s, unsigned long long *key
         }
         if (p < len) {
             __stcg(dk + r, xk);
-            __stcg(dv + r, val[p]);
+            if (dv) __stcg(dv + r, val[p]);
         }
     }
 }
@@ -1493,7 +1500,7 @@ __device__ __noinline__ void finish_stable(const Params &P, SmemTile &s, unsigne
     }
     for (uint32_t p = threadIdx.x; p < len; p += BLOCK) {
         __stcg(dk + p, key[p]);
-        __stcg(dv + p, val[p]);
+        if (dv) __stcg(dv + p, val[p]);
     }
 }
 
@@ -1510,7 +1517,7 @@ __device__ __noinline__ void task_finish(const Params &P, const Item it, SmemTil
     const uint64_t *srck = keys_of(P, buf);
     const uint32_t *srcv = vals_of(P, buf);
     uint64_t *dk = P.ukeys + off;
-    uint32_t *dv = P.uvals + off;
+    uint32_t *dv = P.kv ? P.uvals + off : nullptr;  // keys only: no payload
     unsigned long long *key;
     uint32_t *val;
     if (bulk_ok(P, buf)) {
@@ -1518,7 +1525,7 @@ __device__ __noinline__ void task_finish(const Params &P, const Item it, SmemTil
             const unsigned long long a0 = off & ~1ull, a1 = min((off + len + 1) & ~1ull, P.n & ~1ull);
             const unsigned long long b0 = off & ~3ull, b1 = min((off + len + 3) & ~3ull, P.n & ~3ull);
             const uint32_t bk = a1 > a0 ? (uint32_t)(a1 - a0) * 8u : 0u;
-            const uint32_t bv = b1 > b0 ? (uint32_t)(b1 - b0) * 4u : 0u;
+            const uint32_t bv = P.kv && b1 > b0 ? (uint32_t)(b1 - b0) * 4u : 0u;
             mbar_expect_arrive(&s.bar[0], bk + bv);
             if (bk) bulk_g2s(s.u.leaf.key, srck + a0, bk, &s.bar[0]);
             if (bv) bulk_g2s(s.u.leaf.val, srcv + b0, bv, &s.bar[0]);
@@ -1535,14 +1542,15 @@ __device__ __noinline__ void task_finish(const Params &P, const Item it, SmemTil
         const unsigned long long end = off + len;
         for (unsigned long long e = max(off, P.n & ~1ull) + threadIdx.x; e < end; e += BLOCK)
             key[e - off] = __ldcg(srck + e);
-        for (unsigned long long e = max(off, P.n & ~3ull) + threadIdx.x; e < end; e += BLOCK)
-            val[e - off] = __ldcg(srcv + e);
+        if (P.kv)
+            for (unsigned long long e = max(off, P.n & ~3ull) + threadIdx.x; e < end; e += BLOCK)
+                val[e - off] = __ldcg(srcv + e);
     } else {
         key = s.u.leaf.key;
         val = s.u.leaf.val;
         for (uint32_t i = threadIdx.x; i < len; i += BLOCK) {
             key[i] = __ldcg(srck + off + i);
-            val[i] = __ldcg(srcv + off + i);
+            if (P.kv) val[i] = __ldcg(srcv + off + i);
         }
     }
     __syncthreads();
@@ -1554,7 +1562,7 @@ __device__ __noinline__ void task_finish(const Params &P, const Item it, SmemTil
     for (int j = 0; j < LEAF_IPT; j++) {
         const uint32_t p = threadIdx.x + j * BLOCK;
         kk[j] = p < len ? key[p] : 0ull;
-        vv[j] = p < len ? val[p] : 0u;
+        vv[j] = p < len && P.kv ? val[p] : 0u;
         if (p < len) {
             mn = kk[j] < mn ? kk[j] : mn;
             mx = kk[j] > mx ? kk[j] : mx;
@@ -1582,7 +1590,7 @@ __device__ __noinline__ void task_finish(const Params &P, const Item it, SmemTil
     }
     if (threadIdx.x == 0) {
         atomicAdd(&P.ctl->n_leaves, 1ull);
-        atomicAdd(&P.ctl->bytes, (buf || mn != mx) ? 24ull * len : 12ull * len);
+        atomicAdd(&P.ctl->bytes, ((buf || mn != mx) ? 2ull : 1ull) * elem_bytes(P) * len);
     }
     if (mn == mx) {  // identical keys: in order already
         if (buf) {
@@ -1591,7 +1599,7 @@ __device__ __noinline__ void task_finish(const Params &P, const Item it, SmemTil
                 const uint32_t p = threadIdx.x + j * BLOCK;
                 if (p < len) {
                     __stcg(dk + p, kk[j]);
-                    __stcg(dv + p, vv[j]);
+                    if (dv) __stcg(dv + p, vv[j]);
                 }
             }
         }
@@ -1607,7 +1615,7 @@ __device__ __noinline__ void task_finish(const Params &P, const Item it, SmemTil
                 r += (kq < kt) || (kq == kt && q < t);
             }
             __stcg(dk + r, kt);
-            __stcg(dv + r, vv[0]);
+            if (dv) __stcg(dv + r, vv[0]);
         }
         return;
     }
@@ -1639,9 +1647,9 @@ __device__ __noinline__ void task_copy(const Params &P, uint32_t sid, uint32_t t
     const uint32_t cnt = min((uint32_t)LEAF_CAP, len - tile * LEAF_CAP);
     for (uint32_t p = threadIdx.x; p < cnt; p += BLOCK) {
         __stcg(P.ukeys + off + p, __ldcg(P.skeys + off + p));
-        __stcg(P.uvals + off + p, __ldcg(P.svals + off + p));
+        if (P.kv) __stcg(P.uvals + off + p, __ldcg(P.svals + off + p));
     }
-    if (threadIdx.x == 0) atomicAdd(&P.ctl->bytes, 24ull * cnt);
+    if (threadIdx.x == 0) atomicAdd(&P.ctl->bytes, 2ull * elem_bytes(P) * cnt);
 }
 
 }  // namespace zs

@@ -279,3 +279,56 @@ def test_pairs_graph_replays_with_learned_map():
             z.sort_pairs(kb, vb, opts=opts, stream=stream)
             assert np.array_equal(kb.cpu().numpy().view(np.uint64), ok)
             assert np.array_equal(vb.cpu().numpy().view(np.uint32), ov)
+
+
+# ---------------------------------------------------------------- key-only mode
+def keys_only(keys, opts=None, key_type="u64"):
+    k = torch.from_numpy(np.ascontiguousarray(keys).view(np.int64)).to(DEV)
+    z.sort_pairs(k, None, key_type=key_type, opts=opts)
+    return k.cpu().numpy().view(keys.dtype)
+
+
+@pytest.mark.parametrize("n", [2, 255, 4097, 65537, 200_003, 3_000_000])
+@pytest.mark.parametrize("family", FAMILIES)
+def test_keys_only_matches_oracle(family, n):
+    """vals = NULL: the keys alone, sorted exactly as the oracle sorts the pairs."""
+    keys = inputs.FAMILIES[family](n, seed=n + 101)
+    ok, _ = oracle.zsort_pairs(keys, inputs.index_payload(n))
+    assert np.array_equal(keys_only(keys), ok)
+
+
+@pytest.mark.parametrize("mapper", [z.MAP_ZSCORE, z.MAP_LEARNED])
+def test_keys_only_skewed_and_graph(mapper):
+    keys = inputs.lognormal(2_000_000, 31)
+    ok, _ = oracle.zsort_pairs(keys, inputs.index_payload(keys.size))
+    opts = z.default_opts(mapper=mapper, learn_min=65536, flags=z.FLAG_GRAPH)
+    kp = torch.from_numpy(keys.view(np.int64)).to(DEV)
+    kb = torch.empty_like(kp)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            kb.copy_(kp)
+            z.sort_pairs(kb, None, opts=opts, stream=stream)
+            assert np.array_equal(kb.cpu().numpy().view(np.uint64), ok)
+    # 8-byte elements: the library counts 2/3 of the pairs' bytes per pass
+    st = z.last_stats(stream)
+    kb.copy_(kp)
+    vb = torch.arange(keys.size, dtype=torch.int32, device=DEV)
+    with torch.cuda.stream(stream):
+        z.sort_pairs(kb, vb, opts=z.default_opts(mapper=mapper, learn_min=65536), stream=stream)
+    st2 = z.last_stats(stream)
+    assert st["bytes_algorithmic"] < st2["bytes_algorithmic"]
+
+
+def test_keys_only_int64_float64_and_segmented():
+    x = inputs.dense_interval_i64(400_000, 17)
+    assert np.array_equal(keys_only(x.astype(np.int64), key_type="i64"), np.sort(x.astype(np.int64), kind="stable"))
+    f = inputs.normal_f64_specials(400_000, 18)
+    got = keys_only(f, key_type="f64")
+    want = oracle.key_to_f64(np.sort(oracle.key_from_f64(f)))
+    assert np.array_equal(got.view(np.uint64), want.view(np.uint64))
+    keys, vals, off, _ = inputs.segmented(200, 19, lo=1, hi=200_000)
+    k = torch.from_numpy(keys.view(np.int64)).to(DEV)
+    z.sort_segmented(k, None, torch.from_numpy(off.view(np.int64)).to(DEV))
+    ok, _ = oracle.zsort_segmented(keys, vals, off)
+    assert np.array_equal(k.cpu().numpy().view(np.uint64), ok)
