@@ -64,11 +64,26 @@ enum {
 #define ZSORT_MAX_N ((uint64_t)1 << 30)
 #define ZSORT_MAX_SEG_TOTAL ((uint64_t)1 << 34)
 
-/* Bucket maps. */
+/* Bucket maps (zsort_opts.mapper). */
 enum {
     ZSORT_MAP_ZSCORE = 0,  /* Eq. 1: floor(((x - mean)/sd + |z_min|) * k/4)   */
-    ZSORT_MAP_LEARNED = 1  /* piecewise-linear CDF, 256 pieces, FP32, trained
+    ZSORT_MAP_LEARNED = 1, /* piecewise-linear CDF, 256 pieces, FP32, trained
                               on a sample; Eq. 1 is the fallback             */
+    ZSORT_MAP_MLP = 2      /* 2-layer MLP with positive weights and 32
+                              clamp(., 0, 1) hidden units, FP32, fitted to
+                              the same sample's 257 quantiles: f(u) =
+                              sum_h a_h clamp(w_h u + b_h, 0, 1), a, w >= 0,
+                              bucket = trunc(k (f(u) - f(0)) / (f(u_max) -
+                              f(0))); monotone by construction; Eq. 1 is the
+                              fallback                                       */
+};
+
+/* Map actually used at the top level (zsort_map_info.map). */
+enum {
+    ZSORT_MAPINFO_ZSCORE = 0,
+    ZSORT_MAPINFO_LEARNED = 1,
+    ZSORT_MAPINFO_RANGE = 2,  /* the progress guard's exact range map */
+    ZSORT_MAPINFO_MLP = 3
 };
 
 /* Key types for zsort_pairs_ex. */
@@ -197,7 +212,7 @@ int zsort_last_stats(zsort_stream_t stream, zsort_stats *out);
 
 /* Top-level partition plan of one array (zsort_map_buckets). */
 typedef struct {
-    uint32_t map;               /* ZSORT_MAP_ZSCORE, ZSORT_MAP_LEARNED, or 2 = range map */
+    uint32_t map;               /* ZSORT_MAPINFO_*                                     */
     uint32_t k;                 /* buckets                                            */
     uint64_t min, max;          /* exact min / max of the keys                        */
     double mean_d, sd;          /* mean of key - min, population sd (exact sums)      */
@@ -209,6 +224,8 @@ typedef struct {
     float r[256];               /* learned map reciprocal piece widths                 */
     uint32_t learned_max_load;  /* load test: largest learned bucket on the sample     */
     uint32_t zscore_max_load;   /* load test: largest Eq. 1 bucket on the sample       */
+    float mlp[98];              /* MLP map (mapper ZSORT_MAP_MLP): w[32], b[32], a[32],
+                                   f0, inv                                             */
 } zsort_map_info;
 
 /* Inspection: runs the statistics step and the bucket-map choice (Eq. 1 of

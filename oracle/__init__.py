@@ -93,6 +93,13 @@ def _load():
         lib.oracle_pwl_bucket.restype = ctypes.c_uint32
         lib.oracle_pwl_bucket.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
                                           ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32]
+        lib.oracle_mlp_train.restype = None
+        lib.oracle_mlp_train.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p]
+        lib.oracle_mlp_buckets.restype = None
+        lib.oracle_mlp_buckets.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
+                                           ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p]
+        lib.oracle_mlp_eval.restype = ctypes.c_float
+        lib.oracle_mlp_eval.argtypes = [ctypes.c_void_p, ctypes.c_float]
         _lib = lib
     return _lib
 
@@ -215,3 +222,28 @@ def learned_map(keys, seed: int, m: int, k: int, P: int = P_PIECES):
     sample = k_arr[pos.astype(np.int64)]
     q = pwl_train(sample, mn, mx, P)
     return mn, mx, q, sample
+
+
+MLP_H = 32
+MLP_PARAMS = 3 * MLP_H + 2
+
+
+def mlp_train(q, iters: int):
+    """Trained MLP map parameters (omega, beta, alpha, f0, inv) from the knots q."""
+    qq = np.ascontiguousarray(q, dtype=np.float32)
+    out = np.empty(MLP_PARAMS, dtype=np.float32)
+    _load().oracle_mlp_train(_ptr(qq), qq.size - 1, iters, _ptr(out))
+    return out
+
+
+def mlp_buckets(keys, mn: int, mx: int, params, k: int):
+    kk = np.ascontiguousarray(keys, dtype=np.uint64)
+    pp = np.ascontiguousarray(params, dtype=np.float32)
+    out = np.empty(kk.size, dtype=np.uint32)
+    _load().oracle_mlp_buckets(_ptr(kk), kk.size, mn, mx, _ptr(pp), k, _ptr(out))
+    return out
+
+
+def mlp_eval(params, u: float) -> float:
+    pp = np.ascontiguousarray(params, dtype=np.float32)
+    return float(_load().oracle_mlp_eval(_ptr(pp), ctypes.c_float(u)))

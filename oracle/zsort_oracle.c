@@ -20,6 +20,11 @@
  *   oracle_pwl_bucket        the learned monotone piecewise-linear bucket map
  *                            that replaces the z-score map (not in the paper;
  *                            restated from its written definition)
+ *   oracle_mlp_train, oracle_mlp_bucket
+ *                            the alternative learned map: a 2-layer MLP with
+ *                            positive weights fitted to the same quantile
+ *                            knots (not in the paper; restated from its
+ *                            written definition below)
  *
  * Readings of the paper where it is silent or garbled (each repeated where
  * it is used):
@@ -502,4 +507,146 @@ void oracle_pwl_buckets(const uint64_t *keys, uint64_t n, uint64_t mn, uint64_t 
                         const float *q, uint32_t P, uint32_t k, uint32_t *out)
 {
     for (uint64_t i = 0; i < n; i++) out[i] = oracle_pwl_bucket(keys[i], mn, mx, q, P, k);
+}
+
+
+/* ---------------------------------------------------------------- MLP map
+ * Monotone 2-layer MLP: f(u) = sum_{h<H} a_h * clamp(w_h * u + b_h, 0, 1)
+ * with a_h = alpha_h^2 and w_h = omega_h^2, so every weight is >= 0 and f is
+ * non-decreasing in u by construction; also in binary32, since each step
+ * (a product by a non-negative factor, an addition, a clamp, the sum taken
+ * in the fixed order h = 0, 1, ...) is a monotone rounding of a monotone
+ * function.  The map: g = (f(u) - f(0)) * inv, inv = 1 / (f(u_max) - f(0)),
+ * clipped to [0, 1 - 2^-24], bucket = min(k - 1, trunc(g * k)).
+ *
+ * Training on the P + 1 knots (x_j, y_j) = (q[j], j / P) of the
+ * piecewise-linear map (the exact sample quantiles): the squared error
+ * sum_j (f(x_j) - y_j)^2 minimised by full-batch resilient gradient descent
+ * (each parameter moves by its own step against the sign of its gradient;
+ * the step grows by 1.2 while the sign holds and halves, without a move,
+ * when it flips), `iters` iterations.  Only gradient signs are used, so the
+ * positive factors 2 and a_h of the exact gradients are dropped; a gradient
+ * through a unit with a_h = 0 is zero.  Start: unit h is the linear ramp
+ * from knot h P/H to knot (h+1) P/H with weight 1/H, i.e. f starts as the
+ * H-piece interpolation of the knots.
+ *
+ * params: omega[H], beta[H], alpha[H], f0, inv (3H + 2 floats).
+ * Every operation is an IEEE binary32 operation with round-to-nearest, in
+ * the order written (the file is compiled without contraction). */
+#define ORACLE_MLP_H 32
+
+static float mlp_forward(const float *om, const float *be, const float *al, float u)
+{
+    float f = 0.0f;
+    for (int h = 0; h < ORACLE_MLP_H; h++) {
+        volatile float w = om[h] * om[h];
+        volatile float t = w * u;
+        volatile float t2 = t + be[h];
+        float c = fminf(fmaxf(t2, 0.0f), 1.0f);
+        volatile float a = al[h] * al[h];
+        volatile float term = a * c;
+        f = f + term;
+    }
+    return f;
+}
+
+static void rprop(float *p, float *step, int *sprev, float g)
+{
+    int sg = (g > 0.0f) - (g < 0.0f);
+    if (sg * *sprev < 0) {
+        *step = *step * 0.5f;
+        *sprev = 0;
+        return;
+    }
+    if (sg * *sprev > 0) *step = *step * 1.2f;
+    if (sg > 0) *p = *p - *step;
+    if (sg < 0) *p = *p + *step;
+    *sprev = sg;
+}
+
+void oracle_mlp_train(const float *q, uint32_t P, uint32_t iters, float *params)
+{
+    const int H = ORACLE_MLP_H;
+    float om[ORACLE_MLP_H], be[ORACLE_MLP_H], al[ORACLE_MLP_H];
+    float so[ORACLE_MLP_H], sb[ORACLE_MLP_H], sa[ORACLE_MLP_H];
+    int po[ORACLE_MLP_H], pb[ORACLE_MLP_H], pa[ORACLE_MLP_H];
+    float *r = (float *)malloc((size_t)(P + 1) * sizeof(float));
+    for (int h = 0; h < H; h++) {
+        float lo = q[(uint64_t)h * P / H], hi = q[(uint64_t)(h + 1) * P / H];
+        volatile float den = hi - lo;
+        float w = hi > lo ? 1.0f / den : 1048576.0f;
+        om[h] = sqrtf(w);
+        volatile float lw = lo * w;
+        be[h] = -lw;
+        al[h] = sqrtf(1.0f / (float)H);
+        so[h] = 0.001f * om[h];
+        sb[h] = 0.001f;
+        sa[h] = 0.001f * al[h];
+        po[h] = pb[h] = pa[h] = 0;
+    }
+    for (uint32_t it = 0; it < iters; it++) {
+        for (uint32_t j = 0; j <= P; j++) {
+            volatile float y = (float)j / (float)P;
+            r[j] = mlp_forward(om, be, al, q[j]) - y;
+        }
+        for (int h = 0; h < H; h++) {
+            volatile float w = om[h] * om[h];
+            volatile float a = al[h] * al[h];
+            float ga = 0.0f, gw = 0.0f, gb = 0.0f;
+            for (uint32_t j = 0; j <= P; j++) {
+                volatile float t = w * q[j];
+                volatile float t2 = t + be[h];
+                float c = fminf(fmaxf(t2, 0.0f), 1.0f);
+                volatile float rc = r[j] * c;
+                ga = ga + rc;
+                if (t2 > 0.0f && t2 < 1.0f) {
+                    volatile float rx = r[j] * q[j];
+                    gw = gw + rx;
+                    gb = gb + r[j];
+                }
+            }
+            if (!(a > 0.0f)) gw = gb = 0.0f;
+            volatile float dom = gw * om[h];
+            volatile float dal = ga * al[h];
+            rprop(&om[h], &so[h], &po[h], dom);
+            rprop(&be[h], &sb[h], &pb[h], gb);
+            rprop(&al[h], &sa[h], &pa[h], dal);
+        }
+    }
+    for (int h = 0; h < H; h++) {
+        params[h] = om[h];
+        params[H + h] = be[h];
+        params[2 * H + h] = al[h];
+    }
+    float f0 = mlp_forward(om, be, al, 0.0f);
+    float f1 = mlp_forward(om, be, al, q[P]);
+    volatile float span = f1 - f0;
+    params[3 * H] = f0;
+    params[3 * H + 1] = f1 > f0 ? 1.0f / span : 0.0f;
+    free(r);
+}
+
+uint32_t oracle_mlp_bucket(uint64_t key, uint64_t mn, uint64_t mx, const float *params, uint32_t k)
+{
+    const int H = ORACLE_MLP_H;
+    float u = oracle_pwl_normalise(key, mn, mx);
+    float f = mlp_forward(params, params + H, params + 2 * H, u);
+    volatile float d = f - params[3 * H];
+    volatile float g = d * params[3 * H + 1];
+    float gc = fminf(fmaxf(g, 0.0f), 0.99999994f); /* 1 - 2^-24 */
+    volatile float t = gc * (float)k;
+    uint32_t b = (uint32_t)t;
+    return b > k - 1 ? k - 1 : b;
+}
+
+void oracle_mlp_buckets(const uint64_t *keys, uint64_t n, uint64_t mn, uint64_t mx, const float *params,
+                        uint32_t k, uint32_t *out)
+{
+    for (uint64_t i = 0; i < n; i++) out[i] = oracle_mlp_bucket(keys[i], mn, mx, params, k);
+}
+
+/* f(u) of trained parameters (for the pins: monotonicity, the start state). */
+float oracle_mlp_eval(const float *params, float u)
+{
+    return mlp_forward(params, params + ORACLE_MLP_H, params + 2 * ORACLE_MLP_H, u);
 }

@@ -26,7 +26,8 @@ _lib = None
 OK = 0
 ERR_INVALID, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_BAD_OFFSETS, ERR_CAPACITY, ERR_INTERNAL = (
     -1, -2, -3, -4, -5, -6, -7)
-MAP_ZSCORE, MAP_LEARNED = 0, 1
+MAP_ZSCORE, MAP_LEARNED, MAP_MLP = 0, 1, 2
+MAPINFO_ZSCORE, MAPINFO_LEARNED, MAPINFO_RANGE, MAPINFO_MLP = 0, 1, 2, 3
 KEY_TYPES = {"u64": 0, "i64": 1, "f64": 2}
 NOT_TUNED = 1
 TUNE_FORCE = 1
@@ -121,6 +122,7 @@ class MapInfo(ctypes.Structure):
         ("r", ctypes.c_float * 256),
         ("learned_max_load", ctypes.c_uint32),
         ("zscore_max_load", ctypes.c_uint32),
+        ("mlp", ctypes.c_float * 98),
     ]
 
 

@@ -61,7 +61,10 @@ __global__ void __launch_bounds__(BLOCK, 2) k_persistent(const __grid_constant__
             case T_MPART: task_mpart(P, load_item(P, arg + tile), s, pp); break;
             case T_FINISH:
                 if (threadIdx.x == 0 && j + 1 < count) prefetch_item_l2(P, load_item(P, arg + tile + 1));
-                task_finish(P, load_item(P, arg + tile), s, pp);
+                if (P.kv)
+                    task_finish<true>(P, load_item(P, arg + tile), s, pp);
+                else
+                    task_finish<false>(P, load_item(P, arg + tile), s, pp);
                 break;
             case T_COPY: task_copy(P, arg, tile); break;
             case T_DUMP: task_dump(P, arg, tile, s, pp); break;
@@ -420,7 +423,7 @@ int get_workspace(cudaStream_t stream, unsigned long long n, unsigned long long 
 bool opts_valid(const zsort_opts &o)
 {
     if (o.struct_size != sizeof(zsort_opts)) return false;
-    if (o.mapper > 1) return false;
+    if (o.mapper > ZSORT_MAP_MLP) return false;
     if (o.kmax < MIN_K || o.kmax > NB_MAX || (o.kmax & (o.kmax - 1))) return false;
     if (o.leaf_target < 16 || o.leaf_target > (1u << 24)) return false;
     if (o.large_min < (uint32_t)LEAF_CAP || o.large_min >= (1u << 30)) return false;
@@ -800,7 +803,10 @@ int zsort_map_buckets(const uint64_t *keys, uint64_t n, const zsort_opts *opts, 
     ce = cudaMemcpy(&S, ws->P.segs, sizeof(Seg), cudaMemcpyDeviceToHost);
     if (ce != cudaSuccess) return cuda_err(ce);
     std::memset(info, 0, sizeof(*info));
-    info->map = S.kind == MAP_Z ? ZSORT_MAP_ZSCORE : (S.kind == MAP_PWL ? ZSORT_MAP_LEARNED : 2u);
+    info->map = S.kind == MAP_Z     ? ZSORT_MAPINFO_ZSCORE
+                : S.kind == MAP_PWL ? ZSORT_MAPINFO_LEARNED
+                : S.kind == MAP_MLP ? ZSORT_MAPINFO_MLP
+                                    : ZSORT_MAPINFO_RANGE;
     info->k = S.k;
     info->min = S.mn;
     info->max = S.mx;
@@ -817,6 +823,7 @@ int zsort_map_buckets(const uint64_t *keys, uint64_t n, const zsort_opts *opts, 
         if (ce != cudaSuccess) return cuda_err(ce);
         std::memcpy(info->q, t, sizeof(info->q));
         std::memcpy(info->r, t + PWL_P + 1, sizeof(info->r));
+        std::memcpy(info->mlp, t + PWL_MLP_OFF, sizeof(info->mlp));
         info->trained = 1;
     }
     return ZSORT_OK;

@@ -41,7 +41,10 @@ constexpr int ST_BAD_OFFSETS = -5;
 constexpr int ST_CAPACITY = -6;
 constexpr int ST_INTERNAL = -7;
 
-enum MapKind : uint32_t { MAP_Z = 0, MAP_PWL = 1, MAP_RANGE = 2 };
+enum MapKind : uint32_t { MAP_Z = 0, MAP_PWL = 1, MAP_RANGE = 2, MAP_MLP = 3 };
+constexpr int MLP_H = 32;                 // hidden units of the MLP map
+constexpr int MLP_ITERS = 128;            // its training iterations
+constexpr int MLP_TABLE = 3 * MLP_H + 2;  // w[H], b[H], a[H], f0, inv
 enum TaskType : uint32_t {
     T_NONE = 0,
     T_LSTATS = 1,    // large segment: statistics tile
@@ -134,7 +137,7 @@ struct Params {
     uint32_t *plan_out;          // map inspection: bucket of every key (else null)
     uint32_t user_aligned;       // caller's keys and vals 16-byte aligned: bulk copies allowed
     uint32_t kv;                 // 1: (key, payload) pairs; 0: keys only (vals == null)
-    float *pwl;         // segcap * PWL_STRIDE: breakpoints q[0..P], reciprocals r[0..P)
+    float *pwl;         // segcap * PWL_STRIDE: breakpoints q[0..P], reciprocals r[0..P), MLP table
     unsigned long long *trainbuf; // traincap * 2 * SAMPLE_MAX sampled keys (ping-pong)
     uint32_t traincap;
     // options
@@ -356,7 +359,8 @@ __device__ void moments_from_sums(unsigned long long n, unsigned long long mn,
 // compute bit-identical buckets.  Every map is monotone non-decreasing in
 // the key, which is all the sort's exactness needs.
 constexpr int PWL_BINS = 2048;  // learned map: bins of the normalised key's float bits
-constexpr int PWL_STRIDE = 2 * PWL_P + 1;
+constexpr int PWL_MLP_OFF = 2 * PWL_P + 1;            // per-segment table: q[0..P], r[0..P), MLP table
+constexpr int PWL_STRIDE = PWL_MLP_OFF + MLP_TABLE;
 struct MapSm {
     unsigned long long mn;
     uint32_t kind, k, K, rshift, rmult, zsh;
@@ -364,6 +368,7 @@ struct MapSm {
     float q[PWL_P + 1];          // learned map: breakpoints
     float r[PWL_P];              // learned map: 1 / (q[s+1] - q[s]), 0 for an empty piece
     uint8_t seg0[PWL_BINS + 1];  // learned map: piece holding the lower edge of each bin
+    float mlp[MLP_TABLE];        // MLP map: w = omega^2, b, a = alpha^2 per unit, f0, inv
 };
 
 // fl32(d), round to nearest even, without the 64-bit conversion instruction:
@@ -422,6 +427,29 @@ __device__ __forceinline__ MapK map_regs(const MapSm &m)
     return r;
 }
 
+// MLP map: f(u) = sum_h a_h * clamp(w_h * u + b_h, 0, 1) with a_h, w_h >= 0
+// (summed in unit order), g = (f(u) - f0) * inv clipped to [0, 1 - 2^-24],
+// bucket = min(k - 1, trunc(g * k)).  Every step is a monotone binary32
+// rounding of a monotone function, so the map is non-decreasing in u.
+__device__ __forceinline__ float mlp_f(const float *t, float u)
+{
+    float f = 0.0f;
+#pragma unroll 8
+    for (int h = 0; h < MLP_H; h++) {
+        const float c = fminf(fmaxf(__fadd_rn(__fmul_rn(t[h], u), t[MLP_H + h]), 0.0f), 1.0f);
+        f = __fadd_rn(f, __fmul_rn(t[2 * MLP_H + h], c));
+    }
+    return f;
+}
+__device__ __forceinline__ uint32_t mlp_bucket_u(const float *t, float u, uint32_t k)
+{
+    const float g = __fmul_rn(__fsub_rn(mlp_f(t, u), t[3 * MLP_H]), t[3 * MLP_H + 1]);
+    const float gc = fminf(fmaxf(g, 0.0f), 0x1.fffffep-1f);
+    const uint32_t b = __float2uint_rz(__fmul_rn(gc, (float)k));
+    return b < k ? b : k - 1;
+}
+
+// Eq. 1, the range map or the piecewise-linear map (not the MLP map).
 __device__ __forceinline__ uint32_t map_key(const MapK &r, const MapSm &m, unsigned long long key)
 {
     const unsigned long long d = key - r.mn;
@@ -437,6 +465,20 @@ __device__ __forceinline__ uint32_t map_key(const MapK &r, const MapSm &m, unsig
         return __umulhi((uint32_t)(d >> r.rshift), r.rmult);
     }
     return pwl_bucket_u(m, __fmul_rn(u64_to_f32_rn(d), r.escale));
+}
+
+// The MLP map of a key (its own instantiation of the tile loops, so that the
+// other maps' code keeps its registers).
+__device__ __forceinline__ uint32_t map_key_mlp(const MapK &r, const MapSm &m, unsigned long long key)
+{
+    return mlp_bucket_u(m.mlp, __fmul_rn(u64_to_f32_rn(key - r.mn), r.escale), r.k);
+}
+
+// Any map, MLP included (inspection only).
+__device__ __noinline__ uint32_t map_key_any(const MapSm &m, unsigned long long key)
+{
+    const MapK r = map_regs(m);
+    return r.kind == MAP_MLP ? map_key_mlp(r, m, key) : map_key(r, m, key);
 }
 
 __device__ __forceinline__ uint32_t map_key(const MapSm &m, unsigned long long key)

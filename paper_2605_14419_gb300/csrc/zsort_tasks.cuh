@@ -162,7 +162,7 @@ __device__ __forceinline__ uint32_t choose_k(const Params &P, uint32_t len)
 // its map (the statistics decide later whether Eq. 1 applies at all).
 __device__ __forceinline__ bool wants_learned_map(const Params &P, uint32_t len, uint32_t k, uint32_t level)
 {
-    return P.mapper == 1 && len >= P.learn_min && P.sample <= len && k >= (uint32_t)PWL_P && level < P.guard_level;
+    return P.mapper >= 1 && len >= P.learn_min && P.sample <= len && k >= (uint32_t)PWL_P && level < P.guard_level;
 }
 
 // Takes a training slot for a new large (sub)array (any thread): INVALID if
@@ -270,6 +270,10 @@ __device__ void load_seg_map(const Params &P, uint32_t sid, SmemTile &s)
         s.map.escale = __ldcg(&S->escale);
         s.map.rshift = __ldcg(&S->rshift);
         s.map.rmult = __ldcg(&S->rmult);
+    }
+    if (kind == MAP_MLP) {
+        const float *t = P.pwl + (size_t)sid * PWL_STRIDE + PWL_MLP_OFF;
+        for (int j = threadIdx.x; j < MLP_TABLE; j += BLOCK) s.map.mlp[j] = __ldcg(t + j);
     }
     if (kind == MAP_PWL) {
         const float *t = P.pwl + (size_t)sid * PWL_STRIDE;
@@ -398,13 +402,14 @@ __device__ __forceinline__ void body_stats(Acc &a, uint32_t cnt, const unsigned 
 
 // Histogram of the tile's buckets into s.hist: one shared-memory atomic per
 // key, except when a whole warp slot shares one bucket (duplicate runs).
+template <bool MLP>
 __device__ __forceinline__ void body_hist(SmemTile &s, const MapK &mk, uint32_t cnt, const unsigned long long *sk)
 {
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int i = 0; i < IPT; i++) {
         const uint32_t p = slot_index(i);
-        const uint32_t b = p < cnt ? map_key(mk, s.map, sk[p]) : INVALID;
+        const uint32_t b = p >= cnt ? INVALID : (MLP ? map_key_mlp(mk, s.map, sk[p]) : map_key(mk, s.map, sk[p]));
         const uint32_t b0 = __shfl_sync(0xffffffffu, b, 0);
         if (__all_sync(0xffffffffu, b == b0)) {
             if (lane == 0 && b0 != INVALID) atomicAdd(&s.hist[b0], 32u);
@@ -412,6 +417,16 @@ __device__ __forceinline__ void body_hist(SmemTile &s, const MapK &mk, uint32_t 
             atomicAdd(&s.hist[b], 1u);
         }
     }
+}
+
+// Histogram of [start, start+len) into s.hist (its own instantiation per map
+// family, so that each keeps its registers).
+template <bool MLP>
+__device__ __noinline__ void hist_stream(const Params &P, SmemTile &s, Pipe &pp, const uint64_t *src, bool bulk,
+                                         unsigned long long start, unsigned long long len, const MapK mk)
+{
+    stream_tiles<false>(P, s, pp, src, nullptr, bulk, start, len,
+                        [&](uint32_t, uint32_t cnt, unsigned long long *sk, uint32_t *) { body_hist<MLP>(s, mk, cnt, sk); });
 }
 
 // Stable scatter of [start, start+len) of a (sub)array whose map is in s.map
@@ -422,7 +437,7 @@ __device__ __forceinline__ void body_hist(SmemTile &s, const MapK &mk, uint32_t 
 // for the learned map, whose buckets are staged.  Four barriers a tile: the
 // tile's bulk copy is issued once every thread has left the tile that last
 // used its buffer, and each warp clears its own bucket counters.
-template <int NBITS>
+template <int NBITS, bool MLP, bool KV>
 __device__ __noinline__ void scatter_stream(const Params &P, SmemTile &s, Pipe &pp, const uint64_t *srck,
                                             const uint32_t *srcv, bool bulk, unsigned long long start,
                                             unsigned long long len, uint64_t *dstk, uint32_t *dstv, uint32_t seglen)
@@ -431,14 +446,14 @@ __device__ __noinline__ void scatter_stream(const Params &P, SmemTile &s, Pipe &
     if (nt == 0) return;
     const MapK mk = map_regs(s.map);
     const uint32_t k = mk.k;
-    const bool stage_b = mk.kind == MAP_PWL;
-    const bool kv = P.kv != 0;
+    const bool stage_b = mk.kind == MAP_PWL || mk.kind == MAP_MLP;  // costly maps: stage the bucket
+    constexpr bool kv = KV;  // payloads move with the keys
     // the runs written per tile end inside lines that the next tile (or the
     // neighbouring chunk) completes: keep those lines in L2 until then
     const unsigned long long pol_front = policy_evict_last();
     rank_zero_warp(k, s);
     if (bulk && threadIdx.x == 0)
-        stream_issue<true>(P, s, 0, srck, srcv, start, (uint32_t)min(len, (unsigned long long)TILE));
+        stream_issue<KV>(P, s, 0, srck, srcv, start, (uint32_t)min(len, (unsigned long long)TILE));
     bool err = false;
     for (uint32_t t = 0; t < nt; t++) {
         const int w = t & 1;
@@ -453,7 +468,7 @@ __device__ __noinline__ void scatter_stream(const Params &P, SmemTile &s, Pipe &
             ok = mbar_wait(&s.bar[w], pp.uses[w] & 1u, P.wait_ns);
             pp.uses[w]++;
             if (a + cnt > (P.n & ~3ull)) {  // the array's last elements: plain loads (uniform branch)
-                stream_fix_tail<true>(P, sk, sv, srck, srcv, a, cnt);
+                stream_fix_tail<KV>(P, sk, sv, srck, srcv, a, cnt);
                 __syncthreads();
             }
         } else {
@@ -473,7 +488,7 @@ __device__ __noinline__ void scatter_stream(const Params &P, SmemTile &s, Pipe &
             const bool in = p < cnt;
             x[i] = in ? sk[p] : 0ull;
             v[i] = in && kv ? sv[p] : 0u;
-            b[i] = in ? map_key(mk, s.map, x[i]) : 0u;
+            b[i] = !in ? 0u : (MLP ? map_key_mlp(mk, s.map, x[i]) : map_key(mk, s.map, x[i]));
         }
         rank_peers<IPT, NBITS>(b, cnt, peers);
         rank_leaders<IPT>(b, peers, pos, s);
@@ -487,7 +502,7 @@ __device__ __noinline__ void scatter_stream(const Params &P, SmemTile &s, Pipe &
         }
         if (bulk && t + 1 < nt && threadIdx.x == 0) {
             const unsigned long long an = a + TILE;
-            stream_issue<true>(P, s, w ^ 1, srck, srcv, an, (uint32_t)min((unsigned long long)TILE, start + len - an));
+            stream_issue<KV>(P, s, w ^ 1, srck, srcv, an, (uint32_t)min((unsigned long long)TILE, start + len - an));
         }
         rank_scan<true>(k, s);
         rank_place<IPT>(b, pos, s);
@@ -518,16 +533,38 @@ __device__ __noinline__ void scatter_stream(const Params &P, SmemTile &s, Pipe &
     __syncthreads();
 }
 
+// One instantiation per payload mode, map family (MLP or not) and ballot
+// width, so that each keeps its own registers.
+template <bool KV>
+__device__ __forceinline__ void scatter_pick(const Params &P, SmemTile &s, Pipe &pp, const uint64_t *srck,
+                                             const uint32_t *srcv, bool bulk, unsigned long long start,
+                                             unsigned long long len, uint64_t *dstk, uint32_t *dstv, uint32_t seglen,
+                                             uint32_t k)
+{
+    if (s.map.kind == MAP_MLP) {  // k >= 256 for a learned map
+        switch (rank_bits(k)) {
+        case 8: scatter_stream<8, true, KV>(P, s, pp, srck, srcv, bulk, start, len, dstk, dstv, seglen); break;
+        case 9: scatter_stream<9, true, KV>(P, s, pp, srck, srcv, bulk, start, len, dstk, dstv, seglen); break;
+        default: scatter_stream<10, true, KV>(P, s, pp, srck, srcv, bulk, start, len, dstk, dstv, seglen); break;
+        }
+        return;
+    }
+    switch (rank_bits(k)) {
+    case 7: scatter_stream<7, false, KV>(P, s, pp, srck, srcv, bulk, start, len, dstk, dstv, seglen); break;
+    case 8: scatter_stream<8, false, KV>(P, s, pp, srck, srcv, bulk, start, len, dstk, dstv, seglen); break;
+    case 9: scatter_stream<9, false, KV>(P, s, pp, srck, srcv, bulk, start, len, dstk, dstv, seglen); break;
+    default: scatter_stream<10, false, KV>(P, s, pp, srck, srcv, bulk, start, len, dstk, dstv, seglen); break;
+    }
+}
+
 __device__ void scatter_dispatch(const Params &P, SmemTile &s, Pipe &pp, const uint64_t *srck, const uint32_t *srcv,
                                  bool bulk, unsigned long long start, unsigned long long len, uint64_t *dstk,
                                  uint32_t *dstv, uint32_t seglen, uint32_t k)
 {
-    switch (rank_bits(k)) {
-    case 7: scatter_stream<7>(P, s, pp, srck, srcv, bulk, start, len, dstk, dstv, seglen); break;
-    case 8: scatter_stream<8>(P, s, pp, srck, srcv, bulk, start, len, dstk, dstv, seglen); break;
-    case 9: scatter_stream<9>(P, s, pp, srck, srcv, bulk, start, len, dstk, dstv, seglen); break;
-    default: scatter_stream<10>(P, s, pp, srck, srcv, bulk, start, len, dstk, dstv, seglen); break;
-    }
+    if (P.kv)
+        scatter_pick<true>(P, s, pp, srck, srcv, bulk, start, len, dstk, dstv, seglen, k);
+    else
+        scatter_pick<false>(P, s, pp, srck, srcv, bulk, start, len, dstk, dstv, seglen, k);
 }
 
 // ------------------------------------------------------------ children
@@ -1016,6 +1053,102 @@ __device__ unsigned long long sample_select(const unsigned long long *X, uint32_
     return lo;
 }
 
+// MLP map training state (aliases the tile buffers during the fit).
+struct MlpTrain {
+    float om[MLP_H], be[MLP_H], al[MLP_H];  // w = om^2, b = be, a = al^2
+    float so[MLP_H], sb[MLP_H], sa[MLP_H];  // step of each parameter
+    int po[MLP_H], pb[MLP_H], pa[MLP_H];    // sign of its last gradient
+    float r[PWL_P + 1];                     // residual at each knot
+};
+static_assert(sizeof(MlpTrain) <= sizeof(TileBuf) * 2, "MLP training state fits the tile buffers");
+
+__device__ __forceinline__ float mlp_forward_train(const MlpTrain &T, float u)
+{
+    float f = 0.0f;
+    for (int h = 0; h < MLP_H; h++) {
+        const float w = __fmul_rn(T.om[h], T.om[h]);
+        const float c = fminf(fmaxf(__fadd_rn(__fmul_rn(w, u), T.be[h]), 0.0f), 1.0f);
+        f = __fadd_rn(f, __fmul_rn(__fmul_rn(T.al[h], T.al[h]), c));
+    }
+    return f;
+}
+
+__device__ __forceinline__ void rprop_step(float &p, float &step, int &sprev, float g)
+{
+    const int sg = (g > 0.0f) - (g < 0.0f);
+    if (sg * sprev < 0) {
+        step = __fmul_rn(step, 0.5f);
+        sprev = 0;
+        return;
+    }
+    if (sg * sprev > 0) step = __fmul_rn(step, 1.2f);
+    if (sg > 0) p = __fsub_rn(p, step);
+    if (sg < 0) p = __fadd_rn(p, step);
+    sprev = sg;
+}
+
+// The MLP map fitted to the knots (q[j], j / P) of the piecewise-linear map
+// in s.map.q: a 2-layer MLP with positive weights (w = omega^2, a = alpha^2)
+// and clamp(., 0, 1) hidden units, f(u) = sum_h a_h clamp(w_h u + b_h, 0, 1),
+// started as the MLP_H-piece interpolation of the knots and trained by
+// full-batch resilient gradient descent on the squared error, MLP_ITERS
+// iterations; one thread per knot for the residuals, one per unit for its
+// gradients (each sum in a fixed order, so the result is reproducible).
+// Writes w, b, a, f0 = f(0), inv = 1 / (f(q[P]) - f0) to s.map.mlp and t.
+__device__ void mlp_train(SmemTile &s, float *t)
+{
+    MlpTrain &T = *reinterpret_cast<MlpTrain *>(&s.u);
+    const float *q = s.map.q;
+    const int h = threadIdx.x;
+    if (h < MLP_H) {
+        const float lo = q[h * PWL_P / MLP_H], hi = q[(h + 1) * PWL_P / MLP_H];
+        const float w = hi > lo ? __fdiv_rn(1.0f, __fsub_rn(hi, lo)) : 1048576.0f;
+        T.om[h] = __fsqrt_rn(w);
+        T.be[h] = -__fmul_rn(lo, w);
+        T.al[h] = __fsqrt_rn(__fdiv_rn(1.0f, (float)MLP_H));
+        T.so[h] = __fmul_rn(0.001f, T.om[h]);
+        T.sb[h] = 0.001f;
+        T.sa[h] = __fmul_rn(0.001f, T.al[h]);
+        T.po[h] = T.pb[h] = T.pa[h] = 0;
+    }
+    __syncthreads();
+    for (int it = 0; it < MLP_ITERS; it++) {
+        for (int j = threadIdx.x; j <= PWL_P; j += BLOCK)
+            T.r[j] = __fsub_rn(mlp_forward_train(T, q[j]), __fdiv_rn((float)j, (float)PWL_P));
+        __syncthreads();
+        if (h < MLP_H) {
+            const float w = __fmul_rn(T.om[h], T.om[h]), a = __fmul_rn(T.al[h], T.al[h]);
+            float ga = 0.0f, gw = 0.0f, gb = 0.0f;
+            for (int j = 0; j <= PWL_P; j++) {
+                const float t2 = __fadd_rn(__fmul_rn(w, q[j]), T.be[h]);
+                const float c = fminf(fmaxf(t2, 0.0f), 1.0f);
+                ga = __fadd_rn(ga, __fmul_rn(T.r[j], c));
+                if (t2 > 0.0f && t2 < 1.0f) {
+                    gw = __fadd_rn(gw, __fmul_rn(T.r[j], q[j]));
+                    gb = __fadd_rn(gb, T.r[j]);
+                }
+            }
+            if (!(a > 0.0f)) gw = gb = 0.0f;
+            rprop_step(T.om[h], T.so[h], T.po[h], __fmul_rn(gw, T.om[h]));
+            rprop_step(T.be[h], T.sb[h], T.pb[h], gb);
+            rprop_step(T.al[h], T.sa[h], T.pa[h], __fmul_rn(ga, T.al[h]));
+        }
+        __syncthreads();
+    }
+    if (h < MLP_H) {
+        s.map.mlp[h] = __fmul_rn(T.om[h], T.om[h]);
+        s.map.mlp[MLP_H + h] = T.be[h];
+        s.map.mlp[2 * MLP_H + h] = __fmul_rn(T.al[h], T.al[h]);
+    }
+    if (h == 0) {
+        const float f0 = mlp_forward_train(T, 0.0f), f1 = mlp_forward_train(T, q[PWL_P]);
+        s.map.mlp[3 * MLP_H] = f0;
+        s.map.mlp[3 * MLP_H + 1] = f1 > f0 ? __fdiv_rn(1.0f, __fsub_rn(f1, f0)) : 0.0f;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < MLP_TABLE; j += BLOCK) t[j] = s.map.mlp[j];
+}
+
 // Learned map, second half (after the statistics and the sample): breakpoints
 // at the 1/256 quantiles of the normalised sample and their reciprocal
 // widths, then the load test that keeps Eq. 1 as the fallback.
@@ -1062,6 +1195,8 @@ __device__ __noinline__ void task_lfit(const Params &P, uint32_t sid, SmemTile &
     }
     build_pwl_bins(s.map);
     __syncthreads();
+    const bool mlp = P.mapper == 2;
+    if (mlp) mlp_train(s, t + PWL_MLP_OFF);  // the MLP map replaces the piecewise-linear one
     // load test on the sample: largest learned bucket vs largest Eq. 1 bucket
     for (uint32_t i0 = 0; i0 < m; i0 += BLOCK * IPT) {
         unsigned long long x[IPT];
@@ -1074,7 +1209,8 @@ __device__ __noinline__ void task_lfit(const Params &P, uint32_t sid, SmemTile &
         for (int u = 0; u < IPT; u++) {
             if (i0 + threadIdx.x + u * BLOCK < m) {
                 const unsigned long long d = x[u] - mn;
-                atomicAdd(&s.hist[pwl_bucket_u(s.map, __fmul_rn(u64_to_f32_rn(d), escale))], 1u);
+                const float u = __fmul_rn(u64_to_f32_rn(d), escale);
+                atomicAdd(&s.hist[mlp ? mlp_bucket_u(s.map.mlp, u, k) : pwl_bucket_u(s.map, u)], 1u);
                 const uint32_t bz = __float2uint_rz(__fmul_rn(__uint2float_rz((uint32_t)(d >> zsh)), zc));
                 atomicAdd(&s.cursor[bz < k ? bz : k - 1], 1u);
             }
@@ -1100,11 +1236,12 @@ __device__ __noinline__ void task_lfit(const Params &P, uint32_t sid, SmemTile &
             mz = max(mz, (uint32_t)s.red64[WARPS + w]);
         }
         const bool ok = (float)ml <= P.fallback_ratio * (float)m / (float)k && ml <= mz;
-        S->kind = ok ? MAP_PWL : MAP_Z;
+        const uint32_t learned = mlp ? (uint32_t)MAP_MLP : (uint32_t)MAP_PWL;
+        S->kind = ok ? learned : MAP_Z;
         S->max_learned = ml;
         S->max_z = mz;
         atomicAdd(ok ? &P.ctl->n_learn_ok : &P.ctl->n_learn_rej, 1ull);
-        if (__ldcg(&S->level) == 0 && sid == 0) P.ctl->top_map = ok ? MAP_PWL : MAP_Z;
+        if (__ldcg(&S->level) == 0 && sid == 0) P.ctl->top_map = ok ? learned : MAP_Z;
         publish1(P, P.plan_out ? T_DUMP : T_LHIST, sid, chunks);
     }
 }
@@ -1120,7 +1257,7 @@ __device__ __noinline__ void task_dump(const Params &P, uint32_t sid, uint32_t c
     stream_tiles<false>(P, s, pp, keys_of(P, ch.buf), nullptr, bulk_ok(P, ch.buf), ch.start, ch.len,
                         [&](uint32_t t, uint32_t cnt, unsigned long long *sk, uint32_t *) {
                             const unsigned long long a = ch.start + (unsigned long long)t * TILE;
-                            for (uint32_t p = threadIdx.x; p < cnt; p += BLOCK) __stcg(out + a + p, map_key(s.map, sk[p]));
+                            for (uint32_t p = threadIdx.x; p < cnt; p += BLOCK) __stcg(out + a + p, map_key_any(s.map, sk[p]));
                         });
 }
 
@@ -1139,8 +1276,13 @@ __device__ __noinline__ void task_lhist(const Params &P, uint32_t sid, uint32_t 
     for (uint32_t q = threadIdx.x; q < k; q += BLOCK) s.hist[q] = 0;
     __syncthreads();
     const uint64_t *src = keys_of(P, ch.buf);
-    stream_tiles<false>(P, s, pp, src, nullptr, bulk_ok(P, ch.buf), ch.start, ch.len,
-                        [&](uint32_t, uint32_t cnt, unsigned long long *sk, uint32_t *) { body_hist(s, mk, cnt, sk); });
+    if (mk.kind == MAP_MLP)
+        hist_stream<true>(P, s, pp, src, bulk_ok(P, ch.buf), ch.start, ch.len, mk);
+    else
+        stream_tiles<false>(P, s, pp, src, nullptr, bulk_ok(P, ch.buf), ch.start, ch.len,
+                            [&](uint32_t, uint32_t cnt, unsigned long long *sk, uint32_t *) {
+                                body_hist<false>(s, mk, cnt, sk);
+                            });
     uint32_t *status = P.status + ch.sbase;
     uint32_t *row = status + (size_t)c * k;
     uint32_t *offs = status + (size_t)ch.chunks * k + (size_t)c * k;
@@ -1309,7 +1451,7 @@ __device__ __noinline__ void task_mpart(const Params &P, const Item it, SmemTile
     for (uint32_t q = threadIdx.x; q < k; q += BLOCK) s.hist[q] = 0;
     __syncthreads();
     stream_tiles<false>(P, s, pp, srck, nullptr, bulk, off, len,
-                        [&](uint32_t, uint32_t cnt, unsigned long long *sk, uint32_t *) { body_hist(s, mk, cnt, sk); });
+                        [&](uint32_t, uint32_t cnt, unsigned long long *sk, uint32_t *) { body_hist<false>(s, mk, cnt, sk); });
     block_exclusive_scan(s.hist, s.bs, k, s.wsum);
     for (uint32_t q = threadIdx.x; q < k; q += BLOCK) s.cursor[q] = s.bs[q];
     __syncthreads();
@@ -1413,6 +1555,7 @@ constexpr uint32_t LEAF_FAST_MAX = 32;  // largest sub-bucket the fast path rank
 // rank inside its sub-bucket on (key, leaf position) -- a total order whose
 // sorted sequence is the stable sort -- and goes straight to that rank of the
 // output (consecutive staged pairs have nearly consecutive ranks).
+template <bool KV>
 __device__ __forceinline__ void finish_fast(SmemTile &s, unsigned long long *key, uint32_t *val, uint32_t len,
                                          unsigned long long mn, uint32_t rs, uint32_t rm, uint32_t M2,
                                          const unsigned long long (&kk)[LEAF_IPT], const uint32_t (&vv)[LEAF_IPT],
@@ -1452,7 +1595,7 @@ __device__ __forceinline__ void finish_fast(SmemTile &s, unsigned long long *key
         }
         if (p < len) {
             __stcg(dk + r, xk);
-            if (dv) __stcg(dv + r, val[p]);
+            if (KV) __stcg(dv + r, val[p]);
         }
     }
 }
@@ -1461,6 +1604,7 @@ __device__ __forceinline__ void finish_fast(SmemTile &s, unsigned long long *key
 // keys): sub-buckets by the range map placed in input order by the ballot
 // ranking, then insertion sort per sub-bucket (no moves among equal keys); a
 // bitonic sort on (key, position) if a sub-bucket needs too many moves.
+template <bool KV>
 __device__ __noinline__ void finish_stable(const Params &P, SmemTile &s, unsigned long long *key, uint32_t *val,
                                            uint32_t len, unsigned long long mn, unsigned long long mx,
                                            uint64_t *dk, uint32_t *dv)
@@ -1500,7 +1644,7 @@ __device__ __noinline__ void finish_stable(const Params &P, SmemTile &s, unsigne
     }
     for (uint32_t p = threadIdx.x; p < len; p += BLOCK) {
         __stcg(dk + p, key[p]);
-        if (dv) __stcg(dv + p, val[p]);
+        if (KV) __stcg(dv + p, val[p]);
     }
 }
 
@@ -1510,6 +1654,7 @@ __device__ __noinline__ void finish_stable(const Params &P, SmemTile &s, unsigne
 // partition of the leaf into sub-buckets by the range map, an exact counting
 // sort when the key range is smaller than the sub-bucket count, then each
 // sub-bucket ordered (finish_fast / finish_stable).
+template <bool KV>
 __device__ __noinline__ void task_finish(const Params &P, const Item it, SmemTile &s, Pipe &pp)
 {
     const unsigned long long off = it.off;
@@ -1517,7 +1662,7 @@ __device__ __noinline__ void task_finish(const Params &P, const Item it, SmemTil
     const uint64_t *srck = keys_of(P, buf);
     const uint32_t *srcv = vals_of(P, buf);
     uint64_t *dk = P.ukeys + off;
-    uint32_t *dv = P.kv ? P.uvals + off : nullptr;  // keys only: no payload
+    uint32_t *dv = KV ? P.uvals + off : nullptr;  // keys only: no payload
     unsigned long long *key;
     uint32_t *val;
     if (bulk_ok(P, buf)) {
@@ -1525,7 +1670,7 @@ __device__ __noinline__ void task_finish(const Params &P, const Item it, SmemTil
             const unsigned long long a0 = off & ~1ull, a1 = min((off + len + 1) & ~1ull, P.n & ~1ull);
             const unsigned long long b0 = off & ~3ull, b1 = min((off + len + 3) & ~3ull, P.n & ~3ull);
             const uint32_t bk = a1 > a0 ? (uint32_t)(a1 - a0) * 8u : 0u;
-            const uint32_t bv = P.kv && b1 > b0 ? (uint32_t)(b1 - b0) * 4u : 0u;
+            const uint32_t bv = KV && b1 > b0 ? (uint32_t)(b1 - b0) * 4u : 0u;
             mbar_expect_arrive(&s.bar[0], bk + bv);
             if (bk) bulk_g2s(s.u.leaf.key, srck + a0, bk, &s.bar[0]);
             if (bv) bulk_g2s(s.u.leaf.val, srcv + b0, bv, &s.bar[0]);
@@ -1542,7 +1687,7 @@ __device__ __noinline__ void task_finish(const Params &P, const Item it, SmemTil
         const unsigned long long end = off + len;
         for (unsigned long long e = max(off, P.n & ~1ull) + threadIdx.x; e < end; e += BLOCK)
             key[e - off] = __ldcg(srck + e);
-        if (P.kv)
+        if (KV)
             for (unsigned long long e = max(off, P.n & ~3ull) + threadIdx.x; e < end; e += BLOCK)
                 val[e - off] = __ldcg(srcv + e);
     } else {
@@ -1550,7 +1695,7 @@ __device__ __noinline__ void task_finish(const Params &P, const Item it, SmemTil
         val = s.u.leaf.val;
         for (uint32_t i = threadIdx.x; i < len; i += BLOCK) {
             key[i] = __ldcg(srck + off + i);
-            if (P.kv) val[i] = __ldcg(srcv + off + i);
+            if (KV) val[i] = __ldcg(srcv + off + i);
         }
     }
     __syncthreads();
@@ -1562,7 +1707,7 @@ __device__ __noinline__ void task_finish(const Params &P, const Item it, SmemTil
     for (int j = 0; j < LEAF_IPT; j++) {
         const uint32_t p = threadIdx.x + j * BLOCK;
         kk[j] = p < len ? key[p] : 0ull;
-        vv[j] = p < len && P.kv ? val[p] : 0u;
+        vv[j] = p < len && KV ? val[p] : 0u;
         if (p < len) {
             mn = kk[j] < mn ? kk[j] : mn;
             mx = kk[j] > mx ? kk[j] : mx;
@@ -1599,7 +1744,7 @@ __device__ __noinline__ void task_finish(const Params &P, const Item it, SmemTil
                 const uint32_t p = threadIdx.x + j * BLOCK;
                 if (p < len) {
                     __stcg(dk + p, kk[j]);
-                    if (dv) __stcg(dv + p, vv[j]);
+                    if (KV) __stcg(dv + p, vv[j]);
                 }
             }
         }
@@ -1615,7 +1760,7 @@ __device__ __noinline__ void task_finish(const Params &P, const Item it, SmemTil
                 r += (kq < kt) || (kq == kt && q < t);
             }
             __stcg(dk + r, kt);
-            if (dv) __stcg(dv + r, vv[0]);
+            if (KV) __stcg(dv + r, vv[0]);
         }
         return;
     }
@@ -1632,9 +1777,9 @@ __device__ __noinline__ void task_finish(const Params &P, const Item it, SmemTil
         big = big || a[j] >= LEAF_FAST_MAX;
     }
     if (!__syncthreads_or(big))
-        finish_fast(s, key, val, len, mn, rs2, rm2, M2, kk, vv, a, dk, dv);
+        finish_fast<KV>(s, key, val, len, mn, rs2, rm2, M2, kk, vv, a, dk, dv);
     else
-        finish_stable(P, s, key, val, len, mn, mx, dk, dv);
+        finish_stable<KV>(P, s, key, val, len, mn, mx, dk, dv);
 }
 
 // ------------------------------------------------------------ COPY

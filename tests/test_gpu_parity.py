@@ -332,3 +332,40 @@ def test_keys_only_int64_float64_and_segmented():
     z.sort_segmented(k, None, torch.from_numpy(off.view(np.int64)).to(DEV))
     ok, _ = oracle.zsort_segmented(keys, vals, off)
     assert np.array_equal(k.cpu().numpy().view(np.uint64), ok)
+
+
+# ---------------------------------------------------------------- MLP map
+@pytest.mark.parametrize("gen", [inputs.lognormal, inputs.gaussian_mixture, inputs.uniform,
+                                 inputs.dense_interval_u64])
+def test_mlp_map_bit_exact(gen):
+    """MLP map: the device's trained parameters and every key's bucket equal
+    the oracle's (same knots, same binary32 training steps in the same
+    order); a rejected map is checked by the load-test rule."""
+    n, m = 400_000, 65536
+    keys, kd = _map_case(gen, n, 23)
+    opts = z.default_opts(mapper=z.MAP_MLP, learn_min=m, sample=m, kmax=1024)
+    gb, info = z.map_buckets(kd, opts)
+    mn, mx = int(keys.min()), int(keys.max())
+    assert info.trained == 1
+    pos = oracle.sample_positions(opts.seed, n, m).astype(np.int64)
+    q = oracle.pwl_train(keys[pos], mn, mx)
+    assert np.array_equal(np.frombuffer(bytes(info.q), dtype=np.float32), q)
+    p = oracle.mlp_train(q, 128)
+    H = oracle.MLP_H
+    om, be, al = p[:H], p[H:2 * H], p[2 * H:3 * H]
+    want = np.concatenate([om * om, be, al * al, p[3 * H:]]).astype(np.float32)
+    assert np.array_equal(np.frombuffer(bytes(info.mlp), dtype=np.float32), want)
+    k = info.k
+    if info.map == z.MAPINFO_MLP:
+        ob = oracle.mlp_buckets(keys, mn, mx, p, k)
+        assert np.array_equal(gb.cpu().numpy().view(np.uint32), ob)
+    else:
+        assert info.map == z.MAPINFO_ZSCORE
+        assert (info.learned_max_load > opts.fallback_ratio * m / k
+                or info.learned_max_load > info.zscore_max_load)
+
+
+@pytest.mark.parametrize("gen", [inputs.lognormal, inputs.uniform, inputs.gaussian_mixture])
+def test_mlp_mapper_sorts_exactly(gen):
+    keys = gen(3_000_000, 24)
+    assert_same_as_oracle(keys, opts=z.default_opts(mapper=z.MAP_MLP, learn_min=1 << 20))

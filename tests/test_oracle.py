@@ -311,3 +311,65 @@ def test_level1_map_uniform_fractions():
     frac = np.bincount(b.astype(np.int64), minlength=k) / keys.size
     assert np.allclose(frac[: int(k / 1.1547) - 1], 4.0 / np.sqrt(12) / k, rtol=0.05)
     assert frac[k - 1] < 1.0 / k
+
+
+# ---------------------------------------------------------------- MLP map
+def mlp_knot_loss(params, q):
+    return sum((oracle.mlp_eval(params, float(q[j])) - j / 256) ** 2 for j in range(257))
+
+
+def test_mlp_start_is_the_piecewise_interpolation():
+    """With no training step, unit h is the ramp from knot 8h to knot 8h + 8
+    with weight 1/32: f(q[8h]) = h/32 (up to the rounding of sqrt(1/32)^2),
+    linear in between."""
+    keys = inputs.gaussian_mixture(200_000, 3)
+    mn, mx, q, _ = oracle.learned_map(keys, seed=5, m=65536, k=512)
+    p = oracle.mlp_train(q, 0)
+    for h in range(33):
+        assert abs(oracle.mlp_eval(p, float(q[8 * h])) - h / 32) < 1e-5, h
+    # midway between two knots of one ramp (distinct knots): half a step more
+    for h in range(32):
+        lo, hi = float(q[8 * h]), float(q[8 * h + 8])
+        if hi > lo:
+            mid = np.float32((lo + hi) / 2)
+            assert abs(oracle.mlp_eval(p, float(mid)) - (h + 0.5) / 32) < 1e-4
+
+
+def test_mlp_identity_knots_give_the_uniform_map():
+    """Knots q_j = j/256 (an evenly spread sample): the start state is
+    f(u) = u, so the bucket of u = d / 2^16 is floor(d * k / 2^16) below the
+    top knot."""
+    m, k = 65536, 1024
+    q = oracle.pwl_train(np.arange(m, dtype=np.uint64), 0, m - 1)
+    p = oracle.mlp_train(q, 0)
+    d = np.arange(0, 255 * 256, 41, dtype=np.uint64)
+    b = oracle.mlp_buckets(d, 0, m - 1, p, k)
+    want = (d * np.uint64(k) // np.uint64(m)).astype(np.int64)
+    assert np.max(np.abs(b.astype(np.int64) - want)) <= 1  # f0, inv rescale by f(u_max)
+
+
+@pytest.mark.parametrize("gen", [inputs.lognormal, inputs.gaussian_mixture, inputs.uniform,
+                                 inputs.normal, inputs.dense_interval_u64])
+def test_mlp_training_lowers_the_error_and_stays_monotone(gen):
+    keys = gen(300_000, 9)
+    mn, mx, q, sample = oracle.learned_map(keys, seed=11, m=65536, k=512)
+    p0, p = oracle.mlp_train(q, 0), oracle.mlp_train(q, 128)
+    assert mlp_knot_loss(p, q) < mlp_knot_loss(p0, q)
+    assert np.all(np.isfinite(p))
+    # positive weights by construction: w = omega^2, a = alpha^2
+    probes = np.unique(np.concatenate([np.sort(sample), [mn, mx], np.sort(sample) + np.uint64(1)]))
+    probes = probes[probes <= mx]
+    b = oracle.mlp_buckets(probes, mn, mx, p, 512)
+    assert np.all(b[:-1] <= b[1:])
+    assert b[0] == 0 and b[-1] <= 511
+    # a dense grid of u: f non-decreasing
+    us = np.linspace(0.0, float(q[-1]), 5001, dtype=np.float32)
+    fs = [oracle.mlp_eval(p, float(u)) for u in us]
+    assert all(a <= b for a, b in zip(fs, fs[1:]))
+
+
+def test_mlp_balance_on_uniform_keys():
+    keys = inputs.uniform(400_000, 12)
+    mn, mx, q, sample = oracle.learned_map(keys, seed=13, m=65536, k=512)
+    b = oracle.mlp_buckets(sample, mn, mx, oracle.mlp_train(q, 128), 512)
+    assert np.bincount(b, minlength=512).max() <= 2 * 65536 // 512
