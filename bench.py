@@ -439,6 +439,28 @@ def main():
                  "per_array_ms": [round(sum(step[i][0] for step in pres) / len(pres), 3)
                                   for i in range(len(bufs))]}
 
+    mappers = None
+    if not args.no_plain:
+        # top-level bucket imbalance of each map on the full arrays (largest
+        # bucket over the mean), and the MLP map's sort time beside the others
+        imb = {}
+        for name, kd, _ in pristine:
+            row = {}
+            for label, mp in (("zscore", z.MAP_ZSCORE), ("learned_pwl", z.MAP_LEARNED), ("mlp", z.MAP_MLP)):
+                b, info = z.map_buckets(kd, z.default_opts(mapper=mp))
+                cnt = torch.bincount(b.to(torch.int64), minlength=info.k)
+                row[label] = {"map_used": ["zscore", "learned_pwl", "range", "mlp"][info.map], "k": info.k,
+                              "max_over_mean": round(float(cnt.max()) * info.k / n, 2)}
+                del b, cnt
+            imb[name] = row
+        torch.cuda.empty_cache()
+        mres = run(z.default_opts(mapper=z.MAP_MLP), max(3, args.steps // 2), 1)
+        mms = sum(sum(a[0] for a in step) for step in mres)
+        mappers = {"mlp": {"value": pairs_per_step * len(mres) / (mms / 1e3), "unit": UNIT,
+                           "per_array_ms": [round(sum(step[i][0] for step in mres) / len(mres), 3)
+                                            for i in range(len(bufs))]},
+                   "imbalance": imb}
+
     keys_only = None
     if not args.no_plain:
         kres = run(opts, max(3, args.steps // 2), 1, keys_only=True)
@@ -535,6 +557,7 @@ def main():
                       for i, (name, _, _) in enumerate(pristine)],
         "plain_zscore": plain,
         "keys_only": keys_only,
+        "mappers": mappers,
         "batched": batched,
     }
     print(json.dumps(line), flush=True)
