@@ -27,13 +27,12 @@ __global__ void __launch_bounds__(BLOCK, 2) k_persistent(const __grid_constant__
     extern __shared__ __align__(128) unsigned char smraw[];
     SmemTile &s = *reinterpret_cast<SmemTile *>(smraw);
     if (threadIdx.x == 0) {
-        mbar_init(&s.bar[0]);
-        mbar_init(&s.bar[1]);
+        for (int w = 0; w < KEY_STAGES; w++) mbar_init(&s.bar[w]);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
     Pipe pp;
-    pp.uses[0] = pp.uses[1] = 0;
+    for (int w = 0; w < KEY_STAGES; w++) pp.uses[w] = 0;
     QCache qc;
     qc.e = INVALID;
     unsigned long long t_idle0 = 0, t_task0 = 0;

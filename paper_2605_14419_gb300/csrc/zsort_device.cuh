@@ -520,9 +520,15 @@ struct LeafBuf {
     uint32_t val[LEAF_CAP + 2 * PAD];
 };
 
+constexpr int KEY_STAGES = 3;  // key-only streams: tiles in flight per CTA
+struct KeyRing {
+    unsigned long long key[KEY_STAGES][TILE + PAD];
+};
+
 struct SmemTile {
     union {
         TileBuf buf[2];   // double-buffered streamed tiles (bulk-copy targets)
+        KeyRing ring;     // key-only streams: three stages of keys
         LeafBuf leaf;     // one leaf of up to LEAF_CAP pairs
         ChildList children;
     } u;
@@ -537,12 +543,13 @@ struct SmemTile {
     uint32_t wsum[WARPS + 1];
     Acc acc[WARPS];
     MapSm map;
-    unsigned long long bar[2];       // mbarriers of the two tile buffers
+    unsigned long long bar[KEY_STAGES];  // mbarriers of the tile buffers / key stages
     uint32_t task[8];
     uint32_t flag, flag2, n_leaf, n_med, n_large, n_large_ok, item_base, e_base;
     unsigned long long red64[WARPS * 2];
 };
 static_assert(sizeof(LeafBuf) <= sizeof(TileBuf) * 2, "leaf fits the tile buffers");
+static_assert(sizeof(KeyRing) <= sizeof(TileBuf) * 2, "the key stages fit the tile buffers");
 static_assert(sizeof(ChildList) <= sizeof(TileBuf) * 2, "child lists fit the tile buffers");
 
 // ------------------------------------------------------------ block scan

@@ -286,10 +286,10 @@ __device__ void load_seg_map(const Params &P, uint32_t sid, SmemTile &s)
 }
 
 // ------------------------------------------------------------ tile streaming
-// Per-thread copy (identical in every thread) of how often each of the two
-// tile mbarriers has completed, which gives the parity to wait for.
+// Per-thread copy (identical in every thread) of how often each tile
+// mbarrier has completed, which gives the parity to wait for.
 struct Pipe {
-    uint32_t uses[2];
+    uint32_t uses[KEY_STAGES];
 };
 
 // Thread 0: bulk copies of elements [a, a+cnt) of keys (and vals) into
@@ -329,54 +329,79 @@ __device__ void stream_fix_tail(const Params &P, unsigned long long *sk, uint32_
     }
 }
 
-// Streams elements [start, start+len) through the two tile buffers and calls
-// body(tile, cnt, keys_smem, vals_smem) for each tile, in order, with all
-// threads.  Returns false (error recorded) if a bulk copy did not complete.
+// Thread 0: bulk copy of keys [a, a+cnt) into key stage w (16-byte aligned
+// span inside the array, as stream_issue; the tail is left to plain loads).
+__device__ void stream_issue_keys(const Params &P, SmemTile &s, int w, const uint64_t *keys, unsigned long long a,
+                                  uint32_t cnt)
+{
+    const unsigned long long a0 = a & ~1ull;
+    const unsigned long long a1 = min((a + cnt + 1) & ~1ull, P.n & ~1ull);
+    const uint32_t bk = a1 > a0 ? (uint32_t)(a1 - a0) * 8u : 0u;
+    mbar_expect_arrive(&s.bar[w], bk);
+    if (bk) bulk_g2s(s.u.ring.key[w], keys + a0, bk, &s.bar[w]);
+}
+
+// Streams the keys [start, start+len) through a ring of KEY_STAGES stages
+// (two tiles in flight while one is processed) and calls body(tile, cnt,
+// keys_smem, nullptr) for each tile, in order, with all threads; the body
+// must not need a barrier of its own.  One barrier a tile: once every thread
+// is past it, every thread has left the previous tile, whose stage then
+// takes the copy of the tile after next.  Returns false (error recorded) if
+// a bulk copy did not complete.
 template <bool VALS, class Body>
-__device__ bool stream_tiles(const Params &P, SmemTile &s, Pipe &pp, const uint64_t *keys, const uint32_t *vals,
+__device__ bool stream_tiles(const Params &P, SmemTile &s, Pipe &pp, const uint64_t *keys, const uint32_t *,
                              bool bulk, unsigned long long start, unsigned long long len, Body body)
 {
+    static_assert(!VALS, "streams of payloads go through the scatter's own loop");
     const uint32_t nt = (uint32_t)((len + TILE - 1) / TILE);
     if (nt == 0) return true;
+    auto tile_len = [&](uint32_t t) {
+        return (uint32_t)min((unsigned long long)TILE, len - (unsigned long long)t * TILE);
+    };
     if (bulk && threadIdx.x == 0)
-        stream_issue<VALS>(P, s, 0, keys, vals, start, (uint32_t)min(len, (unsigned long long)TILE));
+        for (uint32_t t = 0; t < KEY_STAGES - 1 && t < nt; t++)
+            stream_issue_keys(P, s, (int)t, keys, start + (unsigned long long)t * TILE, tile_len(t));
     for (uint32_t t = 0; t < nt; t++) {
-        const int w = t & 1;
+        const int w = (int)(t % KEY_STAGES);
         const unsigned long long a = start + (unsigned long long)t * TILE;
-        const uint32_t cnt = (uint32_t)min((unsigned long long)TILE, len - (unsigned long long)t * TILE);
-        if (bulk && t + 1 < nt && threadIdx.x == 0) {
-            const unsigned long long an = a + TILE;
-            stream_issue<VALS>(P, s, w ^ 1, keys, vals, an,
-                               (uint32_t)min((unsigned long long)TILE, start + len - an));
-        }
+        const uint32_t cnt = tile_len(t);
         unsigned long long *sk;
-        uint32_t *sv;
         if (bulk) {
-            sk = s.u.buf[w].key + (a & 1ull);
-            sv = s.u.buf[w].val + (a & 3ull);
+            sk = s.u.ring.key[w] + (a & 1ull);
             const bool ok = mbar_wait(&s.bar[w], pp.uses[w] & 1u, P.wait_ns);
             pp.uses[w]++;
             if (__syncthreads_or(!ok)) {  // CTA-uniform: every thread leaves together
-                // one more bounded wait for each buffer's pending copy
+                // one more bounded wait for every copy that may be in flight
                 mbar_wait(&s.bar[w], (pp.uses[w] - 1u) & 1u, P.wait_ns);
-                if (t + 1 < nt) mbar_wait(&s.bar[w ^ 1], pp.uses[w ^ 1] & 1u, P.wait_ns);
+                for (uint32_t tn = t + 1; tn < nt && tn < t + KEY_STAGES - 1; tn++) {
+                    const int wn = (int)(tn % KEY_STAGES);
+                    mbar_wait(&s.bar[wn], pp.uses[wn] & 1u, P.wait_ns);
+                }
                 set_error(P, ST_TIMEOUT);
                 return false;
             }
-            stream_fix_tail<VALS>(P, sk, sv, keys, vals, a, cnt);
-        } else {
-            sk = s.u.buf[w].key;
-            sv = s.u.buf[w].val;
-            for (uint32_t i = threadIdx.x; i < cnt; i += BLOCK) {
-                sk[i] = __ldcg(keys + a + i);
-                if (VALS && P.kv) sv[i] = __ldcg(vals + a + i);
+            // every thread has left tile t - 1: its stage takes tile t + 2
+            if (t + KEY_STAGES - 1 < nt && threadIdx.x == 0) {
+                const uint32_t tn = t + KEY_STAGES - 1;
+                stream_issue_keys(P, s, (int)(tn % KEY_STAGES), keys, start + (unsigned long long)tn * TILE,
+                                  tile_len(tn));
             }
+            if (a + cnt > (P.n & ~1ull)) {  // the array's last key: a plain load (uniform branch)
+                for (unsigned long long e = max(a, P.n & ~1ull) + threadIdx.x; e < a + cnt; e += BLOCK)
+                    sk[e - a] = __ldcg(keys + e);
+                __syncthreads();
+            }
+        } else {
+            // the stage last held tile t - 3; every thread left it before the
+            // previous tile's barrier
+            sk = s.u.ring.key[w];
+            for (uint32_t i = threadIdx.x; i < cnt; i += BLOCK) sk[i] = __ldcg(keys + a + i);
+            __syncthreads();
         }
-        __syncthreads();
-        body(t, cnt, sk, sv);
-        fence_proxy_async();  // this thread's smem accesses before the buffer's next bulk write
-        __syncthreads();
+        body(t, cnt, sk, (uint32_t *)nullptr);
+        fence_proxy_async();  // this thread's smem accesses before the stage's next bulk write
     }
+    __syncthreads();  // the last tile's body is complete for the caller
     return true;
 }
 
@@ -391,12 +416,14 @@ __device__ __forceinline__ uint32_t leaf_slot(int i)
 
 // ------------------------------------------------------------ tile bodies
 // Exact sums of the tile's keys into a per-thread accumulator.
-__device__ __forceinline__ void body_stats(Acc &a, uint32_t cnt, const unsigned long long *sk)
+__device__ __forceinline__ void body_stats(Acc &a, Acc &b, uint32_t cnt, const unsigned long long *sk)
 {
+    // two accumulators: the even and the odd slots form independent chains
 #pragma unroll
-    for (int i = 0; i < IPT; i++) {
-        const uint32_t p = slot_index(i);
+    for (int i = 0; i < IPT; i += 2) {
+        const uint32_t p = slot_index(i), p1 = slot_index(i + 1);
         if (p < cnt) acc_key(a, sk[p]);
+        if (p1 < cnt) acc_key(b, sk[p1]);
     }
 }
 
@@ -749,11 +776,13 @@ __device__ __noinline__ void task_lstats(const Params &P, uint32_t sid, uint32_t
     // this chunk's look-back row must read zero before the histogram phase
     uint32_t *row = P.status + ch.sbase + (size_t)c * ch.k;
     for (uint32_t q = threadIdx.x; q < ch.k; q += BLOCK) __stcg(row + q, 0u);
-    Acc a;
+    Acc a, a2;
     acc_init(a);
+    acc_init(a2);
     const uint64_t *src = keys_of(P, ch.buf);
     stream_tiles<false>(P, s, pp, src, nullptr, bulk_ok(P, ch.buf), ch.start, ch.len,
-                        [&](uint32_t, uint32_t cnt, unsigned long long *sk, uint32_t *) { body_stats(a, cnt, sk); });
+                        [&](uint32_t, uint32_t cnt, unsigned long long *sk, uint32_t *) { body_stats(a, a2, cnt, sk); });
+    acc_merge(a, a2);
     acc_block_reduce(a, s.acc);
     if (threadIdx.x == 0) {
         Seg *W = &P.segs[sid];
@@ -1413,10 +1442,12 @@ __device__ __noinline__ void task_mpart(const Params &P, const Item it, SmemTile
     const uint64_t *srck = keys_of(P, buf);
     const uint32_t *srcv = vals_of(P, buf);
     const bool bulk = bulk_ok(P, buf);
-    Acc a;
+    Acc a, a2;
     acc_init(a);
+    acc_init(a2);
     stream_tiles<false>(P, s, pp, srck, nullptr, bulk, off, len,
-                        [&](uint32_t, uint32_t cnt, unsigned long long *sk, uint32_t *) { body_stats(a, cnt, sk); });
+                        [&](uint32_t, uint32_t cnt, unsigned long long *sk, uint32_t *) { body_stats(a, a2, cnt, sk); });
+    acc_merge(a, a2);
     acc_block_reduce(a, s.acc);
     if (threadIdx.x == 0) {
         if (a.mn == a.mx) {
