@@ -459,9 +459,9 @@ __device__ __noinline__ void hist_stream(const Params &P, SmemTile &s, Pipe &pp,
 // Stable scatter of [start, start+len) of a (sub)array whose map is in s.map
 // and whose running bucket cursors are in s.cursor.  Per tile: rank the
 // pairs by (bucket, position) with ballots, stage them in that order in the
-// tile's own buffer, then write each bucket's run at its cursor (coalesced
-// within runs); the output pass recomputes each staged key's bucket, except
-// for the learned map, whose buckets are staged.  Four barriers a tile: the
+// tile's own buffer with their buckets, then write each bucket's run at its
+// cursor (coalesced within runs; a staged bucket is cheaper to read back
+// than any map is to recompute).  Four barriers a tile: the
 // tile's bulk copy is issued once every thread has left the tile that last
 // used its buffer, and each warp clears its own bucket counters.
 template <int NBITS, bool MLP, bool KV>
@@ -473,7 +473,6 @@ __device__ __noinline__ void scatter_stream(const Params &P, SmemTile &s, Pipe &
     if (nt == 0) return;
     const MapK mk = map_regs(s.map);
     const uint32_t k = mk.k;
-    const bool stage_b = mk.kind == MAP_PWL || mk.kind == MAP_MLP;  // costly maps: stage the bucket
     constexpr bool kv = KV;  // payloads move with the keys
     // the runs written per tile end inside lines that the next tile (or the
     // neighbouring chunk) completes: keep those lines in L2 until then
@@ -539,13 +538,13 @@ __device__ __noinline__ void scatter_stream(const Params &P, SmemTile &s, Pipe &
             if (pos[i] != INVALID) {
                 sk[pos[i]] = x[i];
                 if (kv) sv[pos[i]] = v[i];
-                if (stage_b) s.bkt[pos[i]] = (uint16_t)b[i];
+                s.bkt[pos[i]] = (uint16_t)b[i];
             }
         }
         __syncthreads();
         for (uint32_t p = threadIdx.x; p < cnt; p += BLOCK) {
             const unsigned long long key = sk[p];
-            const uint32_t q = stage_b ? (uint32_t)s.bkt[p] : map_key(mk, s.map, key);
+            const uint32_t q = s.bkt[p];
             const uint32_t rel = s.gdelta[q] + p;
             if (rel < seglen) {
                 st_front(dstk + rel, key, pol_front);
