@@ -542,15 +542,18 @@ __device__ __noinline__ void scatter_stream(const Params &P, SmemTile &s, Pipe &
             }
         }
         __syncthreads();
-        for (uint32_t p = threadIdx.x; p < cnt; p += BLOCK) {
-            const unsigned long long key = sk[p];
-            const uint32_t q = s.bkt[p];
-            const uint32_t rel = s.gdelta[q] + p;
-            if (rel < seglen) {
-                st_front(dstk + rel, key, pol_front);
-                if (kv) st_front(dstv + rel, sv[p], pol_front);
-            } else {
-                set_error(P, ST_INTERNAL);
+#pragma unroll
+        for (int i = 0; i < IPT; i++) {
+            const uint32_t p = threadIdx.x + i * BLOCK;
+            if (p < cnt) {
+                const unsigned long long key = sk[p];
+                const uint32_t rel = s.gdelta[s.bkt[p]] + p;
+                if (rel < seglen) {
+                    st_front(dstk + rel, key, pol_front);
+                    if (kv) st_front(dstv + rel, sv[p], pol_front);
+                } else {
+                    set_error(P, ST_INTERNAL);
+                }
             }
         }
         fence_proxy_async();  // this thread's smem accesses before the buffer's next bulk write
