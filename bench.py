@@ -145,8 +145,12 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_workload(n: int):
-    return [("lognormal", inputs.lognormal(n, 30)), ("gmm8", inputs.gaussian_mixture(n, 31))]
+def make_workload(n: int, rank: int = 0):
+    """The two arrays of a rank (rank 0: seeds 30 and 31; other ranks their own)."""
+    from paper_2605_14419_gb300 import replicas
+
+    return [("lognormal", inputs.lognormal(n, replicas.rank_seed(30, rank))),
+            ("gmm8", inputs.gaussian_mixture(n, replicas.rank_seed(31, rank)))]
 
 
 def batched_measure(z, torch, dev, nseg: int, seed: int, steps: int, warmup: int, plain_segments: int,
@@ -308,10 +312,9 @@ def main():
 
     import paper_2605_14419_gb300 as z
     from paper_2605_14419_gb300 import build as zbuild
+    from paper_2605_14419_gb300 import replicas
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank, world, local = replicas.world_info()
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
@@ -323,11 +326,13 @@ def main():
     z.load()
 
     if args.workload == "batched":
-        res = batched_measure(z, torch, dev, args.segments, 5, args.steps, args.warmup, 2000,
-                              args.tune_cache, args.tune_budget_ms)
+        res = batched_measure(z, torch, dev, args.segments, replicas.rank_seed(5, rank), args.steps, args.warmup,
+                              2000, args.tune_cache, args.tune_budget_ms)
+        # every rank sorts its own batch; the job's time is the slowest rank's
+        job_value = replicas.job_rate(res["pairs"], res["ms"] / 1e3, dev)
         if rank == 0:
             line = {
-                "metric": METRIC, "value": world * res["value"], "unit": UNIT, "n_gpus": world,
+                "metric": METRIC, "value": job_value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
                 "data": "synthetic (seeded numpy PCG64)",
@@ -341,7 +346,7 @@ def main():
         return
 
     n = 1 << args.logn
-    work = make_workload(n)
+    work = make_workload(n, rank)
     pristine = []
     for name, keys in work:
         kd = torch.from_numpy(keys.view(np.int64)).to(dev)
@@ -407,10 +412,7 @@ def main():
         dist.barrier()
     step_ms = [sum(a[0] for a in step) for step in res]
     total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = replicas.max_over_ranks(total_ms, dev)  # the slowest rank
     n_arrays = len(bufs)
     pairs_per_step = n * n_arrays
     value = world * pairs_per_step * args.steps / (total_ms / 1e3)
@@ -507,7 +509,7 @@ def main():
         rc = z.sync_status(stream)
         if rc != 0:
             raise z.ZsortError(rc, "bench e2e")
-        ems = e0.elapsed_time(e1)
+        ems = replicas.max_over_ranks(e0.elapsed_time(e1), dev)  # the slowest rank
         e2e = {"value": world * pairs_per_step * e_steps / (ems / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": pairs_per_step * BYTES_PER_PAIR,
                "d2h_bytes_per_step": pairs_per_step * BYTES_PER_PAIR}

@@ -126,6 +126,13 @@ typedef struct {
  * with one cudaGraphLaunch while the workspace, pointers, sizes and options
  * stay the same.  Needs a non-default stream (else ignored). */
 #define ZSORT_FLAG_GRAPH 1u
+/* Test of the bounded waits: the call publishes no work but counts one
+ * pending entry, so every CTA of the persistent kernel waits at the empty
+ * queue -- for a ready word that nothing sets -- until wait_limit_ms pass
+ * without progress; the kernel then records ZSORT_ERR_TIMEOUT and returns.
+ * keys/vals are not touched and the next call on the stream works as usual.
+ * Not a sort: it exists to check the failure path without any GPU fault. */
+#define ZSORT_FLAG_TEST_STALL 2u
 
 /* Counters of the last completed call on a (device, stream) workspace. */
 typedef struct {

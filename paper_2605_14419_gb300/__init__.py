@@ -35,6 +35,7 @@ TUNE_CLASS_MAX = 64
 MAX_N = 1 << 30
 MAX_SEG_TOTAL = 1 << 34
 FLAG_GRAPH = 1
+FLAG_TEST_STALL = 2
 NOALLOC_MAX_N = 1 << 20
 
 

@@ -210,6 +210,12 @@ __global__ void k_init_publish(Params P, unsigned long long nseg)
         q_write(P, e++, T_LSTATS, sid, P.segs[sid].chunks);
     }
     C->t_first = ~0ull;
+    if (P.test_stall) {  // test of the bounded waits: nothing published, one entry pending
+        C->q_alloc = 0;
+        C->pending = 1;
+        C->item_alloc = (uint32_t)(2 * nseg);
+        return;
+    }
     C->q_alloc = e;
     C->pending = e;
     C->item_alloc = (uint32_t)(2 * nseg);
@@ -462,6 +468,7 @@ int launch(uint64_t *keys, uint32_t *vals, unsigned long long n, const uint64_t 
     P.wait_ns = (unsigned long long)o.wait_limit_ms * 1000000ull;
     P.user_aligned = ((reinterpret_cast<uintptr_t>(keys) | reinterpret_cast<uintptr_t>(vals)) & 15u) == 0;
     P.kv = vals != nullptr;  // null vals: keys only
+    P.test_stall = (o.flags & ZSORT_FLAG_TEST_STALL) ? 1u : 0u;
     int per_sm = o.ctas_per_sm ? (int)std::min<uint32_t>(o.ctas_per_sm, (uint32_t)ws->occ) : ws->occ;
     P.nctas = (uint32_t)(ws->sms * per_sm);
     P.plan_out = plan_out;

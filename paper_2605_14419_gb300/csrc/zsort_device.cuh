@@ -137,6 +137,7 @@ struct Params {
     uint32_t *plan_out;          // map inspection: bucket of every key (else null)
     uint32_t user_aligned;       // caller's keys and vals 16-byte aligned: bulk copies allowed
     uint32_t kv;                 // 1: (key, payload) pairs; 0: keys only (vals == null)
+    uint32_t test_stall;         // publish nothing, one entry pending: every wait runs out
     float *pwl;         // segcap * PWL_STRIDE: breakpoints q[0..P], reciprocals r[0..P), MLP table
     unsigned long long *trainbuf; // traincap * 2 * SAMPLE_MAX sampled keys (ping-pong)
     uint32_t traincap;

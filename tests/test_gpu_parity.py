@@ -369,3 +369,28 @@ def test_mlp_map_bit_exact(gen):
 def test_mlp_mapper_sorts_exactly(gen):
     keys = gen(3_000_000, 24)
     assert_same_as_oracle(keys, opts=z.default_opts(mapper=z.MAP_MLP, learn_min=1 << 20))
+
+
+# ---------------------------------------------------------------- failure path
+def test_bounded_wait_runs_out_and_the_context_recovers():
+    """ZSORT_FLAG_TEST_STALL: every CTA waits for a queue entry that nothing
+    publishes; after wait_limit_ms without progress the kernel records
+    ZSORT_ERR_TIMEOUT and returns (no trap, no hang).  The data is untouched
+    and the next call on the same stream sorts exactly."""
+    import time
+
+    keys = inputs.uniform(1 << 20, 41)
+    vals = inputs.index_payload(keys.size)
+    k, v = to_dev(keys, vals)
+    t0 = time.perf_counter()
+    with pytest.raises(z.ZsortError) as ei:
+        z.sort_pairs(k, v, opts=z.default_opts(flags=z.FLAG_TEST_STALL, wait_limit_ms=50))
+    assert ei.value.code == z.ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 10.0
+    assert np.array_equal(k.cpu().numpy().view(np.uint64), keys)
+    assert np.array_equal(v.cpu().numpy().view(np.uint32), vals)
+    assert z.sync_status() == z.OK  # the status word was read and cleared
+    z.sort_pairs(k, v)
+    ok, ov = oracle.zsort_pairs(keys, vals)
+    assert np.array_equal(k.cpu().numpy().view(np.uint64), ok)
+    assert np.array_equal(v.cpu().numpy().view(np.uint32), ov)
