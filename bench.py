@@ -243,6 +243,17 @@ def cpu_oracle_rate(n_sample: int, budget_s: float = 12.0):
     return done / t_total, t_total, reps
 
 
+def pairs_config(logn: int, mapper_name: str, world: int = 1) -> dict:
+    """The config of the pairs workload (the same dict in both arms)."""
+    return {
+        "workload": f"zsort_pairs, 2 arrays x n=2^{logn} (u64 key, u32 index): lognormal "
+                    f"floor(exp(N(30,2))) and 8-component Gaussian mixture; mapper={mapper_name}",
+        "pairs_per_step": 2 * (1 << logn),
+        "l2": f"inputs ({3 * (1 << logn) >> 28} GiB per array) far larger than L2; restored between steps",
+        "parallelism": "replicas" if world > 1 else "single GPU",
+    }
+
+
 def run_reference(args):
     """Reference arm: the CPU oracle, timed on this host, on the workload shape."""
     rank = int(os.environ.get("RANK", "0"))
@@ -270,11 +281,11 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
         "data": "synthetic (seeded numpy PCG64)",
-        "config": {"workload": f"zsort oracle (plain sequential C zSort), lognormal + gmm8 samples of "
-                               f"n={n_sample} each per step (full workload: 2 x 2^28)",
-                   "l2": "n/a (CPU)"},
+        "config": pairs_config(args.logn, args.mapper),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"2 x {n_sample} pairs per step"},
+                         "sample": f"each step sorts the two arrays' laws at n={n_sample} (lognormal and "
+                                   f"8-component mixture) with the sequential C oracle on one host core; "
+                                   f"pairs/s of that sample stand for the 2 x 2^{args.logn} workload"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -533,13 +544,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic (seeded numpy PCG64)",
-        "config": {
-            "workload": f"zsort_pairs, 2 arrays x n=2^{args.logn} (u64 key, u32 index): lognormal "
-                        f"floor(exp(N(30,2))) and 8-component Gaussian mixture; mapper={args.mapper}",
-            "pairs_per_step": pairs_per_step,
-            "l2": "inputs (3 GiB per array) far larger than L2; restored between steps",
-            "parallelism": "replicas" if world > 1 else "single GPU",
-        },
+        "config": pairs_config(args.logn, args.mapper, world),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
                      "traffic": None if traffic_pp is None else traffic_pp * n, "traffic_note": traffic_note,
