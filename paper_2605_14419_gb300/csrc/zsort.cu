@@ -33,8 +33,8 @@ __global__ void __launch_bounds__(BLOCK, 2) k_persistent(const __grid_constant__
     __syncthreads();
     Pipe pp;
     for (int w = 0; w < KEY_STAGES; w++) pp.uses[w] = 0;
-    QCache qc;
-    qc.e = INVALID;
+    QCache qc[QUEUES];
+    for (int q = 0; q < QUEUES; q++) qc[q].e = INVALID;
     unsigned long long t_idle0 = 0, t_task0 = 0;
     for (;;) {
         if (threadIdx.x == 0) {
@@ -189,8 +189,7 @@ __global__ void k_init_publish(Params P, unsigned long long nseg)
     C->epoch = ep;
     const uint32_t nl = C->init_leaf, nm = C->init_med;
     const uint32_t ns = min(C->seg_alloc, P.segcap);
-    uint32_t e = 0;
-    if (nl) q_write(P, e++, T_FINISH, 0, nl);
+    uint32_t e = 0;  // partition queue; the leaf entry goes to the leaf queue
     if (nm) q_write(P, e++, T_MPART, (uint32_t)nseg, nm);
     for (uint32_t sid = 0; sid < ns; sid++) {
         if (P.segs[sid].len == 0) continue;
@@ -211,15 +210,19 @@ __global__ void k_init_publish(Params P, unsigned long long nseg)
     }
     C->t_first = ~0ull;
     if (P.test_stall) {  // test of the bounded waits: nothing published, one entry pending
-        C->q_alloc = 0;
+        C->q_alloc[0] = C->q_alloc[1] = 0;
         C->pending = 1;
         C->item_alloc = (uint32_t)(2 * nseg);
         return;
     }
-    C->q_alloc = e;
-    C->pending = e;
+    const uint32_t eleaf = P.qcap;  // first entry of the leaf queue
+    if (nl) q_write(P, eleaf, T_FINISH, 0, nl);
+    C->q_alloc[0] = e;
+    C->q_alloc[1] = nl ? 1u : 0u;
+    C->pending = e + (nl ? 1u : 0u);
     C->item_alloc = (uint32_t)(2 * nseg);
     for (uint32_t i = 0; i < e; i++) P.ready[i] = ep;
+    if (nl) P.ready[eleaf] = ep;
 }
 
 // Order-preserving encodings to uint64 and back (in place).
@@ -310,10 +313,10 @@ Plan make_plan(unsigned long long n, unsigned long long nseg, unsigned long long
     p.off_svals = take(n * 4);
     p.off_ctl = take(sizeof(Ctl));
     p.off_epoch = take(16);
-    p.off_entries = take(p.qcap * sizeof(Entry));
-    p.off_ready = take(p.qcap * 4);
-    p.off_tnext = take(p.qcap * 4);
-    p.off_tdone = take(p.qcap * 4);
+    p.off_entries = take(QUEUES * p.qcap * sizeof(Entry));
+    p.off_ready = take(QUEUES * p.qcap * 4);
+    p.off_tnext = take(QUEUES * p.qcap * 4);
+    p.off_tdone = take(QUEUES * p.qcap * 4);
     p.off_segs = take(p.segcap * sizeof(Seg));
     p.off_items = take(p.itemcap * sizeof(Item));
     p.off_counts = take(p.segcap * NB_MAX * 4);
@@ -566,10 +569,10 @@ constexpr NaLayout na_layout()
     L.svals = o; o = na_align(o + NA_MAX_N * 4);
     L.ctl = o; o = na_align(o + sizeof(Ctl));
     L.epoch = o; o = na_align(o + 16);
-    L.entries = o; o = na_align(o + L.qcap * sizeof(Entry));
-    L.ready = o; o = na_align(o + L.qcap * 4);
-    L.tnext = o; o = na_align(o + L.qcap * 4);
-    L.tdone = o; o = na_align(o + L.qcap * 4);
+    L.entries = o; o = na_align(o + QUEUES * L.qcap * sizeof(Entry));
+    L.ready = o; o = na_align(o + QUEUES * L.qcap * 4);
+    L.tnext = o; o = na_align(o + QUEUES * L.qcap * 4);
+    L.tdone = o; o = na_align(o + QUEUES * L.qcap * 4);
     L.segs = o; o = na_align(o + L.segcap * sizeof(Seg));
     L.items = o; o = na_align(o + L.itemcap * sizeof(Item));
     L.counts = o; o = na_align(o + L.segcap * NB_MAX * 4);

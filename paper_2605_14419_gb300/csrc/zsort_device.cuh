@@ -96,10 +96,17 @@ struct Entry {
     uint32_t type, arg, ntiles, pad;
 };
 
+// Two work queues, each an append-only array of entries: 0 = partition work
+// (statistics, samples, histograms, scatters, fits, single-CTA partitions,
+// copies), 1 = leaves.  A CTA takes partition work first: it creates the
+// later work, so the deep chains of skewed inputs start early, and leaves,
+// which depend on nothing, fill the gaps.
+constexpr int QUEUES = 2;
+
 struct Ctl {
-    unsigned int q_head, q_alloc, pending, error;
-    unsigned int seg_alloc, item_alloc, train_alloc, init_leaf;
-    unsigned int init_med, pad0, pad1, pad2;
+    unsigned int q_head[QUEUES], q_alloc[QUEUES];
+    unsigned int pending, error, seg_alloc, item_alloc;
+    unsigned int train_alloc, init_leaf, init_med, pad0;
     unsigned long long status_alloc;
     unsigned long long progress;
     // counters reported through zsort_stats
@@ -123,7 +130,8 @@ struct Params {
     Ctl *ctl;
     Entry *entries;
     uint32_t *ready, *tnext, *tdone;
-    uint32_t qcap, epoch_unused;
+    uint32_t qcap;               // entries per queue (entries, ready, tnext, tdone hold QUEUES * qcap)
+    uint32_t epoch_unused;
     uint32_t *epoch_ctr;         // persistent call counter (not cleared between calls)
     Seg *segs;
     uint32_t segcap;

@@ -18,18 +18,26 @@
 namespace zs {
 
 // ------------------------------------------------------------ queue
-// Reserves `count` consecutive entries (thread 0 only) and counts them as
-// pending; returns INVALID when the queue is full (error recorded).
-__device__ uint32_t q_reserve(const Params &P, uint32_t count)
+// Queue of a task type: leaves go to the leaf queue, all else to the
+// partition queue.
+__device__ __forceinline__ uint32_t queue_of(uint32_t type)
+{
+    return type == T_FINISH ? 1u : 0u;
+}
+
+// Reserves `count` consecutive entries of queue q (thread 0 only) and counts
+// them as pending; returns their absolute index, INVALID when the queue is
+// full (error recorded).
+__device__ uint32_t q_reserve(const Params &P, uint32_t count, uint32_t q = 0)
 {
     if (count == 0) return 0;
-    uint32_t e = atomicAdd(&P.ctl->q_alloc, count);
+    uint32_t e = atomicAdd(&P.ctl->q_alloc[q], count);
     if (e + count > P.qcap) {
         set_error(P, ST_CAPACITY);
         return INVALID;
     }
     atomicAdd(&P.ctl->pending, count);
-    return e;
+    return q * P.qcap + e;
 }
 
 // Writes an entry; it becomes visible once q_release_all() ran.
@@ -59,16 +67,17 @@ __device__ void q_release_all(const Params &P, uint32_t e, uint32_t count)
     for (uint32_t i = 0; i < count; i++) st_relaxed(&P.ready[e + i], ep);
 }
 
-// Thread 0's cached copy of the entry at the queue head.
+// Thread 0's cached copy of the entry at a queue's head.
 struct QCache {
     uint32_t e, type, arg, ntiles;
 };
 
-// Thread 0: claims the next tiles of the entry at the queue head.  out =
-// {type, arg, first tile, entry, ntiles, count}; type T_NONE when all work
-// is done or an error was recorded.  A wait without any progress anywhere for
-// longer than P.wait_ns records ST_TIMEOUT.
-__device__ void dequeue(const Params &P, uint32_t *out, QCache &qc)
+// Thread 0: claims the next tiles of the entry at the head of the partition
+// queue, else of the leaf queue.  out = {type, arg, first tile, entry,
+// ntiles, count}; type T_NONE when all work is done or an error was
+// recorded.  A wait without any progress anywhere for longer than
+// P.wait_ns records ST_TIMEOUT.
+__device__ void dequeue(const Params &P, uint32_t *out, QCache *qc)
 {
     Ctl *C = P.ctl;
     unsigned long long last = ld_relaxed64(&C->progress);
@@ -77,42 +86,45 @@ __device__ void dequeue(const Params &P, uint32_t *out, QCache &qc)
     out[0] = T_NONE;
     for (;;) {
         if (ld_relaxed(&C->error)) return;
-        uint32_t e = ld_relaxed(&C->q_head);
-        if (e != qc.e) {
-            if (e < P.qcap && ld_acquire(&P.ready[e]) == ep) {
-                uint4 en = __ldcg(reinterpret_cast<const uint4 *>(P.entries + e));
-                qc.e = e;
-                qc.type = en.x;
-                qc.arg = en.y;
-                qc.ntiles = en.z;
-            } else {
-                if (ld_acquire(&C->pending) == 0) return;
-                unsigned long long pr = ld_relaxed64(&C->progress), now = globaltimer();
-                if (pr != last) {
-                    last = pr;
-                    t0 = now;
-                } else if (now - t0 > P.wait_ns) {
-                    set_error(P, ST_TIMEOUT);
+        for (uint32_t q = 0; q < (uint32_t)QUEUES; q++) {
+            for (;;) {
+                const uint32_t h = ld_relaxed(&C->q_head[q]);
+                const uint32_t e = q * P.qcap + h;
+                if (e != qc[q].e) {
+                    if (h >= P.qcap || ld_acquire(&P.ready[e]) != ep) break;  // this queue is empty now
+                    uint4 en = __ldcg(reinterpret_cast<const uint4 *>(P.entries + e));
+                    qc[q].e = e;
+                    qc[q].type = en.x;
+                    qc[q].arg = en.y;
+                    qc[q].ntiles = en.z;
+                }
+                // leaves are claimed a few at a time, so that each can be
+                // prefetched while its predecessor is sorted
+                const uint32_t nt = qc[q].ntiles;
+                const uint32_t claim = qc[q].type != T_FINISH ? 1u : (nt >= 64u ? 4u : (nt >= 16u ? 2u : 1u));
+                const uint32_t t = atomicAdd(&P.tnext[e], claim);
+                if (t < nt) {
+                    out[0] = qc[q].type;
+                    out[1] = qc[q].arg;
+                    out[2] = t;
+                    out[3] = e;
+                    out[4] = nt;
+                    out[5] = min(claim, nt - t);
                     return;
                 }
-                __nanosleep(128);
-                continue;
+                atomicCAS(&C->q_head[q], h, h + 1);
             }
         }
-        // leaves are claimed a few at a time, so that each can be prefetched
-        // while its predecessor is sorted
-        const uint32_t claim = qc.type != T_FINISH ? 1u : (qc.ntiles >= 64u ? 4u : (qc.ntiles >= 16u ? 2u : 1u));
-        uint32_t t = atomicAdd(&P.tnext[e], claim);
-        if (t < qc.ntiles) {
-            out[0] = qc.type;
-            out[1] = qc.arg;
-            out[2] = t;
-            out[3] = e;
-            out[4] = qc.ntiles;
-            out[5] = min(claim, qc.ntiles - t);
+        if (ld_acquire(&C->pending) == 0) return;
+        const unsigned long long pr = ld_relaxed64(&C->progress), now = globaltimer();
+        if (pr != last) {
+            last = pr;
+            t0 = now;
+        } else if (now - t0 > P.wait_ns) {
+            set_error(P, ST_TIMEOUT);
             return;
         }
-        atomicCAS(&C->q_head, e, e + 1);
+        __nanosleep(128);
     }
 }
 
@@ -726,22 +738,28 @@ __device__ __noinline__ void classify_children(const Params &P, unsigned long lo
     if (threadIdx.x == 0) {
         uint32_t nsample = 0;
         for (uint32_t g = 0; g < nok; g++) nsample += L.lg_slot[g] != INVALID;
-        const uint32_t cnt = (nl > 0) + (nm > 0) + nok + nsample;
-        const uint32_t e = q_reserve(P, cnt);
+        const uint32_t cnt = (nm > 0) + nok + nsample;
+        const uint32_t e = q_reserve(P, cnt, 0);
         if (e != INVALID && cnt) {
             uint32_t j = e;
             // the learned-map samples first: each is one CTA's long task that
             // runs beside its (sub)array's statistics tiles
             for (uint32_t g = 0; g < nok; g++)
                 if (L.lg_slot[g] != INVALID) q_write(P, j++, T_LSAMPLE, sid0 + g, SAMPLE_RUNS);
-            if (nl) q_write(P, j++, T_FINISH, base, nl);
-            if (nm) q_write(P, j++, T_MPART, base + nl, nm);
             for (uint32_t g = 0; g < nok; g++) {
                 const uint32_t tiles = (L.lg_len[g] + TILE - 1) / TILE;
                 const uint32_t ct = choose_chunk_tiles(P, tiles, L.lg_len[g]);
                 q_write(P, j++, T_LSTATS, sid0 + g, (tiles + ct - 1) / ct);
             }
+            if (nm) q_write(P, j++, T_MPART, base + nl, nm);
             q_release_all(P, e, cnt);
+        }
+        if (nl) {
+            const uint32_t el = q_reserve(P, 1, queue_of(T_FINISH));
+            if (el != INVALID) {
+                q_write(P, el, T_FINISH, base, nl);
+                q_release_all(P, el, 1);
+            }
         }
     }
     __syncthreads();
@@ -802,7 +820,7 @@ __device__ __noinline__ void task_lstats(const Params &P, uint32_t sid, uint32_t
 __device__ void publish1(const Params &P, uint32_t type, uint32_t arg, uint32_t nt)
 {
     if (type == T_NONE) return;
-    const uint32_t e = q_reserve(P, 1);
+    const uint32_t e = q_reserve(P, 1, queue_of(type));
     if (e != INVALID) {
         q_write(P, e, type, arg, nt);
         q_release_all(P, e, 1);
