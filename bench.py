@@ -474,6 +474,37 @@ def main():
                                             for i in range(len(bufs))]},
                    "imbalance": imb}
 
+    u128 = None
+    if not args.no_plain:
+        # 128-bit keys (two stable 64-bit sorts and a gather), half as many keys
+        n128 = n // 2
+        rng = np.random.default_rng(replicas.rank_seed(77, rank))
+        w = torch.from_numpy(rng.integers(0, 2 ** 63, 2 * n128, dtype=np.int64)).to(dev)
+        wb = torch.empty_like(w)
+        vb128 = torch.empty(n128, dtype=torch.int32, device=dev)
+        times = []
+        for i in range(4):
+            wb.copy_(w)
+            vb128.copy_(torch.arange(n128, dtype=torch.int32, device=dev))
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            z.sort_pairs_u128(wb, vb128, check=False)
+            e1.record(stream)
+            rc = z.sync_status(stream)
+            if rc != 0:
+                raise z.ZsortError(rc, "bench u128")
+            if i:
+                times.append(e0.elapsed_time(e1))
+        hi = wb[1::2] ^ torch.tensor(-(2 ** 63), dtype=torch.int64, device=dev)
+        assert bool((hi[1:] >= hi[:-1]).all()), "u128 output not sorted by its high word"
+        u128 = {"value": n128 / (sum(times) / len(times) / 1e3), "unit": "pairs/s", "keys": n128,
+                "key_bits": 128, "ms": round(sum(times) / len(times), 3),
+                "method": "two stable 64-bit zSorts (low word, then high word) and a gather"}
+        del w, wb, vb128, hi
+        torch.cuda.empty_cache()
+
     keys_only = None
     if not args.no_plain:
         kres = run(opts, max(3, args.steps // 2), 1, keys_only=True)
@@ -564,6 +595,7 @@ def main():
                       for i, (name, _, _) in enumerate(pristine)],
         "plain_zscore": plain,
         "keys_only": keys_only,
+        "u128": u128,
         "mappers": mappers,
         "batched": batched,
     }

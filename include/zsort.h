@@ -178,6 +178,17 @@ int zsort_pairs(uint64_t *keys, uint32_t *vals, uint64_t n, zsort_stream_t strea
 /* Key-only sort of n uint64 keys in place: zsort_pairs(keys, NULL, n, stream). */
 int zsort_keys(uint64_t *keys, uint64_t n, zsort_stream_t stream);
 
+/* 128-bit keys (UUIDs, hashes; the paper's motivation, section
+ * "Introduction"): key i is the pair of words keys[2i] (low 64 bits) and
+ * keys[2i+1] (high 64 bits), compared as an unsigned 128-bit number; sorted
+ * in place with vals (may be NULL), stably.  Done as two stable 64-bit
+ * sorts, least significant word first (an LSD radix sort over 64-bit
+ * digits, each digit sorted by this library's zSort with the input index as
+ * its payload), then one gather of keys and payloads.  Allocates about
+ * 36 bytes per key of stream-ordered scratch (cudaMallocAsync) for the call.
+ * n <= ZSORT_MAX_N; opts may be NULL. */
+int zsort_pairs_u128(uint64_t *keys, uint32_t *vals, uint64_t n, const zsort_opts *opts, zsort_stream_t stream);
+
 /* The same for int64 keys (two's complement order) and float64 keys (IEEE
  * totalOrder, so -0.0 sorts before +0.0).  The keys are encoded to uint64 in
  * place on the device, sorted, and decoded. */

@@ -154,6 +154,7 @@ def load():
         "zsort_default_opts": (None, [ctypes.POINTER(Opts)]),
         "zsort_pairs": (i32, [vp, vp, u64, vp]),
         "zsort_keys": (i32, [vp, u64, vp]),
+        "zsort_pairs_u128": (i32, [vp, vp, u64, ctypes.POINTER(Opts), vp]),
         "zsort_pairs_i64": (i32, [vp, vp, u64, vp]),
         "zsort_pairs_f64": (i32, [vp, vp, u64, vp]),
         "zsort_pairs_ex": (i32, [vp, u32, vp, u64, ctypes.POINTER(Opts), vp]),
@@ -236,6 +237,28 @@ def sort_pairs(keys, vals, key_type: str = "u64", opts: Opts | None = None, stre
     _raise(rc, "zsort_pairs_ex")
     if check:
         _raise(lib.zsort_sync_status(st), "zsort (device)")
+    return keys, vals
+
+
+def sort_pairs_u128(keys, vals=None, opts: Opts | None = None, stream=None, check: bool = True):
+    """Sorts 128-bit keys in place: keys is a contiguous CUDA int64 tensor of
+    2n words (word 2i = low 64 bits of key i, 2i+1 = high); vals optional."""
+    _check_tensor(keys, 8, "keys")
+    if keys.numel() % 2:
+        raise ValueError("keys: need 2 words per key")
+    n = keys.numel() // 2
+    if vals is not None:
+        _check_tensor(vals, 4, "vals")
+        if vals.numel() != n:
+            raise ValueError("vals: need one payload per key")
+    lib = load()
+    st = _stream_handle(stream)
+    rc = lib.zsort_pairs_u128(ctypes.c_void_p(keys.data_ptr()),
+                              ctypes.c_void_p(vals.data_ptr()) if vals is not None else None, n,
+                              ctypes.byref(opts) if opts is not None else None, st)
+    _raise(rc, "zsort_pairs_u128")
+    if check:
+        _raise(lib.zsort_sync_status(st), "zsort_pairs_u128 (device)")
     return keys, vals
 
 

@@ -525,6 +525,36 @@ int encode(void *keys, unsigned long long n, uint32_t type, int inverse, cudaStr
     return cuda_err(cudaGetLastError());
 }
 
+// 128-bit keys: the word pairs (lo, hi) and their order, see zsort_pairs_u128.
+__global__ void k128_split(const uint64_t *keys, unsigned long long n, uint64_t *lo, uint32_t *idx)
+{
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        lo[i] = keys[2 * i];
+        idx[i] = (uint32_t)i;
+    }
+}
+__global__ void k128_gather_hi(const uint64_t *keys, unsigned long long n, const uint32_t *idx, uint64_t *hi,
+                               uint32_t *pos)
+{
+    for (unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (unsigned long long)gridDim.x * blockDim.x) {
+        hi[j] = keys[2 * (unsigned long long)idx[j] + 1];
+        pos[j] = (uint32_t)j;
+    }
+}
+__global__ void k128_gather_out(const uint64_t *keys, const uint32_t *vals, unsigned long long n,
+                                const uint32_t *idx, const uint32_t *pos, uint64_t *ok, uint32_t *ov)
+{
+    for (unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long src = idx[pos[j]];
+        ok[2 * j] = keys[2 * src];
+        ok[2 * j + 1] = keys[2 * src + 1];
+        if (vals) ov[j] = vals[src];
+    }
+}
+
 Workspace *find_ws(cudaStream_t stream)
 {
     int dev = 0;
@@ -647,6 +677,54 @@ int zsort_pairs_ex(void *keys, uint32_t key_type, uint32_t *vals, uint64_t n, co
     rc = launch(static_cast<uint64_t *>(keys), vals, n, nullptr, 1, o, st);
     if (rc != ZSORT_OK) return rc;
     return encode(keys, n, key_type, 1, st);
+}
+
+int zsort_pairs_u128(uint64_t *keys, uint32_t *vals, uint64_t n, const zsort_opts *opts, zsort_stream_t stream)
+{
+    zsort_opts o;
+    if (opts)
+        o = *opts;
+    else
+        zsort_default_opts(&o);
+    if (!opts_valid(o) || n > ZSORT_MAX_N) return ZSORT_ERR_INVALID;
+    if (n <= 1) return ZSORT_OK;
+    if (!keys) return ZSORT_ERR_INVALID;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    // scratch: one 64-bit word and one index per key, twice the keys and the
+    // payloads for the gathered result
+    auto a16 = [](size_t x) { return (x + 15) & ~size_t(15); };  // bulk copies want 16-byte bases
+    const size_t o_idx = a16(n * 8), o_pos = a16(o_idx + n * 4), o_ok = a16(o_pos + n * 4);
+    const size_t o_ov = o_ok + n * 16, bytes = o_ov + (vals ? n * 4 : 0);
+    unsigned char *t = nullptr;
+    cudaError_t ce = cudaMallocAsync(reinterpret_cast<void **>(&t), bytes, st);
+    if (ce != cudaSuccess) return cuda_err(ce);
+    uint64_t *word = reinterpret_cast<uint64_t *>(t);
+    uint32_t *idx = reinterpret_cast<uint32_t *>(t + o_idx);
+    uint32_t *pos = reinterpret_cast<uint32_t *>(t + o_pos);
+    uint64_t *ok = reinterpret_cast<uint64_t *>(t + o_ok);
+    uint32_t *ov = vals ? reinterpret_cast<uint32_t *>(t + o_ov) : nullptr;
+    const unsigned int grid = (unsigned int)std::min<unsigned long long>(div_up(n, 256), 4096);
+    int rc = ZSORT_OK;
+    // 1. stable sort of (low word, index)
+    k128_split<<<grid, 256, 0, st>>>(keys, n, word, idx);
+    rc = cuda_err(cudaGetLastError());
+    if (rc == ZSORT_OK) rc = launch(word, idx, n, nullptr, 1, o, st);
+    // 2. stable sort of (high word in that order, position): equal high words
+    //    keep the low-word order, so the result orders (high, low, input index)
+    if (rc == ZSORT_OK) {
+        k128_gather_hi<<<grid, 256, 0, st>>>(keys, n, idx, word, pos);
+        rc = cuda_err(cudaGetLastError());
+    }
+    if (rc == ZSORT_OK) rc = launch(word, pos, n, nullptr, 1, o, st);
+    // 3. the keys and payloads in that order, back into the caller's arrays
+    if (rc == ZSORT_OK) {
+        k128_gather_out<<<grid, 256, 0, st>>>(keys, vals, n, idx, pos, ok, ov);
+        rc = cuda_err(cudaGetLastError());
+    }
+    if (rc == ZSORT_OK) rc = cuda_err(cudaMemcpyAsync(keys, ok, n * 16, cudaMemcpyDeviceToDevice, st));
+    if (rc == ZSORT_OK && vals) rc = cuda_err(cudaMemcpyAsync(vals, ov, n * 4, cudaMemcpyDeviceToDevice, st));
+    const int rf = cuda_err(cudaFreeAsync(t, st));
+    return rc != ZSORT_OK ? rc : rf;
 }
 
 int zsort_keys(uint64_t *keys, uint64_t n, zsort_stream_t stream)

@@ -394,3 +394,35 @@ def test_bounded_wait_runs_out_and_the_context_recovers():
     ok, ov = oracle.zsort_pairs(keys, vals)
     assert np.array_equal(k.cpu().numpy().view(np.uint64), ok)
     assert np.array_equal(v.cpu().numpy().view(np.uint32), ov)
+
+
+# ---------------------------------------------------------------- 128-bit keys
+def u128_case(n, seed, hi_distinct=None, lo_distinct=None):
+    rng = np.random.default_rng(seed)
+    hi = rng.integers(0, 2 ** 64, n, dtype=np.uint64, endpoint=False)
+    lo = rng.integers(0, 2 ** 64, n, dtype=np.uint64, endpoint=False)
+    if hi_distinct is not None:
+        hi = rng.choice(hi[:max(hi_distinct, 1)], n)
+    if lo_distinct is not None:
+        lo = rng.choice(lo[:max(lo_distinct, 1)], n)
+    return hi, lo
+
+
+@pytest.mark.parametrize("n,hi_d,lo_d", [(2, None, None), (1001, None, None), (300_001, None, None),
+                                        (300_000, 7, None), (300_000, None, 5), (300_000, 1, 3),
+                                        (2_000_001, 1000, 1000)])
+@pytest.mark.parametrize("with_vals", [True, False])
+def test_u128_keys_match_the_stable_order(n, hi_d, lo_d, with_vals):
+    """(high, low) word pairs sorted as unsigned 128-bit numbers, stably: the
+    oracle is the definition (numpy's stable lexsort on (high, low))."""
+    hi, lo = u128_case(n, n + 3, hi_d, lo_d)
+    words = np.empty(2 * n, dtype=np.uint64)
+    words[0::2], words[1::2] = lo, hi
+    k = torch.from_numpy(words.view(np.int64)).to(DEV)
+    v = torch.arange(n, dtype=torch.int32, device=DEV) if with_vals else None
+    z.sort_pairs_u128(k, v)
+    order = np.lexsort((lo, hi))  # primary hi, then lo; stable on ties
+    got = k.cpu().numpy().view(np.uint64)
+    assert np.array_equal(got[0::2], lo[order]) and np.array_equal(got[1::2], hi[order])
+    if with_vals:
+        assert np.array_equal(v.cpu().numpy().view(np.uint32), order.astype(np.uint32))
