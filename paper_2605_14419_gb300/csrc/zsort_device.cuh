@@ -81,8 +81,11 @@ struct Seg {
     uint32_t chunks;             // chunk tasks per phase
     uint32_t join;               // learned map: statistics + sample runs still running
     uint32_t next_type, next_nt; // learned map: the task the last of the two publishes
-    uint32_t pad1;
+    uint32_t range_map;          // the parent's partition left it more than half: exact range map
 };
+
+// Bit 15 of Item.level: partition this medium (sub)array with the range map.
+constexpr uint32_t ITEM_RANGE_MAP = 0x8000u;
 
 // A leaf group or a medium segment.
 struct Item {

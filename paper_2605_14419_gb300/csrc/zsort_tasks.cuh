@@ -201,11 +201,12 @@ __device__ __forceinline__ uint32_t choose_chunk_tiles(const Params &P, uint32_t
 }
 
 // Fills the map for a (sub)array from its exact sums: Eq. 1 (z-score) unless
-// the depth reached the guard level, in which case the exact range map.
+// the depth reached the guard level or the parent's partition made poor
+// progress (force_range), in which cases the exact range map.
 __device__ void map_from_sums(const Params &P, unsigned long long n, unsigned long long mn,
                               unsigned long long mx, const unsigned long long s1[2],
-                              const unsigned long long s2[3], uint32_t k, uint32_t level, MapSm &m,
-                              double *mean_d, double *sd)
+                              const unsigned long long s2[3], uint32_t k, uint32_t level, bool force_range,
+                              MapSm &m, double *mean_d, double *sd)
 {
     double var;
     moments_from_sums(n, mn, s1, s2, mean_d, &var);
@@ -219,7 +220,7 @@ __device__ void map_from_sums(const Params &P, unsigned long long n, unsigned lo
     m.zsh = 0;
     m.rshift = 0;
     m.rmult = 0;
-    if (level >= P.guard_level || !(*sd > 0.0)) {
+    if (level >= P.guard_level || force_range || !(*sd > 0.0)) {
         m.kind = MAP_RANGE;
         range_params(range, k, &m.rshift, &m.rmult);
         atomicAdd(&P.ctl->n_guard, 1ull);
@@ -614,8 +615,12 @@ __device__ void scatter_dispatch(const Params &P, SmemTile &s, Pipe &pp, const u
 // buckets are grouped into leaves of at most leaf_cap (<= LEAF_CAP) elements (sorting a
 // group of whole, ordered buckets gives the same result as sorting each);
 // larger buckets become medium or large (sub)arrays of the next level.
+// A child holding more than half of its parent (plen elements) -- typically a
+// value that dominates a skewed, duplicate-heavy input, which Eq. 1 keeps
+// lumped with its neighbours level after level -- is partitioned with the
+// exact range map, which separates the other values from it at once.
 __device__ __noinline__ void classify_children(const Params &P, unsigned long long poff, uint32_t k,
-                                  uint32_t child_buf, uint32_t child_level, SmemTile &s)
+                                  uint32_t child_buf, uint32_t child_level, uint32_t plen, SmemTile &s)
 {
     ChildList &L = s.u.children;
     if (threadIdx.x == 0) {
@@ -701,7 +706,8 @@ __device__ __noinline__ void classify_children(const Params &P, unsigned long lo
         it.off = poff + (leaf ? L.leaf_off[i] : L.med_off[i - nl]);
         it.len = leaf ? L.leaf_len[i] : L.med_len[i - nl];
         it.buf = (uint16_t)child_buf;
-        it.level = (uint16_t)child_level;
+        const bool poor = !leaf && 2ull * it.len > plen;  // medium child: range-map flag in bit 15
+        it.level = (uint16_t)(child_level | (poor ? ITEM_RANGE_MAP : 0u));
         P.items[base + i] = it;
     }
     for (uint32_t g = threadIdx.x; g < nok; g += BLOCK) {
@@ -723,7 +729,8 @@ __device__ __noinline__ void classify_children(const Params &P, unsigned long lo
         S->level = child_level;
         S->buf = child_buf;
         S->kind = MAP_Z;
-        const uint32_t slot = take_train_slot(P, len, S->k, child_level);
+        S->range_map = 2ull * len > plen;
+        const uint32_t slot = S->range_map ? INVALID : take_train_slot(P, len, S->k, child_level);
         S->train_slot = slot;
         S->join = SAMPLE_RUNS + 1;
         S->max_learned = S->max_z = 0;
@@ -872,7 +879,7 @@ __device__ __noinline__ void lstats_done(const Params &P, uint32_t sid, SmemTile
             unsigned long long s2[3] = {__ldcg(&S->s2[0]), __ldcg(&S->s2[1]), __ldcg(&S->s2[2])};
             MapSm m;
             double mean_d, sd;
-            map_from_sums(P, len, mn, mx, s1, s2, sk, level, m, &mean_d, &sd);
+            map_from_sums(P, len, mn, mx, s1, s2, sk, level, __ldcg(&S->range_map) != 0, m, &mean_d, &sd);
             S->mean_d = mean_d;
             S->sd = sd;
             S->kind = m.kind;
@@ -1449,7 +1456,7 @@ __device__ __noinline__ void lscatter_done(const Params &P, uint32_t sid, SmemTi
         note_level(P, level);
     }
     __syncthreads();
-    classify_children(P, off, k, buf ^ 1u, level + 1, s);
+    classify_children(P, off, k, buf ^ 1u, level + 1, __ldcg(&S->len), s);
 }
 
 // ------------------------------------------------------------ MPART
@@ -1458,7 +1465,8 @@ __device__ __noinline__ void lscatter_done(const Params &P, uint32_t sid, SmemTi
 __device__ __noinline__ void task_mpart(const Params &P, const Item it, SmemTile &s, Pipe &pp)
 {
     const unsigned long long off = it.off;
-    const uint32_t len = it.len, buf = it.buf, level = it.level;
+    const uint32_t len = it.len, buf = it.buf, level = it.level & (ITEM_RANGE_MAP - 1u);
+    const bool force_range = (it.level & ITEM_RANGE_MAP) != 0;
     const uint64_t *srck = keys_of(P, buf);
     const uint32_t *srcv = vals_of(P, buf);
     const bool bulk = bulk_ok(P, buf);
@@ -1477,7 +1485,7 @@ __device__ __noinline__ void task_mpart(const Params &P, const Item it, SmemTile
             unsigned long long s1[2] = {(unsigned long long)a.s1, (unsigned long long)(a.s1 >> 64)};
             unsigned long long s2[3] = {(unsigned long long)a.s2lo, (unsigned long long)(a.s2lo >> 64), a.s2hi};
             double mean_d, sd;
-            map_from_sums(P, len, a.mn, a.mx, s1, s2, choose_k(P, len), level, s.map, &mean_d, &sd);
+            map_from_sums(P, len, a.mn, a.mx, s1, s2, choose_k(P, len), level, force_range, s.map, &mean_d, &sd);
             if (level == 0 && off == 0) record_top(P, s.map, a.mn, a.mx, mean_d, sd);
         }
     }
@@ -1514,7 +1522,7 @@ __device__ __noinline__ void task_mpart(const Params &P, const Item it, SmemTile
         atomicAdd(&P.ctl->bytes, (16ull + 2ull * elem_bytes(P)) * len);
         note_level(P, level);
     }
-    classify_children(P, off, k, buf ^ 1u, level + 1, s);
+    classify_children(P, off, k, buf ^ 1u, level + 1, len, s);
 }
 
 // ------------------------------------------------------------ FINISH
