@@ -33,16 +33,16 @@ __global__ void __launch_bounds__(BLOCK, 2) k_persistent(const __grid_constant__
     __syncthreads();
     Pipe pp;
     for (int w = 0; w < KEY_STAGES; w++) pp.uses[w] = 0;
-    QCache qc[QUEUES];
-    for (int q = 0; q < QUEUES; q++) qc[q].e = INVALID;
     unsigned long long t_idle0 = 0, t_task0 = 0;
     for (;;) {
-        if (threadIdx.x == 0) {
+        if (threadIdx.x < 32) {  // warp 0 finds the next work
             t_idle0 = globaltimer();
-            dequeue(P, s.task, qc);
+            dequeue(P, s.task);
             t_task0 = globaltimer();
-            atomicAdd(&P.ctl->idle_ns, t_task0 - t_idle0);
-            if (s.task[0] != T_NONE) atomicMin(&P.ctl->t_first, t_task0);
+            if (threadIdx.x == 0) {
+                atomicAdd(&P.ctl->idle_ns, t_task0 - t_idle0);
+                if (s.task[0] != T_NONE) atomicMin(&P.ctl->t_first, t_task0);
+            }
         }
         __syncthreads();
         const uint32_t type = s.task[0], arg = s.task[1], tile0 = s.task[2];

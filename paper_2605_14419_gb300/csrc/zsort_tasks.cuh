@@ -67,63 +67,91 @@ __device__ void q_release_all(const Params &P, uint32_t e, uint32_t count)
     for (uint32_t i = 0; i < count; i++) st_relaxed(&P.ready[e + i], ep);
 }
 
-// Thread 0's cached copy of the entry at a queue's head.
-struct QCache {
-    uint32_t e, type, arg, ntiles;
-};
-
-// Thread 0: claims the next tiles of the entry at the head of the partition
-// queue, else of the leaf queue.  out = {type, arg, first tile, entry,
-// ntiles, count}; type T_NONE when all work is done or an error was
-// recorded.  A wait without any progress anywhere for longer than
+// Warp 0 of a CTA (all 32 lanes): claims the next tiles of a published entry,
+// partition queue first, else the leaf queue.  The lanes look at 32 entries
+// from the queue head at once: lane i reads entry head + i's ready word and
+// claim counter, the first entry with tiles left is claimed with one atomic,
+// and the head jumps over the leading run of published entries whose tiles
+// are all claimed (one compare-and-swap).  Lane 0 writes out = {type, arg,
+// first tile, entry, ntiles, count}; type T_NONE when all work is done or an
+// error was recorded.  A wait without any progress anywhere for longer than
 // P.wait_ns records ST_TIMEOUT.
-__device__ void dequeue(const Params &P, uint32_t *out, QCache *qc)
+__device__ void dequeue(const Params &P, uint32_t *out)
 {
+    const uint32_t full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
     Ctl *C = P.ctl;
     unsigned long long last = ld_relaxed64(&C->progress);
     unsigned long long t0 = globaltimer();
     const uint32_t ep = call_epoch(P);
-    out[0] = T_NONE;
+    if (lane == 0) out[0] = T_NONE;
     for (;;) {
-        if (ld_relaxed(&C->error)) return;
+        if (__shfl_sync(full, lane == 0 ? ld_relaxed(&C->error) : 0u, 0)) return;
         for (uint32_t q = 0; q < (uint32_t)QUEUES; q++) {
-            for (;;) {
-                const uint32_t h = ld_relaxed(&C->q_head[q]);
-                const uint32_t e = q * P.qcap + h;
-                if (e != qc[q].e) {
-                    if (h >= P.qcap || ld_acquire(&P.ready[e]) != ep) break;  // this queue is empty now
-                    uint4 en = __ldcg(reinterpret_cast<const uint4 *>(P.entries + e));
-                    qc[q].e = e;
-                    qc[q].type = en.x;
-                    qc[q].arg = en.y;
-                    qc[q].ntiles = en.z;
+            const uint32_t h = __shfl_sync(full, lane == 0 ? ld_relaxed(&C->q_head[q]) : 0u, 0);
+            uint32_t next_head = h;
+            for (uint32_t base = h; base < P.qcap; base += 32) {
+                const uint32_t i = base + lane;
+                const uint32_t e = q * P.qcap + i;
+                const bool rdy = i < P.qcap && ld_acquire(&P.ready[e]) == ep;
+                uint32_t type = 0, arg = 0, nt = 0, tn = 0;
+                if (rdy) {
+                    const uint4 en = __ldcg(reinterpret_cast<const uint4 *>(P.entries + e));
+                    type = en.x;
+                    arg = en.y;
+                    nt = en.z;
+                    tn = ld_relaxed(&P.tnext[e]);
                 }
-                // leaves are claimed a few at a time, so that each can be
-                // prefetched while its predecessor is sorted
-                const uint32_t nt = qc[q].ntiles;
-                const uint32_t claim = qc[q].type != T_FINISH ? 1u : (nt >= 64u ? 4u : (nt >= 16u ? 2u : 1u));
-                const uint32_t t = atomicAdd(&P.tnext[e], claim);
-                if (t < nt) {
-                    out[0] = qc[q].type;
-                    out[1] = qc[q].arg;
-                    out[2] = t;
-                    out[3] = e;
-                    out[4] = nt;
-                    out[5] = min(claim, nt - t);
-                    return;
+                const uint32_t mr = __ballot_sync(full, rdy);
+                uint32_t m = __ballot_sync(full, rdy && tn < nt);
+                while (m) {  // claim from the first entry with tiles left
+                    const int f = __ffs(m) - 1;
+                    uint32_t got = 0;
+                    if (lane == f) {
+                        // leaves are claimed a few at a time, so that each can
+                        // be prefetched while its predecessor is sorted
+                        const uint32_t claim = type != T_FINISH ? 1u : (nt >= 64u ? 4u : (nt >= 16u ? 2u : 1u));
+                        const uint32_t t = atomicAdd(&P.tnext[e], claim);
+                        if (t < nt) {
+                            out[0] = type;
+                            out[1] = arg;
+                            out[2] = t;
+                            out[3] = e;
+                            out[4] = nt;
+                            out[5] = min(claim, nt - t);
+                            got = 1;
+                        }
+                    }
+                    if (__shfl_sync(full, got, f)) {
+                        if (lane == 0 && next_head > h) atomicCAS(&C->q_head[q], h, next_head);
+                        return;
+                    }
+                    m &= m - 1;
                 }
-                atomicCAS(&C->q_head[q], h, h + 1);
+                // every published entry of this window is now fully claimed;
+                // the head may pass the leading run of them
+                const uint32_t lead = mr == full ? 32u : (uint32_t)(__ffs(~mr) - 1);
+                if (next_head == base) next_head = base + lead;
+                if (mr != full) break;  // an unpublished entry: look again later
+            }
+            if (lane == 0 && next_head > h) atomicCAS(&C->q_head[q], h, next_head);
+        }
+        uint32_t stop = 0;
+        if (lane == 0) {
+            if (ld_acquire(&C->pending) == 0) {
+                stop = 1;
+            } else {
+                const unsigned long long pr = ld_relaxed64(&C->progress), now = globaltimer();
+                if (pr != last) {
+                    last = pr;
+                    t0 = now;
+                } else if (now - t0 > P.wait_ns) {
+                    set_error(P, ST_TIMEOUT);
+                    stop = 1;
+                }
             }
         }
-        if (ld_acquire(&C->pending) == 0) return;
-        const unsigned long long pr = ld_relaxed64(&C->progress), now = globaltimer();
-        if (pr != last) {
-            last = pr;
-            t0 = now;
-        } else if (now - t0 > P.wait_ns) {
-            set_error(P, ST_TIMEOUT);
-            return;
-        }
+        if (__shfl_sync(full, stop, 0)) return;
         __nanosleep(128);
     }
 }
