@@ -1585,43 +1585,46 @@ __device__ bool insertion_sort_budget(unsigned long long *k, uint32_t *v, uint32
     return true;
 }
 
-// Bitonic sort of key/val[0..len) by (key, current position): stable.
-__device__ void bitonic_fallback(SmemTile &s, unsigned long long *key, uint32_t *val, uint32_t len)
+// Sorting network on key/val[a, a+c) by (key, current position), so stable:
+// the bitonic merge in the form whose comparators all put the smaller item
+// first (each merge starts by pairing i with the mirror index), so the
+// implicit +infinity items past c never move and need no storage.
+__device__ void bitonic_range(SmemTile &s, unsigned long long *key, uint32_t *val, uint32_t a, uint32_t c)
 {
-    const uint32_t L = pow2ceil32(len);
-    for (uint32_t p = threadIdx.x; p < L; p += BLOCK) {
-        if (p >= len) {
-            key[p] = ~0ull;
-            val[p] = 0u;
-            s.bkt[p] = 0xFFFFu;
-        } else {
-            s.bkt[p] = (uint16_t)p;
-        }
-    }
+    const uint32_t L = pow2ceil32(c);
+    for (uint32_t i = threadIdx.x; i < c; i += BLOCK) s.bkt[a + i] = (uint16_t)i;
     __syncthreads();
+    auto cmpswap = [&](uint32_t i, uint32_t j) {
+        const unsigned long long ki = key[a + i], kj = key[a + j];
+        const uint16_t ii = s.bkt[a + i], ij = s.bkt[a + j];
+        if (ki > kj || (ki == kj && ii > ij)) {
+            key[a + i] = kj;
+            key[a + j] = ki;
+            s.bkt[a + i] = ij;
+            s.bkt[a + j] = ii;
+            const uint32_t tv = val[a + i];
+            val[a + i] = val[a + j];
+            val[a + j] = tv;
+        }
+    };
     for (uint32_t size = 2; size <= L; size <<= 1) {
-        for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+        const uint32_t half = size >> 1;
+        for (uint32_t t = threadIdx.x; t < L / 2; t += BLOCK) {
+            const uint32_t blk = t / half, o = t % half;
+            const uint32_t i = blk * size + o, j = blk * size + size - 1 - o;
+            if (j < c) cmpswap(i, j);
+        }
+        __syncthreads();
+        for (uint32_t stride = half >> 1; stride > 0; stride >>= 1) {
             for (uint32_t t = threadIdx.x; t < L / 2; t += BLOCK) {
-                const uint32_t i = 2 * stride * (t / stride) + (t % stride);
-                const uint32_t jj = i + stride;
-                const bool asc = (i & size) == 0;
-                const unsigned long long ki = key[i], kj = key[jj];
-                const uint16_t ii = s.bkt[i], ij = s.bkt[jj];
-                const bool gt = ki > kj || (ki == kj && ii > ij);
-                if (gt == asc) {
-                    key[i] = kj;
-                    key[jj] = ki;
-                    s.bkt[i] = ij;
-                    s.bkt[jj] = ii;
-                    const uint32_t tv = val[i];
-                    val[i] = val[jj];
-                    val[jj] = tv;
-                }
+                const uint32_t i = 2 * stride * (t / stride) + (t % stride), j = i + stride;
+                if (j < c) cmpswap(i, j);
             }
             __syncthreads();
         }
     }
 }
+
 
 // Sub-bucket of a leaf key: range map (the counting map when rm == 0).
 __device__ __forceinline__ uint32_t leaf_sub(unsigned long long key, unsigned long long mn, uint32_t rs,
@@ -1717,18 +1720,37 @@ __device__ __noinline__ void finish_stable(const Params &P, SmemTile &s, unsigne
         }
     }
     if (threadIdx.x == 0) s.flag = 0;
+    for (uint32_t q = threadIdx.x; q < M; q += BLOCK) s.hist[q] = 0;
     __syncthreads();
-    bool ok = true;
+    // a sub-bucket is in order (stably: equal keys are in input order) unless
+    // two neighbours in it are inverted; only those are sorted -- one thread
+    // walking a long run of equal keys would hold up the whole CTA
+    for (uint32_t p = threadIdx.x + 1; p < len; p += BLOCK) {
+        const unsigned long long kp = key[p], kq = key[p - 1];
+        if (kq > kp) {
+            const uint32_t q = leaf_sub(kp, mn, rshift, rmult);
+            if (q == leaf_sub(kq, mn, rshift, rmult)) s.hist[q] = 1u;
+        }
+    }
+    __syncthreads();
+    // insertion sort (bounded moves) of each inverted sub-bucket; those that
+    // need more moves -- several distinct keys, each repeated many times --
+    // are listed and sorted by a CTA-wide network one after the other (an
+    // unfinished insertion sort keeps equal keys in input order, so sorting
+    // on the current position stays stable)
+    uint32_t *fail = s.bs;  // failed sub-buckets
     for (uint32_t q = threadIdx.x; q < M; q += BLOCK) {
         const uint32_t c = s.tcount[q];
-        if (c >= 2) ok = ok && insertion_sort_budget(key + s.tstart[q], val + s.tstart[q], c, 1024);
+        if (c >= 2 && s.hist[q] && !insertion_sort_budget(key + s.tstart[q], val + s.tstart[q], c, 1024))
+            fail[atomicAdd(&s.flag, 1u)] = q;
     }
-    if (!ok) s.flag = 1;
     __syncthreads();
-    if (s.flag) {
-        bitonic_fallback(s, key, val, len);
-        if (threadIdx.x == 0) atomicAdd(&P.ctl->n_leaf_fb, 1ull);
+    const uint32_t nfail = s.flag;
+    for (uint32_t f = 0; f < nfail; f++) {
+        const uint32_t q = fail[f];
+        bitonic_range(s, key, val, s.tstart[q], s.tcount[q]);
     }
+    if (threadIdx.x == 0 && nfail) atomicAdd(&P.ctl->n_leaf_fb, 1ull);
     for (uint32_t p = threadIdx.x; p < len; p += BLOCK) {
         __stcg(dk + p, key[p]);
         if (KV) __stcg(dv + p, val[p]);

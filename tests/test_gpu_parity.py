@@ -426,3 +426,28 @@ def test_u128_keys_match_the_stable_order(n, hi_d, lo_d, with_vals):
     assert np.array_equal(got[0::2], lo[order]) and np.array_equal(got[1::2], hi[order])
     if with_vals:
         assert np.array_equal(v.cpu().numpy().view(np.uint32), order.astype(np.uint32))
+
+
+def test_leaf_with_interleaved_repeated_keys_takes_the_network():
+    """Leaves whose sub-buckets mix two adjacent keys, each repeated ~1500
+    times in random order (the insertion sort's move budget runs out), plus
+    a few far keys that widen the range: sorted by the per-sub-bucket
+    sorting network, stably."""
+    rng = np.random.default_rng(51)
+    parts = []
+    for g in range(40):  # 40 leaves' worth, far apart
+        base = np.uint64(g) << np.uint64(56)
+        x = base + rng.integers(0, 2, 3000).astype(np.uint64) * np.uint64(1)
+        x[::997] = base + np.uint64(1 << 40)  # widen each leaf's range
+        parts.append(x)
+    keys = np.concatenate(parts)
+    vals = inputs.index_payload(keys.size)
+    k, v = to_dev(keys, vals)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        z.sort_pairs(k, v, stream=stream)
+        fb = z.last_stats(stream)["leaf_fallbacks"]
+    ok, ov = oracle.zsort_pairs(keys, vals)
+    assert np.array_equal(k.cpu().numpy().view(np.uint64), ok)
+    assert np.array_equal(v.cpu().numpy().view(np.uint32), ov)
+    assert fb > 0
