@@ -133,6 +133,33 @@ typedef struct {
  * keys/vals are not touched and the next call on the stream works as usual.
  * Not a sort: it exists to check the failure path without any GPU fault. */
 #define ZSORT_FLAG_TEST_STALL 2u
+/* Task trace: the persistent kernel records every task it runs (one record
+ * per dequeued task: start and end time, CTA, task type, partition depth),
+ * read back with zsort_last_trace.  The first traced call on a stream
+ * allocates the workspace's trace buffer of ZSORT_TRACE_CAP records (32 MB);
+ * tasks past it are counted, not recorded.  Costs one global atomic and one
+ * 32-byte store per task. */
+#define ZSORT_FLAG_TRACE 4u
+#define ZSORT_TRACE_CAP (1u << 20)
+
+/* One record of the task trace.  type is the task type of zsort_stats.task_ns
+ * (1 statistics chunk, 2 learned-map sample run, 3 histogram chunk, 4
+ * scatter chunk, 5 single-CTA partition, 6 finish, 7 copy, 8 map inspection,
+ * 9 learned-map fit), or ZSORT_TRACE_HANDLER + t for the phase-completion
+ * work that the last task of a phase of type t ran right after it (the
+ * bucket scan after a histogram, the classification of the children after
+ * a scatter; count 0).  Times are the device's globaltimer in ns.  A CTA's
+ * idle time is the gap between its consecutive records. */
+#define ZSORT_TRACE_HANDLER 16u
+typedef struct {
+    uint64_t t_start_ns;
+    uint64_t t_end_ns;
+    uint32_t cta;     /* block index in the persistent launch                 */
+    uint16_t type;    /* task type (above)                                    */
+    uint16_t level;   /* partition depth of the task's (sub)array              */
+    uint32_t arg;     /* (sub)array descriptor, or item index for types 5 and 6 */
+    uint32_t count;   /* chunks / items the task covered                       */
+} zsort_trace_rec;
 
 /* Counters of the last completed call on a (device, stream) workspace. */
 typedef struct {
@@ -227,6 +254,13 @@ int zsort_sync_status(zsort_stream_t stream);
 
 /* Waits for `stream` and copies the counters of its last call to *out. */
 int zsort_last_stats(zsort_stream_t stream, zsort_stats *out);
+
+/* Waits for `stream` and copies the task trace of its last call (made with
+ * ZSORT_FLAG_TRACE) to out[0 .. min(cap, recorded, ZSORT_TRACE_CAP)), in the
+ * order the tasks finished.  *count = tasks of that call (more than were
+ * recorded if the buffer overflowed; 0 if the call was not traced).  out may
+ * be NULL when cap is 0.  ZSORT_ERR_INVALID if count is NULL. */
+int zsort_last_trace(zsort_stream_t stream, zsort_trace_rec *out, uint64_t cap, uint64_t *count);
 
 /* Top-level partition plan of one array (zsort_map_buckets). */
 typedef struct {

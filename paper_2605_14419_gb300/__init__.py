@@ -36,6 +36,11 @@ MAX_N = 1 << 30
 MAX_SEG_TOTAL = 1 << 34
 FLAG_GRAPH = 1
 FLAG_TEST_STALL = 2
+FLAG_TRACE = 4
+TRACE_CAP = 1 << 20
+TASK_TYPES = {1: "stats", 2: "train", 3: "hist", 4: "scatter", 5: "mpart", 6: "finish", 7: "copy",
+              8: "dump", 9: "fit"}
+TRACE_HANDLER = 16
 NOALLOC_MAX_N = 1 << 20
 
 
@@ -105,6 +110,20 @@ class Stats(ctypes.Structure):
         return out
 
 
+class TraceRec(ctypes.Structure):
+    """``zsort_trace_rec``: one task of the persistent kernel."""
+
+    _fields_ = [
+        ("t_start_ns", ctypes.c_uint64),
+        ("t_end_ns", ctypes.c_uint64),
+        ("cta", ctypes.c_uint32),
+        ("type", ctypes.c_uint16),
+        ("level", ctypes.c_uint16),
+        ("arg", ctypes.c_uint32),
+        ("count", ctypes.c_uint32),
+    ]
+
+
 class MapInfo(ctypes.Structure):
     """``zsort_map_info``: the top-level partition plan of one array."""
 
@@ -164,6 +183,7 @@ def load():
         "zsort_release": (i32, []),
         "zsort_sync_status": (i32, [vp]),
         "zsort_last_stats": (i32, [vp, ctypes.POINTER(Stats)]),
+        "zsort_last_trace": (i32, [vp, ctypes.POINTER(TraceRec), u64, ctypes.POINTER(u64)]),
         "zsort_strerror": (ctypes.c_char_p, [i32]),
         "zsort_pairs_noalloc": (i32, [vp, vp, u64, vp, vp]),
         "zsort_map_buckets": (i32, [vp, u64, ctypes.POINTER(Opts), vp, ctypes.POINTER(MapInfo), vp]),
@@ -319,6 +339,22 @@ def last_stats(stream=None) -> dict:
     s = Stats()
     _raise(load().zsort_last_stats(_stream_handle(stream), ctypes.byref(s)), "zsort_last_stats")
     return s.as_dict()
+
+
+def last_trace(stream=None, cap: int = TRACE_CAP):
+    """Task trace of the last call on a stream (made with ``FLAG_TRACE``):
+    (numpy structured array of the recorded tasks, number of tasks)."""
+    import numpy as np
+
+    buf = (TraceRec * max(cap, 1))()
+    count = ctypes.c_uint64(0)
+    _raise(load().zsort_last_trace(_stream_handle(stream), buf, cap, ctypes.byref(count)), "zsort_last_trace")
+    m = min(count.value, cap, TRACE_CAP)
+    dt = np.dtype([("t_start_ns", "<u8"), ("t_end_ns", "<u8"), ("cta", "<u4"), ("type", "<u2"),
+                   ("level", "<u2"), ("arg", "<u4"), ("count", "<u4")])
+    assert dt.itemsize == ctypes.sizeof(TraceRec)
+    arr = np.frombuffer(ctypes.string_at(ctypes.addressof(buf), m * dt.itemsize), dtype=dt).copy()
+    return arr, count.value
 
 
 # ------------------------------------------------------------ autotuner

@@ -16,12 +16,42 @@
 #include <mutex>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/zsort.h"
 #include "zsort_tasks.cuh"
+
+static_assert(sizeof(zsort_trace_rec) == sizeof(zs::TraceRec), "trace record layout");
 
 using namespace zs;
 
 // ---------------------------------------------------------------- kernels
+// Thread 0: one record of the task trace (records past the buffer are
+// counted, not written).
+__device__ __noinline__ void trace_task(const Params &P, uint32_t type, uint32_t arg, uint32_t tile0, uint32_t count,
+                                        unsigned long long t0, unsigned long long t1)
+{
+    const unsigned long long i = atomicAdd(&P.ctl->trace_n, 1ull);
+    if (i >= P.trace_cap) return;
+    uint32_t level = 0, a = arg;
+    const uint32_t base = type & (TRACE_HANDLER - 1u);
+    if (base == T_MPART || base == T_FINISH) {
+        a = arg + tile0;
+        level = load_item(P, a).level & (ITEM_RANGE_MAP - 1u);
+    } else if (base != T_NONE && arg < P.segcap) {
+        level = __ldcg(&P.segs[arg].level);
+    }
+    TraceRec r;
+    r.t_start = t0;
+    r.t_end = t1;
+    r.cta = blockIdx.x;
+    r.type = (uint16_t)type;
+    r.level = (uint16_t)min(level, 0xffffu);
+    r.arg = a;
+    r.count = count;
+    P.trace[i] = r;
+}
+
 __global__ void __launch_bounds__(BLOCK, 2) k_persistent(const __grid_constant__ Params P)
 {
     extern __shared__ __align__(128) unsigned char smraw[];
@@ -33,7 +63,7 @@ __global__ void __launch_bounds__(BLOCK, 2) k_persistent(const __grid_constant__
     __syncthreads();
     Pipe pp;
     for (int w = 0; w < KEY_STAGES; w++) pp.uses[w] = 0;
-    unsigned long long t_idle0 = 0, t_task0 = 0;
+    unsigned long long t_idle0 = 0, t_task0 = 0, t_task1 = 0;
     for (;;) {
         if (threadIdx.x < 32) {  // warp 0 finds the next work
             t_idle0 = globaltimer();
@@ -73,7 +103,8 @@ __global__ void __launch_bounds__(BLOCK, 2) k_persistent(const __grid_constant__
             __syncthreads();
         }
         if (threadIdx.x == 0) {
-            unsigned long long t1 = globaltimer();
+            const unsigned long long t1 = globaltimer();
+            t_task1 = t1;
             const uint32_t ti = type == T_LFIT ? (uint32_t)T_LSAMPLE : (type & 7u);  // both: learned map
             atomicAdd(&P.ctl->task_ns[ti], t1 - t_task0);
             atomicAdd(&P.ctl->task_cnt[ti], (unsigned long long)count);
@@ -102,6 +133,10 @@ __global__ void __launch_bounds__(BLOCK, 2) k_persistent(const __grid_constant__
             unsigned long long t2 = globaltimer();
             if (s.flag2) atomicAdd(&P.ctl->handler_ns, t2 - t_task0);
             atomicMax(&P.ctl->t_last, t2);
+            if (P.trace) {
+                trace_task(P, type, arg, tile0, count, t_task0, t_task1);
+                if (s.flag2) trace_task(P, TRACE_HANDLER | type, arg, tile0, 0, t_task1, t2);
+            }
         }
     }
 }
@@ -165,7 +200,6 @@ __global__ void k_init_segments(Params P, const uint64_t *off, unsigned long lon
             S->train_slot = take_train_slot(P, (uint32_t)len, kk, 0);
             S->join = SAMPLE_RUNS + 1;
             S->max_learned = S->max_z = 0;
-            for (uint32_t q = 0; q < kk; q++) P.counts[(size_t)sid * NB_MAX + q] = 0;
             return;
         }
         if (sid < P.segcap) P.segs[sid].len = 0;  // no room: partitioned by one CTA
@@ -271,6 +305,13 @@ struct Workspace {
     uint32_t epoch = 0;
     int sms = 0;
     int occ = 0;
+    TraceRec *trace = nullptr;  // task trace buffer (ZSORT_TRACE_CAP records), on first traced call
+};
+
+// Names the host-side span of a public call in profiler timelines (NVTX).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
 };
 
 std::mutex g_mu;
@@ -286,7 +327,7 @@ size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 struct Plan {
     unsigned long long qcap, segcap, itemcap, statuscap, traincap;
     size_t off_skeys, off_svals, off_ctl, off_epoch, off_entries, off_ready, off_tnext, off_tdone, off_segs,
-        off_items, off_counts, off_bstart, off_status, off_pwl, off_train, total;
+        off_items, off_bstart, off_status, off_pwl, off_train, total;
 };
 
 Plan make_plan(unsigned long long n, unsigned long long nseg, unsigned long long large_min, int sms,
@@ -320,7 +361,6 @@ Plan make_plan(unsigned long long n, unsigned long long nseg, unsigned long long
     p.off_tdone = take(QUEUES * p.qcap * 4);
     p.off_segs = take(p.segcap * sizeof(Seg));
     p.off_items = take(p.itemcap * sizeof(Item));
-    p.off_counts = take(p.segcap * NB_MAX * 4);
     p.off_bstart = take(p.segcap * NB_MAX * 4);
     p.off_status = take(p.statuscap * 4);
     p.off_pwl = take(p.segcap * PWL_STRIDE * 4);
@@ -403,7 +443,6 @@ int get_workspace(cudaStream_t stream, unsigned long long n, unsigned long long 
         P.segcap = (uint32_t)p.segcap;
         P.items = reinterpret_cast<Item *>(b + p.off_items);
         P.itemcap = (uint32_t)p.itemcap;
-        P.counts = reinterpret_cast<uint32_t *>(b + p.off_counts);
         P.bstart = reinterpret_cast<uint32_t *>(b + p.off_bstart);
         P.status = reinterpret_cast<uint32_t *>(b + p.off_status);
         P.statuscap = p.statuscap;
@@ -473,6 +512,18 @@ int launch(uint64_t *keys, uint32_t *vals, unsigned long long n, const uint64_t 
     P.user_aligned = ((reinterpret_cast<uintptr_t>(keys) | reinterpret_cast<uintptr_t>(vals)) & 15u) == 0;
     P.kv = vals != nullptr;  // null vals: keys only
     P.test_stall = (o.flags & ZSORT_FLAG_TEST_STALL) ? 1u : 0u;
+    if (o.flags & ZSORT_FLAG_TRACE) {
+        if (!ws->trace) {
+            void *t = nullptr;
+            if (cudaMalloc(&t, (size_t)ZSORT_TRACE_CAP * sizeof(TraceRec)) != cudaSuccess) {
+                cudaGetLastError();
+                return ZSORT_ERR_NOMEM;
+            }
+            ws->trace = static_cast<TraceRec *>(t);
+        }
+        P.trace = ws->trace;
+        P.trace_cap = ZSORT_TRACE_CAP;
+    }
     int per_sm = o.ctas_per_sm ? (int)std::min<uint32_t>(o.ctas_per_sm, (uint32_t)ws->occ) : ws->occ;
     P.nctas = (uint32_t)(ws->sms * per_sm);
     P.plan_out = plan_out;
@@ -584,7 +635,7 @@ constexpr size_t na_align(size_t x) { return (x + 255) & ~size_t(255); }
 // NA_MAX_N elements and one segment, with one learned-map training slot.
 struct NaLayout {
     unsigned long long qcap, segcap, itemcap, statuscap, traincap;
-    size_t skeys, svals, ctl, epoch, entries, ready, tnext, tdone, segs, items, counts, bstart, status, pwl,
+    size_t skeys, svals, ctl, epoch, entries, ready, tnext, tdone, segs, items, bstart, status, pwl,
         train, total;
 };
 constexpr NaLayout na_layout()
@@ -606,7 +657,6 @@ constexpr NaLayout na_layout()
     L.tdone = o; o = na_align(o + QUEUES * L.qcap * 4);
     L.segs = o; o = na_align(o + L.segcap * sizeof(Seg));
     L.items = o; o = na_align(o + L.itemcap * sizeof(Item));
-    L.counts = o; o = na_align(o + L.segcap * NB_MAX * 4);
     L.bstart = o; o = na_align(o + L.segcap * NB_MAX * 4);
     L.status = o; o = na_align(o + L.statuscap * 4);
     L.pwl = o; o = na_align(o + L.segcap * PWL_STRIDE * 4);
@@ -663,6 +713,7 @@ void zsort_default_opts(zsort_opts *o)
 int zsort_pairs_ex(void *keys, uint32_t key_type, uint32_t *vals, uint64_t n, const zsort_opts *opts,
                    zsort_stream_t stream)
 {
+    NvtxRange nv("zsort_pairs_ex");
     zsort_opts o;
     if (opts)
         o = *opts;
@@ -682,6 +733,7 @@ int zsort_pairs_ex(void *keys, uint32_t key_type, uint32_t *vals, uint64_t n, co
 
 int zsort_pairs_u128(uint64_t *keys, uint32_t *vals, uint64_t n, const zsort_opts *opts, zsort_stream_t stream)
 {
+    NvtxRange nv("zsort_pairs_u128");
     zsort_opts o;
     if (opts)
         o = *opts;
@@ -751,6 +803,7 @@ int zsort_pairs_f64(double *keys, uint32_t *vals, uint64_t n, zsort_stream_t str
 int zsort_segmented_ex(uint64_t *keys, uint32_t *vals, uint64_t n, const uint64_t *seg_offsets,
                        uint64_t nseg, const zsort_opts *opts, zsort_stream_t stream)
 {
+    NvtxRange nv("zsort_segmented_ex");
     zsort_opts o;
     if (opts)
         o = *opts;
@@ -794,6 +847,7 @@ int zsort_release(void)
         }
         if (w->graph.valid) cudaGraphExecDestroy(w->graph.exec);
         if (w->block && cudaFree(w->block) != cudaSuccess) rc = ZSORT_ERR_CUDA;
+        if (w->trace && cudaFree(w->trace) != cudaSuccess) rc = ZSORT_ERR_CUDA;
         delete w;
     }
     g_ws.swap(keep);
@@ -860,9 +914,29 @@ int zsort_last_stats(zsort_stream_t stream, zsort_stats *out)
     return ZSORT_OK;
 }
 
+int zsort_last_trace(zsort_stream_t stream, zsort_trace_rec *out, uint64_t cap, uint64_t *count)
+{
+    if (!count || (cap > 0 && !out)) return ZSORT_ERR_INVALID;
+    *count = 0;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t ce = cudaStreamSynchronize(st);
+    if (ce != cudaSuccess) return cuda_err(ce);
+    std::lock_guard<std::mutex> lock(g_mu);
+    Workspace *ws = find_ws(st);
+    if (!ws || !ws->block) return ZSORT_OK;
+    unsigned long long nrec = 0;
+    ce = cudaMemcpy(&nrec, &ws->P.ctl->trace_n, sizeof(nrec), cudaMemcpyDeviceToHost);
+    if (ce != cudaSuccess) return cuda_err(ce);
+    *count = nrec;
+    const unsigned long long m = std::min<unsigned long long>(std::min<unsigned long long>(nrec, cap), ZSORT_TRACE_CAP);
+    if (m == 0 || !ws->trace) return ZSORT_OK;
+    return cuda_err(cudaMemcpy(out, ws->trace, m * sizeof(TraceRec), cudaMemcpyDeviceToHost));
+}
+
 int zsort_map_buckets(const uint64_t *keys, uint64_t n, const zsort_opts *opts, uint32_t *buckets,
                       zsort_map_info *info, zsort_stream_t stream)
 {
+    NvtxRange nv("zsort_map_buckets");
     zsort_opts o;
     if (opts)
         o = *opts;
@@ -923,6 +997,7 @@ int zsort_map_buckets(const uint64_t *keys, uint64_t n, const zsort_opts *opts, 
 // that first call before any stream capture.
 int zsort_pairs_noalloc(uint64_t *keys, uint32_t *vals, uint64_t n, int32_t *status, zsort_stream_t stream)
 {
+    NvtxRange nv("zsort_pairs_noalloc");
     if (n > NA_MAX_N) return ZSORT_ERR_INVALID;
     if (n <= 1) {
         if (status) {
@@ -973,7 +1048,6 @@ int zsort_pairs_noalloc(uint64_t *keys, uint32_t *vals, uint64_t n, int32_t *sta
     P.segcap = (uint32_t)NA.segcap;
     P.items = reinterpret_cast<Item *>(b + NA.items);
     P.itemcap = (uint32_t)NA.itemcap;
-    P.counts = reinterpret_cast<uint32_t *>(b + NA.counts);
     P.bstart = reinterpret_cast<uint32_t *>(b + NA.bstart);
     P.status = reinterpret_cast<uint32_t *>(b + NA.status);
     P.statuscap = NA.statuscap;

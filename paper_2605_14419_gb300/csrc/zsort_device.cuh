@@ -4,7 +4,7 @@
 // payloads):  the caller's keys/vals, a scratch pair of the same length
 // (scratch[i] mirrors user[i]; a bucket keeps its index range in both), and
 // the bookkeeping pools of the persistent executor (queue entries, large
-// segment descriptors, work items, bucket counts, look-back status rows,
+// segment descriptors, work items, bucket starts, look-back status rows,
 // learned-map tables and training buffers).
 #pragma once
 #include <cuda_runtime.h>
@@ -122,7 +122,19 @@ struct Ctl {
     // device time per task type (ns, summed over CTAs), handler and idle time
     unsigned long long task_ns[8], task_cnt[8], handler_ns, idle_ns;
     unsigned long long t_first, t_last;
+    unsigned long long trace_n;    // task records written (or attempted) to the trace
 };
+
+// Trace type of the phase-completion work a task triggered (type | this).
+constexpr uint32_t TRACE_HANDLER = 16u;
+// One task of the persistent kernel in the optional trace (zsort_trace_rec).
+struct TraceRec {
+    unsigned long long t_start, t_end;
+    uint32_t cta;
+    uint16_t type, level;
+    uint32_t arg, count;
+};
+static_assert(sizeof(TraceRec) == 32, "trace record layout");
 
 struct Params {
     uint64_t *ukeys;
@@ -140,7 +152,6 @@ struct Params {
     uint32_t segcap;
     Item *items;
     uint32_t itemcap;
-    uint32_t *counts;   // segcap * NB_MAX
     uint32_t *bstart;   // segcap * NB_MAX
     uint32_t *status;            // look-back words and chunk offsets: 2 * chunks * k per segment
     unsigned long long statuscap;
@@ -149,6 +160,8 @@ struct Params {
     uint32_t user_aligned;       // caller's keys and vals 16-byte aligned: bulk copies allowed
     uint32_t kv;                 // 1: (key, payload) pairs; 0: keys only (vals == null)
     uint32_t test_stall;         // publish nothing, one entry pending: every wait runs out
+    TraceRec *trace;             // task trace (null: not traced)
+    uint32_t trace_cap;          // records trace can hold
     float *pwl;         // segcap * PWL_STRIDE: breakpoints q[0..P], reciprocals r[0..P), MLP table
     unsigned long long *trainbuf; // traincap * 2 * SAMPLE_MAX sampled keys (ping-pong)
     uint32_t traincap;
@@ -521,6 +534,7 @@ struct ChildList {
     uint32_t leaf_off[NB_MAX], leaf_len[NB_MAX];
     uint32_t med_off[NB_MAX], med_len[NB_MAX];
     uint32_t lg_off[NB_MAX], lg_len[NB_MAX], lg_need[NB_MAX], lg_slot[NB_MAX];
+    uint32_t lg_ct[NB_MAX], lg_chunks[NB_MAX], lg_k[NB_MAX];  // chunk tiles, chunks, buckets
 };
 
 struct TileBuf {

@@ -651,49 +651,84 @@ __device__ __noinline__ void classify_children(const Params &P, unsigned long lo
                                   uint32_t child_buf, uint32_t child_level, uint32_t plen, SmemTile &s)
 {
     ChildList &L = s.u.children;
+    // 1. thread 0 walks the buckets in order: leaf groups, medium and large
+    //    children (shared memory only)
     if (threadIdx.x == 0) {
+        // in registers: the loop's shared-memory stores would otherwise make
+        // the compiler reload the launch parameters on every bucket
+        const uint32_t leaf_cap = P.leaf_cap, large_min = P.large_min;
         uint32_t nl = 0, nm = 0, ng = 0, glen = 0, gstart = 0;
-        for (uint32_t b = 0; b < k; b++) {
-            uint32_t c = s.hist[b];
+        for (uint32_t b8 = 0; b8 < k; b8 += 8) {  // k: a power of two >= 16
+          uint32_t cc[8], ss[8];
+#pragma unroll
+          for (int j = 0; j < 8; j++) {  // eight independent loads, then the walk
+              cc[j] = s.hist[b8 + j];
+              ss[j] = s.bs[b8 + j];
+          }
+#pragma unroll
+          for (int j = 0; j < 8; j++) {
+            const uint32_t c = cc[j];
             if (c == 0) continue;
-            if (c > P.leaf_cap) {
+            if (c > leaf_cap) {
                 if (glen) {
                     L.leaf_off[nl] = gstart;
                     L.leaf_len[nl++] = glen;
                     glen = 0;
                 }
-                if (c <= P.large_min) {
-                    L.med_off[nm] = s.bs[b];
+                if (c <= large_min) {
+                    L.med_off[nm] = ss[j];
                     L.med_len[nm++] = c;
                 } else {
-                    L.lg_off[ng] = s.bs[b];
+                    L.lg_off[ng] = ss[j];
                     L.lg_len[ng++] = c;
                 }
             } else {
-                if (glen + c > P.leaf_cap) {
+                if (glen + c > leaf_cap) {
                     L.leaf_off[nl] = gstart;
                     L.leaf_len[nl++] = glen;
                     glen = 0;
                 }
-                if (glen == 0) gstart = s.bs[b];
+                if (glen == 0) gstart = ss[j];
                 glen += c;
             }
+          }
         }
         if (glen) {
             L.leaf_off[nl] = gstart;
             L.leaf_len[nl++] = glen;
         }
         if (child_level > (uint32_t)MAX_LEVEL && (nm + ng) > 0) set_error(P, ST_INTERNAL);
-        // large children: one descriptor and look-back rows each, allocated
-        // for the whole batch with two atomics; no room -> all medium
-        unsigned long long need = 0;
-        for (uint32_t g = 0; g < ng; g++) {
-            const uint32_t len = L.lg_len[g];
-            const uint32_t tiles = (len + TILE - 1) / TILE;
-            const uint32_t chunks = (tiles + choose_chunk_tiles(P, tiles, len) - 1) / choose_chunk_tiles(P, tiles, len);
-            L.lg_need[g] = (uint32_t)need;
-            need += 2ull * chunks * choose_k(P, len);
-        }
+        s.n_leaf = nl;
+        s.n_med = nm;
+        s.n_large = ng;
+        s.red64[0] = 0;
+    }
+    __syncthreads();
+    const uint32_t ng = s.n_large;
+    // 2. every thread a share of the large children: chunk geometry and
+    //    look-back rows (2 x chunks x k words each), then their offsets
+    unsigned long long part = 0;
+    for (uint32_t g = threadIdx.x; g < ng; g += BLOCK) {
+        const uint32_t len = L.lg_len[g];
+        const uint32_t tiles = (len + TILE - 1) / TILE;
+        const uint32_t ct = choose_chunk_tiles(P, tiles, len);
+        const uint32_t chunks = (tiles + ct - 1) / ct;
+        const uint32_t kk = choose_k(P, len);
+        L.lg_ct[g] = ct;
+        L.lg_chunks[g] = chunks;
+        L.lg_k[g] = kk;
+        L.lg_need[g] = 2u * chunks * kk;
+        part += 2ull * chunks * kk;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if ((threadIdx.x & 31) == 0 && part) atomicAdd(&s.red64[0], part);
+    __syncthreads();
+    const unsigned long long need = s.red64[0];
+    if (need < (1ull << 32)) block_exclusive_scan(L.lg_need, L.lg_need, ng, s.wsum);  // ends with a barrier
+    // 3. thread 0: one allocation of descriptors, look-back rows and items
+    if (threadIdx.x == 0) {
+        uint32_t nl = s.n_leaf, nm = s.n_med;
         uint32_t sid0 = 0;
         unsigned long long sb0 = 0;
         bool ok = ng > 0 && need < (1ull << 32);
@@ -706,7 +741,7 @@ __device__ __noinline__ void classify_children(const Params &P, unsigned long lo
             ok = sb0 + need <= P.statuscap;
         }
         uint32_t nok = ng;
-        if (!ok && ng > 0) {
+        if (!ok && ng > 0) {  // no room: all medium
             for (uint32_t g = 0; g < ng; g++) {
                 L.med_off[nm] = L.lg_off[g];
                 L.med_len[nm++] = L.lg_len[g];
@@ -723,11 +758,12 @@ __device__ __noinline__ void classify_children(const Params &P, unsigned long lo
         s.n_large_ok = nok;
         s.item_base = base;
         s.e_base = sid0;
-        s.red64[0] = sb0;
+        s.red64[1] = sb0;
     }
     __syncthreads();
     const uint32_t nl = s.n_leaf, nm = s.n_med, nok = s.n_large_ok, base = s.item_base, sid0 = s.e_base;
-    const unsigned long long sb0 = s.red64[0];
+    const unsigned long long sb0 = s.red64[1];
+    // 4. items, descriptors and cleared counters, every thread a share
     for (uint32_t i = threadIdx.x; i < nl + nm; i += BLOCK) {
         Item it;
         const bool leaf = i < nl;
@@ -740,8 +776,6 @@ __device__ __noinline__ void classify_children(const Params &P, unsigned long lo
     }
     for (uint32_t g = threadIdx.x; g < nok; g += BLOCK) {
         const uint32_t len = L.lg_len[g];
-        const uint32_t tiles = (len + TILE - 1) / TILE;
-        const uint32_t ct = choose_chunk_tiles(P, tiles, len);
         Seg *S = &P.segs[sid0 + g];
         S->off = poff + L.lg_off[g];
         S->mn = ~0ull;
@@ -750,10 +784,10 @@ __device__ __noinline__ void classify_children(const Params &P, unsigned long lo
         S->s2[0] = S->s2[1] = S->s2[2] = 0ull;
         S->status_base = sb0 + L.lg_need[g];
         S->len = len;
-        S->k = choose_k(P, len);
-        S->tiles = tiles;
-        S->chunk_tiles = ct;
-        S->chunks = (tiles + ct - 1) / ct;
+        S->k = L.lg_k[g];
+        S->tiles = (len + TILE - 1) / TILE;
+        S->chunk_tiles = L.lg_ct[g];
+        S->chunks = L.lg_chunks[g];
         S->level = child_level;
         S->buf = child_buf;
         S->kind = MAP_Z;
@@ -764,31 +798,26 @@ __device__ __noinline__ void classify_children(const Params &P, unsigned long lo
         S->max_learned = S->max_z = 0;
         L.lg_slot[g] = slot;
     }
-    for (uint32_t g = 0; g < nok; g++) {
-        const uint32_t kk = choose_k(P, L.lg_len[g]);
-        for (uint32_t q = threadIdx.x; q < kk; q += BLOCK) P.counts[(size_t)(sid0 + g) * NB_MAX + q] = 0;
-    }
-    __threadfence();  // descriptors, items and counters before the entries are published
+    __threadfence();  // descriptors and items before the entries are published
     __syncthreads();
+    // 5. queue entries: thread 0 reserves them and writes the learned-map
+    //    samples (few: one per training slot) first -- each is one CTA's long
+    //    task that runs beside its (sub)array's statistics tiles; every
+    //    thread then writes a share of the statistics entries, and the ready
+    //    words follow one fence later
     if (threadIdx.x == 0) {
         uint32_t nsample = 0;
         for (uint32_t g = 0; g < nok; g++) nsample += L.lg_slot[g] != INVALID;
         const uint32_t cnt = (nm > 0) + nok + nsample;
-        const uint32_t e = q_reserve(P, cnt, 0);
-        if (e != INVALID && cnt) {
+        uint32_t e = cnt ? q_reserve(P, cnt, 0) : INVALID;
+        if (e != INVALID) {
             uint32_t j = e;
-            // the learned-map samples first: each is one CTA's long task that
-            // runs beside its (sub)array's statistics tiles
-            for (uint32_t g = 0; g < nok; g++)
+            for (uint32_t g = 0; g < nok && j < e + nsample; g++)
                 if (L.lg_slot[g] != INVALID) q_write(P, j++, T_LSAMPLE, sid0 + g, SAMPLE_RUNS);
-            for (uint32_t g = 0; g < nok; g++) {
-                const uint32_t tiles = (L.lg_len[g] + TILE - 1) / TILE;
-                const uint32_t ct = choose_chunk_tiles(P, tiles, L.lg_len[g]);
-                q_write(P, j++, T_LSTATS, sid0 + g, (tiles + ct - 1) / ct);
-            }
-            if (nm) q_write(P, j++, T_MPART, base + nl, nm);
-            q_release_all(P, e, cnt);
+            if (nm) q_write(P, e + nsample + nok, T_MPART, base + nl, nm);
         }
+        s.red64[2] = e;
+        s.red64[3] = ((unsigned long long)cnt << 32) | nsample;
         if (nl) {
             const uint32_t el = q_reserve(P, 1, queue_of(T_FINISH));
             if (el != INVALID) {
@@ -796,6 +825,16 @@ __device__ __noinline__ void classify_children(const Params &P, unsigned long lo
                 q_release_all(P, el, 1);
             }
         }
+    }
+    __syncthreads();
+    const uint32_t e = (uint32_t)s.red64[2], nsample = (uint32_t)s.red64[3], cnt = (uint32_t)(s.red64[3] >> 32);
+    if (e != INVALID) {
+        for (uint32_t g = threadIdx.x; g < nok; g += BLOCK)
+            q_write(P, e + nsample + g, T_LSTATS, sid0 + g, L.lg_chunks[g]);
+        __threadfence();
+        __syncthreads();
+        const uint32_t ep = call_epoch(P);
+        for (uint32_t i = threadIdx.x; i < cnt; i += BLOCK) st_relaxed(&P.ready[e + i], ep);
     }
     __syncthreads();
 }
@@ -1373,7 +1412,6 @@ __device__ __noinline__ void task_lhist(const Params &P, uint32_t sid, uint32_t 
     for (uint32_t q = threadIdx.x; q < k; q += BLOCK) {
         const uint32_t h = s.hist[q];
         st_relaxed(row + q, (c == 0 ? FLAG_P : FLAG_A) | h);
-        if (h) atomicAdd(&P.counts[(size_t)sid * NB_MAX + q], h);
     }
     constexpr int PER = NB_MAX / BLOCK;
     uint32_t excl[PER], j[PER];
@@ -1433,11 +1471,20 @@ __device__ __noinline__ void task_lhist(const Params &P, uint32_t sid, uint32_t 
     if (threadIdx.x == 0) atomicAdd(&P.ctl->bytes, 8ull * ch.len);
 }
 
+// Bucket totals of a large (sub)array once all its chunks are through the
+// look-back: the inclusive prefix that its last chunk published.
+__device__ __forceinline__ void load_bucket_totals(const Params &P, const Seg *S, uint32_t k, uint32_t chunks,
+                                                   uint32_t *out)
+{
+    const uint32_t *last = P.status + __ldcg(&S->status_base) + (size_t)(chunks - 1) * k;
+    for (uint32_t q = threadIdx.x; q < k; q += BLOCK) out[q] = __ldcg(last + q) & VAL_MASK;
+}
+
 __device__ __noinline__ void lhist_done(const Params &P, uint32_t sid, SmemTile &s)
 {
     const Seg *S = &P.segs[sid];
     const uint32_t k = __ldcg(&S->k), chunks = __ldcg(&S->chunks);
-    for (uint32_t q = threadIdx.x; q < k; q += BLOCK) s.hist[q] = __ldcg(&P.counts[(size_t)sid * NB_MAX + q]);
+    load_bucket_totals(P, S, k, chunks, s.hist);
     __syncthreads();
     block_exclusive_scan(s.hist, s.bs, k, s.wsum);
     for (uint32_t q = threadIdx.x; q < k; q += BLOCK) P.bstart[(size_t)sid * NB_MAX + q] = s.bs[q];
@@ -1475,10 +1522,8 @@ __device__ __noinline__ void lscatter_done(const Params &P, uint32_t sid, SmemTi
     const Seg *S = &P.segs[sid];
     const uint32_t k = __ldcg(&S->k), buf = __ldcg(&S->buf), level = __ldcg(&S->level);
     const unsigned long long off = __ldcg(&S->off);
-    for (uint32_t q = threadIdx.x; q < k; q += BLOCK) {
-        s.hist[q] = __ldcg(&P.counts[(size_t)sid * NB_MAX + q]);
-        s.bs[q] = __ldcg(&P.bstart[(size_t)sid * NB_MAX + q]);
-    }
+    load_bucket_totals(P, S, k, __ldcg(&S->chunks), s.hist);
+    for (uint32_t q = threadIdx.x; q < k; q += BLOCK) s.bs[q] = __ldcg(&P.bstart[(size_t)sid * NB_MAX + q]);
     if (threadIdx.x == 0) {
         atomicAdd(&P.ctl->n_large, 1ull);
         note_level(P, level);
