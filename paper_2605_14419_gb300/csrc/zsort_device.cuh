@@ -383,7 +383,7 @@ __device__ void moments_from_sums(unsigned long long n, unsigned long long mn,
 // One definition serves the histogram and the scatter, so both passes
 // compute bit-identical buckets.  Every map is monotone non-decreasing in
 // the key, which is all the sort's exactness needs.
-constexpr int PWL_BINS = 2048;  // learned map: bins of the normalised key's float bits
+constexpr int PWL_BINS = 4096;  // learned map: bins of the normalised key's float bits
 constexpr int PWL_MLP_OFF = 2 * PWL_P + 1;            // per-segment table: q[0..P], r[0..P), MLP table
 constexpr int PWL_STRIDE = PWL_MLP_OFF + MLP_TABLE;
 struct MapSm {
@@ -392,7 +392,9 @@ struct MapSm {
     float zc, escale;
     float q[PWL_P + 1];          // learned map: breakpoints
     float r[PWL_P];              // learned map: 1 / (q[s+1] - q[s]), 0 for an empty piece
-    uint8_t seg0[PWL_BINS + 1];  // learned map: piece holding the lower edge of each bin
+    uint8_t lo8[PWL_BINS];       // learned map: piece holding the lower edge of each bin
+    uint32_t bin_lo, bin_sh;     // learned map: bin of u = (bits(u) - bin_lo) >> bin_sh, clamped
+    uint32_t steps;              // learned map: 2^steps > most pieces a bin touches, minus one
     float mlp[MLP_TABLE];        // MLP map: w = omega^2, b, a = alpha^2 per unit, f0, inv
 };
 
@@ -410,24 +412,37 @@ __device__ __forceinline__ float u64_to_f32_rn(unsigned long long d)
 }
 
 // Learned map on the normalised key u = fl32(key - min) * 2^-E in [0, 1]:
-// piece s = the last breakpoint q[s] <= u (found from the bin table, then a
-// binary search inside the bin), linear interpolation inside the piece.
-__device__ __forceinline__ uint32_t pwl_bucket_u(const MapSm &m, float u)
+// piece s = the last breakpoint q[s] <= u, linear interpolation inside the
+// piece.  The piece is found from a bin table over the float bits of u
+// (bins spread over [q[1], 1], the range the breakpoints occupy) that gives
+// the piece at the bin's lower edge, then by binary lifting: steps
+// strides 2^(steps-1), ..., 1, each taken if its breakpoint is still <= u
+// (indices clamped to the last piece).  A bin touches at most 2^steps
+// pieces, so the lifting always ends on the piece, with no data-dependent
+// branch: the tile loops interleave the searches of all their keys.
+__device__ __forceinline__ uint32_t pwl_bin(const MapSm &m, float u)
 {
-    const uint32_t c = __float_as_uint(u) >> 19;  // u <= 1.0f: c <= 2032
-    uint32_t lo = m.seg0[c], hi = m.seg0[c + 1];
-    while (lo < hi) {
-        const uint32_t mid = (lo + hi + 1) >> 1;
-        if (m.q[mid] <= u)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
+    const int c = ((int)__float_as_uint(u) - (int)m.bin_lo) >> m.bin_sh;
+    return (uint32_t)min(max(c, 0), PWL_BINS - 1);
+}
+__device__ __forceinline__ uint32_t pwl_lift(const MapSm &m, float u, uint32_t lo, uint32_t st)
+{
+    const uint32_t j = min(lo + st, (uint32_t)PWL_P - 1u);
+    return m.q[j] <= u ? j : lo;
+}
+__device__ __forceinline__ uint32_t pwl_finish(const MapSm &m, float u, uint32_t lo)
+{
     float frac = __fmul_rn(__fsub_rn(u, m.q[lo]), m.r[lo]);
     frac = fminf(fmaxf(frac, 0.0f), 0x1.fffffep-1f);
     uint32_t w = __float2uint_rz(__fmul_rn(frac, (float)m.K));
     w = w < m.K ? w : m.K - 1;
     return lo * m.K + w;
+}
+__device__ __forceinline__ uint32_t pwl_bucket_u(const MapSm &m, float u)
+{
+    uint32_t lo = m.lo8[pwl_bin(m, u)];
+    for (uint32_t st = m.steps ? 1u << (m.steps - 1) : 0u; st; st >>= 1) lo = pwl_lift(m, u, lo, st);
+    return pwl_finish(m, u, lo);
 }
 
 // The scalar part of a map, held in registers by the tile loops (the tables
@@ -511,6 +526,36 @@ __device__ __forceinline__ uint32_t map_key(const MapSm &m, unsigned long long k
     return map_key(map_regs(m), m, key);
 }
 
+// The buckets of NI keys of a tile loop (the MLP map when MLP, else the
+// segment's map).  The learned map runs phase by phase over all NI keys --
+// normalise and look up the bin, each lifting step, interpolate -- so the
+// keys' shared-memory lookups overlap.  Same function as map_key.
+template <int NI, bool MLP>
+__device__ __forceinline__ void map_tile(const MapK &mk, const MapSm &m, const unsigned long long (&x)[NI],
+                                         uint32_t (&b)[NI])
+{
+    if (MLP) {
+#pragma unroll
+        for (int i = 0; i < NI; i++) b[i] = map_key_mlp(mk, m, x[i]);
+    } else if (mk.kind == MAP_PWL) {
+        float u[NI];
+#pragma unroll
+        for (int i = 0; i < NI; i++) {
+            u[i] = __fmul_rn(u64_to_f32_rn(x[i] - mk.mn), mk.escale);
+            b[i] = m.lo8[pwl_bin(m, u[i])];
+        }
+        for (uint32_t st = m.steps ? 1u << (m.steps - 1) : 0u; st; st >>= 1) {
+#pragma unroll
+            for (int i = 0; i < NI; i++) b[i] = pwl_lift(m, u[i], b[i], st);
+        }
+#pragma unroll
+        for (int i = 0; i < NI; i++) b[i] = pwl_finish(m, u[i], b[i]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < NI; i++) b[i] = map_key(mk, m, x[i]);
+    }
+}
+
 // Range map parameters: floor-like (d >> shift) * mult / 2^32, monotone,
 // bucket(0) = 0, bucket(range) >= 1 for k >= 16, never above k - 1.
 __device__ __forceinline__ void range_params(unsigned long long range, uint32_t k, uint32_t *rshift,
@@ -571,7 +616,7 @@ struct SmemTile {
     MapSm map;
     unsigned long long bar[KEY_STAGES];  // mbarriers of the tile buffers / key stages
     uint32_t task[8];
-    uint32_t flag, flag2, n_leaf, n_med, n_large, n_large_ok, item_base, e_base;
+    uint32_t flag, flag2, n_leaf, n_med, n_large, n_large_ok, item_base, e_base, span_max;
     unsigned long long red64[WARPS * 2];
 };
 static_assert(sizeof(LeafBuf) <= sizeof(TileBuf) * 2, "leaf fits the tile buffers");

@@ -278,21 +278,51 @@ __device__ void note_level(const Params &P, uint32_t level)
     atomicMax(&P.ctl->max_level, (unsigned long long)level);
 }
 
-// Bin table of the learned map: seg0[c] = the last piece s whose breakpoint
-// q[s] lies at or below the lower edge of bin c (float bits c << 19).
-__device__ void build_pwl_bins(MapSm &m)
+// Bin table of the learned map (all threads; q[0..P] in place): bins of
+// equal width in the float bits of u between q[1] and 1 (below q[1] every
+// key is in piece 0), lo8[c] = the last piece s whose breakpoint q[s] lies
+// at or below the lower edge of bin c, and the lifting steps for the most
+// pieces one bin touches (its upper edge is the next bin's lower edge, or 1).
+__device__ uint32_t pwl_piece_at(const MapSm &m, float edge)
 {
-    for (uint32_t c = threadIdx.x; c <= (uint32_t)PWL_BINS; c += BLOCK) {
-        const float edge = __uint_as_float(c << 19);
-        uint32_t lo = 0, hi = PWL_P - 1;
-        while (lo < hi) {
-            const uint32_t mid = (lo + hi + 1) >> 1;
-            if (m.q[mid] <= edge)
-                lo = mid;
-            else
-                hi = mid - 1;
-        }
-        m.seg0[c] = (uint8_t)lo;
+    uint32_t lo = 0, hi = PWL_P - 1;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (m.q[mid] <= edge)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+__device__ void build_pwl_bins(MapSm &m, uint32_t *scratch)
+{
+    const uint32_t top = __float_as_uint(1.0f);
+    const uint32_t lo_bits = min(__float_as_uint(m.q[1]), top);
+    uint32_t sh = 0;
+    while (((top - lo_bits) >> sh) >= (uint32_t)PWL_BINS) sh++;
+    if (threadIdx.x == 0) {
+        m.bin_lo = lo_bits;
+        m.bin_sh = sh;
+        *scratch = 0;
+    }
+    __syncthreads();
+    uint32_t span = 0;
+    for (uint32_t c = threadIdx.x; c < (uint32_t)PWL_BINS; c += BLOCK) {
+        const float lo_edge = c == 0 ? 0.0f : __uint_as_float(min(lo_bits + (c << sh), top));
+        const unsigned long long up = (unsigned long long)lo_bits + ((unsigned long long)(c + 1) << sh);
+        const float hi_edge = c + 1 == (uint32_t)PWL_BINS || up >= top ? 1.0f : __uint_as_float((uint32_t)up);
+        const uint32_t a = pwl_piece_at(m, lo_edge);
+        m.lo8[c] = (uint8_t)a;
+        span = max(span, pwl_piece_at(m, hi_edge) - a);
+    }
+    span = __reduce_max_sync(0xffffffffu, span);
+    if ((threadIdx.x & 31) == 0) atomicMax(scratch, span);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t st = 0;
+        while ((1u << st) <= *scratch) st++;
+        m.steps = st;
     }
 }
 
@@ -321,7 +351,7 @@ __device__ void load_seg_map(const Params &P, uint32_t sid, SmemTile &s)
         for (int j = threadIdx.x; j <= PWL_P; j += BLOCK) s.map.q[j] = __ldcg(t + j);
         for (int j = threadIdx.x; j < PWL_P; j += BLOCK) s.map.r[j] = __ldcg(t + PWL_P + 1 + j);
         __syncthreads();
-        build_pwl_bins(s.map);
+        build_pwl_bins(s.map, &s.span_max);
     }
     __syncthreads();
 }
@@ -474,10 +504,17 @@ template <bool MLP>
 __device__ __forceinline__ void body_hist(SmemTile &s, const MapK &mk, uint32_t cnt, const unsigned long long *sk)
 {
     const int lane = threadIdx.x & 31;
+    unsigned long long x[IPT];
+    uint32_t bb[IPT];
 #pragma unroll
     for (int i = 0; i < IPT; i++) {
         const uint32_t p = slot_index(i);
-        const uint32_t b = p >= cnt ? INVALID : (MLP ? map_key_mlp(mk, s.map, sk[p]) : map_key(mk, s.map, sk[p]));
+        x[i] = p < cnt ? sk[p] : mk.mn;
+    }
+    map_tile<IPT, MLP>(mk, s.map, x, bb);
+#pragma unroll
+    for (int i = 0; i < IPT; i++) {
+        const uint32_t b = slot_index(i) >= cnt ? INVALID : bb[i];
         const uint32_t b0 = __shfl_sync(0xffffffffu, b, 0);
         if (__all_sync(0xffffffffu, b == b0)) {
             if (lane == 0 && b0 != INVALID) atomicAdd(&s.hist[b0], 32u);
@@ -553,10 +590,10 @@ __device__ __noinline__ void scatter_stream(const Params &P, SmemTile &s, Pipe &
         for (int i = 0; i < IPT; i++) {
             const uint32_t p = slot_index(i);
             const bool in = p < cnt;
-            x[i] = in ? sk[p] : 0ull;
+            x[i] = in ? sk[p] : mk.mn;
             v[i] = in && kv ? sv[p] : 0u;
-            b[i] = !in ? 0u : (MLP ? map_key_mlp(mk, s.map, x[i]) : map_key(mk, s.map, x[i]));
         }
+        map_tile<IPT, MLP>(mk, s.map, x, b);  // lanes past cnt: ignored by the ranking
         rank_peers<IPT, NBITS>(b, cnt, peers);
         rank_leaders<IPT>(b, peers, pos, s);
         // every thread has left the previous tile: its buffer may be refilled
@@ -1316,7 +1353,7 @@ __device__ __noinline__ void task_lfit(const Params &P, uint32_t sid, SmemTile &
         s.map.r[j] = r;
         t[PWL_P + 1 + j] = r;
     }
-    build_pwl_bins(s.map);
+    build_pwl_bins(s.map, &s.span_max);
     __syncthreads();
     const bool mlp = P.mapper == 2;
     if (mlp) mlp_train(s, t + PWL_MLP_OFF);  // the MLP map replaces the piecewise-linear one
