@@ -198,7 +198,8 @@ __global__ void k_init_segments(Params P, const uint64_t *off, unsigned long lon
             S->kind = MAP_Z;
             S->range_map = 0;
             S->train_slot = take_train_slot(P, (uint32_t)len, kk, 0);
-            S->join = SAMPLE_RUNS + 1;
+            S->join = 2;
+            S->runs_left = SAMPLE_RUNS;
             S->max_learned = S->max_z = 0;
             return;
         }

@@ -79,7 +79,8 @@ struct Seg {
     uint32_t max_learned, max_z; // load test: largest sample bucket per map
     uint32_t chunk_tiles;        // tiles per chunk task
     uint32_t chunks;             // chunk tasks per phase
-    uint32_t join;               // learned map: statistics + sample runs still running
+    uint32_t join;               // learned map: statistics + sample selection still running
+    uint32_t runs_left;          // learned map: sample runs not yet sorted
     uint32_t next_type, next_nt; // learned map: the task the last of the two publishes
     uint32_t range_map;          // the parent's partition left it more than half: exact range map
 };

@@ -831,7 +831,8 @@ __device__ __noinline__ void classify_children(const Params &P, unsigned long lo
         S->range_map = 2ull * len > plen;
         const uint32_t slot = S->range_map ? INVALID : take_train_slot(P, len, S->k, child_level);
         S->train_slot = slot;
-        S->join = SAMPLE_RUNS + 1;
+        S->join = 2;
+        S->runs_left = SAMPLE_RUNS;
         S->max_learned = S->max_z = 0;
         L.lg_slot[g] = slot;
     }
@@ -1088,68 +1089,6 @@ __device__ uint32_t cta_lsd_sort64(unsigned long long *A, unsigned long long *B,
     return sel;
 }
 
-// Learned map, first half (beside the statistics tiles): run `run` of the
-// sample, i.e. sample indices [run * m / R, (run + 1) * m / R) at the
-// stratified positions, drawn and sorted exactly by one CTA (in place in
-// buffer A of the slot).  The keys are sorted as they are: the
-// normalisation u = fl32(key - min) * 2^-E is monotone, so the sorted keys
-// give the sorted normalised sample once min and max are known.
-__device__ __noinline__ void task_lsample(const Params &P, uint32_t sid, uint32_t run, SmemTile &s)
-{
-    Seg *S = &P.segs[sid];
-    const unsigned long long off = __ldcg(&S->off);
-    const uint32_t len = __ldcg(&S->len), buf = __ldcg(&S->buf), slot = __ldcg(&S->train_slot);
-    const uint32_t m = P.sample;
-    const uint32_t lo = (uint32_t)((unsigned long long)run * m / SAMPLE_RUNS);
-    const uint32_t hi = (uint32_t)((unsigned long long)(run + 1) * m / SAMPLE_RUNS);
-    const uint32_t mr = hi - lo;
-    unsigned long long *A = P.trainbuf + (size_t)slot * 2 * SAMPLE_MAX + lo;
-    unsigned long long *B = A + SAMPLE_MAX;
-    const uint64_t *src = keys_of(P, buf) + off;
-    unsigned long long mn = ~0ull, mx = 0ull;
-    constexpr int U = 8;  // independent loads in flight per thread
-    for (uint32_t i0 = 0; i0 < mr; i0 += BLOCK * U) {
-        unsigned long long x[U];
-#pragma unroll
-        for (int u = 0; u < U; u++) {
-            const uint32_t i = i0 + threadIdx.x + u * BLOCK;
-            x[u] = i < mr ? __ldcg(src + sample_pos(P.seed, len, m, lo + i)) : 0ull;
-        }
-#pragma unroll
-        for (int u = 0; u < U; u++) {
-            const uint32_t i = i0 + threadIdx.x + u * BLOCK;
-            if (i < mr) {
-                __stcg(A + i, x[u]);
-                mn = x[u] < mn ? x[u] : mn;
-                mx = x[u] > mx ? x[u] : mx;
-            }
-        }
-    }
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-        const unsigned long long a = shfl_down64(mn, o), b2 = shfl_down64(mx, o);
-        mn = a < mn ? a : mn;
-        mx = b2 > mx ? b2 : mx;
-    }
-    if ((threadIdx.x & 31) == 0) {
-        s.red64[threadIdx.x >> 5] = mn;
-        s.red64[WARPS + (threadIdx.x >> 5)] = mx;
-    }
-    __syncthreads();
-    mn = s.red64[0];
-    mx = s.red64[WARPS];
-    for (int w = 1; w < WARPS; w++) {
-        mn = s.red64[w] < mn ? s.red64[w] : mn;
-        mx = s.red64[WARPS + w] > mx ? s.red64[WARPS + w] : mx;
-    }
-    __syncthreads();
-    if (mr > 0 && cta_lsd_sort64(A, B, mr, mn, (bitlen64(mx - mn) + 7) / 8, s))
-        for (uint32_t i = threadIdx.x; i < mr; i += BLOCK) __stcg(A + i, __ldcg(B + i));
-    __threadfence();  // the sorted run before the join publishes the fit
-    __syncthreads();
-    if (threadIdx.x == 0) learned_join(P, sid);
-}
-
 // The r-th smallest (0-based) of the sample held as SAMPLE_RUNS sorted runs
 // in X: the smallest value v with at least r + 1 sample keys <= v, by a
 // binary search over values between the sample's min and max.  Each run
@@ -1211,6 +1150,81 @@ __device__ unsigned long long sample_select(const unsigned long long *X, uint32_
         }
     }
     return lo;
+}
+
+// Learned map, first half (beside the statistics tiles): run `run` of the
+// sample, i.e. sample indices [run * m / R, (run + 1) * m / R) at the
+// stratified positions, drawn and sorted exactly by one CTA (in place in
+// buffer A of the slot).  The keys are sorted as they are: the
+// normalisation u = fl32(key - min) * 2^-E is monotone, so the sorted keys
+// give the sorted normalised sample once min and max are known.
+__device__ __noinline__ void task_lsample(const Params &P, uint32_t sid, uint32_t run, SmemTile &s)
+{
+    Seg *S = &P.segs[sid];
+    const unsigned long long off = __ldcg(&S->off);
+    const uint32_t len = __ldcg(&S->len), buf = __ldcg(&S->buf), slot = __ldcg(&S->train_slot);
+    const uint32_t m = P.sample;
+    const uint32_t lo = (uint32_t)((unsigned long long)run * m / SAMPLE_RUNS);
+    const uint32_t hi = (uint32_t)((unsigned long long)(run + 1) * m / SAMPLE_RUNS);
+    const uint32_t mr = hi - lo;
+    unsigned long long *A = P.trainbuf + (size_t)slot * 2 * SAMPLE_MAX + lo;
+    unsigned long long *B = A + SAMPLE_MAX;
+    const uint64_t *src = keys_of(P, buf) + off;
+    unsigned long long mn = ~0ull, mx = 0ull;
+    constexpr int U = 8;  // independent loads in flight per thread
+    for (uint32_t i0 = 0; i0 < mr; i0 += BLOCK * U) {
+        unsigned long long x[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const uint32_t i = i0 + threadIdx.x + u * BLOCK;
+            x[u] = i < mr ? __ldcg(src + sample_pos(P.seed, len, m, lo + i)) : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const uint32_t i = i0 + threadIdx.x + u * BLOCK;
+            if (i < mr) {
+                __stcg(A + i, x[u]);
+                mn = x[u] < mn ? x[u] : mn;
+                mx = x[u] > mx ? x[u] : mx;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const unsigned long long a = shfl_down64(mn, o), b2 = shfl_down64(mx, o);
+        mn = a < mn ? a : mn;
+        mx = b2 > mx ? b2 : mx;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        s.red64[threadIdx.x >> 5] = mn;
+        s.red64[WARPS + (threadIdx.x >> 5)] = mx;
+    }
+    __syncthreads();
+    mn = s.red64[0];
+    mx = s.red64[WARPS];
+    for (int w = 1; w < WARPS; w++) {
+        mn = s.red64[w] < mn ? s.red64[w] : mn;
+        mx = s.red64[WARPS + w] > mx ? s.red64[WARPS + w] : mx;
+    }
+    __syncthreads();
+    if (mr > 0 && cta_lsd_sort64(A, B, mr, mn, (bitlen64(mx - mn) + 7) / 8, s))
+        for (uint32_t i = threadIdx.x; i < mr; i += BLOCK) __stcg(A + i, __ldcg(B + i));
+    __threadfence();  // the sorted run before the last run's selection reads it
+    __syncthreads();
+    if (threadIdx.x == 0) s.flag = atomicSub(&S->runs_left, 1u) == 1u ? 1u : 0u;
+    __syncthreads();
+    if (!s.flag) return;
+    // the last run to finish selects the breakpoint keys from all runs (it
+    // needs no statistics, so it runs beside the statistics pass): key of
+    // rank floor(j m / P) for j = 1..P-1, into the free half of the buffer
+    __threadfence();
+    const unsigned long long *X = P.trainbuf + (size_t)slot * 2 * SAMPLE_MAX;
+    unsigned long long *sel = P.trainbuf + (size_t)slot * 2 * SAMPLE_MAX + SAMPLE_MAX;
+    for (int j = 1 + threadIdx.x; j < PWL_P; j += BLOCK)
+        __stcg(sel + j, sample_select(X, m, (uint32_t)((size_t)j * m / PWL_P)));
+    __threadfence();  // the selected keys before the join publishes the fit
+    __syncthreads();
+    if (threadIdx.x == 0) learned_join(P, sid);
 }
 
 // MLP map training state (aliases the tile buffers during the fit).
@@ -1338,7 +1352,7 @@ __device__ __noinline__ void task_lfit(const Params &P, uint32_t sid, SmemTile &
         else if (j == PWL_P)
             q = __fmul_rn(u64_to_f32_rn(mx - mn), escale);
         else
-            q = __fmul_rn(u64_to_f32_rn(sample_select(X, m, (uint32_t)((size_t)j * m / PWL_P)) - mn), escale);
+            q = __fmul_rn(u64_to_f32_rn(__ldcg(X + SAMPLE_MAX + j) - mn), escale);  // selected by the last run
         s.map.q[j] = q;
         t[j] = q;
     }
