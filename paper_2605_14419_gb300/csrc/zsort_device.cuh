@@ -236,24 +236,6 @@ struct Acc {
     unsigned long long s2hi;
 };
 
-__device__ __forceinline__ void acc_init(Acc &a)
-{
-    a.mn = ~0ull;
-    a.mx = 0ull;
-    a.s1 = 0;
-    a.s2lo = 0;
-    a.s2hi = 0;
-}
-__device__ __forceinline__ void acc_key(Acc &a, unsigned long long x)
-{
-    a.mn = x < a.mn ? x : a.mn;
-    a.mx = x > a.mx ? x : a.mx;
-    a.s1 += x;
-    unsigned __int128 sq = (unsigned __int128)x * x;
-    unsigned __int128 t = a.s2lo + sq;
-    a.s2hi += (t < sq) ? 1ull : 0ull;
-    a.s2lo = t;
-}
 __device__ __forceinline__ void acc_merge(Acc &a, const Acc &b)
 {
     a.mn = b.mn < a.mn ? b.mn : a.mn;
@@ -262,6 +244,65 @@ __device__ __forceinline__ void acc_merge(Acc &a, const Acc &b)
     unsigned __int128 t = a.s2lo + b.s2lo;
     a.s2hi += b.s2hi + ((t < b.s2lo) ? 1ull : 0ull);
     a.s2lo = t;
+}
+// The per-thread form of the streamed sums, in 32-bit pieces: with x = h 2^32
+// + l, S1 = 2^32 sum h + sum l and S2 = 2^64 sum h^2 + 2^33 sum h l +
+// sum l^2.  Each product is one 32 x 32 -> 64-bit multiply, added into a
+// 96-bit sum by one carry chain (no 128-bit multiply or compare per key).
+// A thread adds at most 2^30 keys, so no sum overflows its width.
+struct LAcc {
+    unsigned long long mn, mx;
+    unsigned long long sl, sh;       // sum l, sum h
+    uint32_t a0, a1, a2;             // sum l^2
+    uint32_t b0, b1, b2;             // sum h l
+    uint32_t c0, c1, c2;             // sum h^2
+};
+__device__ __forceinline__ void lacc_init(LAcc &a)
+{
+    a.mn = ~0ull;
+    a.mx = 0ull;
+    a.sl = a.sh = 0ull;
+    a.a0 = a.a1 = a.a2 = a.b0 = a.b1 = a.b2 = a.c0 = a.c1 = a.c2 = 0u;
+}
+__device__ __forceinline__ void add96(uint32_t &x0, uint32_t &x1, uint32_t &x2, unsigned long long p)
+{
+    asm("add.cc.u32 %0, %0, %3;\n\taddc.cc.u32 %1, %1, %4;\n\taddc.u32 %2, %2, 0;"
+        : "+r"(x0), "+r"(x1), "+r"(x2)
+        : "r"((uint32_t)p), "r"((uint32_t)(p >> 32)));
+}
+__device__ __forceinline__ void lacc_key(LAcc &a, unsigned long long x)
+{
+    a.mn = x < a.mn ? x : a.mn;
+    a.mx = x > a.mx ? x : a.mx;
+    const uint32_t l = (uint32_t)x, h = (uint32_t)(x >> 32);
+    a.sl += l;
+    a.sh += h;
+    add96(a.a0, a.a1, a.a2, (unsigned long long)l * l);
+    add96(a.b0, a.b1, a.b2, (unsigned long long)h * l);
+    add96(a.c0, a.c1, a.c2, (unsigned long long)h * h);
+}
+// The canonical sums of a piecewise accumulator.
+__device__ __forceinline__ Acc lacc_sums(const LAcc &a)
+{
+    Acc r;
+    r.mn = a.mn;
+    r.mx = a.mx;
+    r.s1 = ((unsigned __int128)a.sh << 32) + a.sl;
+    const unsigned __int128 A = ((unsigned __int128)a.a2 << 64) | ((unsigned long long)a.a1 << 32) | a.a0;
+    const unsigned __int128 B = ((unsigned __int128)a.b2 << 64) | ((unsigned long long)a.b1 << 32) | a.b0;
+    const unsigned __int128 C = ((unsigned __int128)a.c2 << 64) | ((unsigned long long)a.c1 << 32) | a.c0;
+    unsigned __int128 lo = A;
+    unsigned long long hi = 0;
+    unsigned __int128 t = B << 33;  // 2^33 B: low 128 bits, then the bits above
+    unsigned __int128 u = lo + t;
+    hi += (unsigned long long)(B >> 95) + (u < t ? 1ull : 0ull);
+    lo = u;
+    t = C << 64;  // 2^64 C
+    u = lo + t;
+    hi += (unsigned long long)(C >> 64) + (u < t ? 1ull : 0ull);
+    r.s2lo = u;
+    r.s2hi = hi;
+    return r;
 }
 __device__ __forceinline__ unsigned long long shfl_down64(unsigned long long v, int o)
 {

@@ -487,14 +487,14 @@ __device__ __forceinline__ uint32_t leaf_slot(int i)
 
 // ------------------------------------------------------------ tile bodies
 // Exact sums of the tile's keys into a per-thread accumulator.
-__device__ __forceinline__ void body_stats(Acc &a, Acc &b, uint32_t cnt, const unsigned long long *sk)
+__device__ __forceinline__ void body_stats(LAcc &a, LAcc &b, uint32_t cnt, const unsigned long long *sk)
 {
     // two accumulators: the even and the odd slots form independent chains
 #pragma unroll
     for (int i = 0; i < IPT; i += 2) {
         const uint32_t p = slot_index(i), p1 = slot_index(i + 1);
-        if (p < cnt) acc_key(a, sk[p]);
-        if (p1 < cnt) acc_key(b, sk[p1]);
+        if (p < cnt) lacc_key(a, sk[p]);
+        if (p1 < cnt) lacc_key(b, sk[p1]);
     }
 }
 
@@ -908,13 +908,14 @@ __device__ __noinline__ void task_lstats(const Params &P, uint32_t sid, uint32_t
     // this chunk's look-back row must read zero before the histogram phase
     uint32_t *row = P.status + ch.sbase + (size_t)c * ch.k;
     for (uint32_t q = threadIdx.x; q < ch.k; q += BLOCK) __stcg(row + q, 0u);
-    Acc a, a2;
-    acc_init(a);
-    acc_init(a2);
+    LAcc la, la2;
+    lacc_init(la);
+    lacc_init(la2);
     const uint64_t *src = keys_of(P, ch.buf);
     stream_tiles<false>(P, s, pp, src, nullptr, bulk_ok(P, ch.buf), ch.start, ch.len,
-                        [&](uint32_t, uint32_t cnt, unsigned long long *sk, uint32_t *) { body_stats(a, a2, cnt, sk); });
-    acc_merge(a, a2);
+                        [&](uint32_t, uint32_t cnt, unsigned long long *sk, uint32_t *) { body_stats(la, la2, cnt, sk); });
+    Acc a = lacc_sums(la);
+    acc_merge(a, lacc_sums(la2));
     acc_block_reduce(a, s.acc);
     if (threadIdx.x == 0) {
         Seg *W = &P.segs[sid];
@@ -1594,12 +1595,13 @@ __device__ __noinline__ void task_mpart(const Params &P, const Item it, SmemTile
     const uint64_t *srck = keys_of(P, buf);
     const uint32_t *srcv = vals_of(P, buf);
     const bool bulk = bulk_ok(P, buf);
-    Acc a, a2;
-    acc_init(a);
-    acc_init(a2);
+    LAcc la, la2;
+    lacc_init(la);
+    lacc_init(la2);
     stream_tiles<false>(P, s, pp, srck, nullptr, bulk, off, len,
-                        [&](uint32_t, uint32_t cnt, unsigned long long *sk, uint32_t *) { body_stats(a, a2, cnt, sk); });
-    acc_merge(a, a2);
+                        [&](uint32_t, uint32_t cnt, unsigned long long *sk, uint32_t *) { body_stats(la, la2, cnt, sk); });
+    Acc a = lacc_sums(la);
+    acc_merge(a, lacc_sums(la2));
     acc_block_reduce(a, s.acc);
     if (threadIdx.x == 0) {
         if (a.mn == a.mx) {

@@ -216,7 +216,14 @@ def test_learned_map_buckets_bit_exact(gen):
                 or info.learned_max_load > info.zscore_max_load)
 
 
-@pytest.mark.parametrize("gen", [inputs.uniform, inputs.normal, inputs.lognormal, inputs.nearly_sorted])
+def _top_keys(n, seed):
+    """Keys just below 2^64 with both 32-bit halves large: every limb of the
+    exact sums carries."""
+    rng = np.random.default_rng(seed)
+    return (np.uint64(2**64 - 1) - rng.integers(0, 2**40, n, dtype=np.uint64)).astype(np.uint64)
+
+
+@pytest.mark.parametrize("gen", [inputs.uniform, inputs.normal, inputs.lognormal, inputs.nearly_sorted, _top_keys])
 def test_zscore_map_and_stats(gen):
     """Eq. 1 map on the device: exact statistics match the oracle's FP64
     loops (relative 1e-12), the map is monotone, covers [min, min + 4 sd)
