@@ -529,13 +529,33 @@ def main():
         ok_v = [torch.empty(n, dtype=torch.int32, pin_memory=True) for _ in pristine]
         torch.cuda.synchronize()
 
+        # the copies run on their own streams, one per direction, so that one
+        # array's transfers overlap the other's sort and the two directions
+        # overlap each other; a device buffer is refilled once its result has
+        # been read back
+        h2d_s = torch.cuda.Stream(device=dev)
+        d2h_s = torch.cuda.Stream(device=dev)
+        free = [torch.cuda.Event() for _ in bufs]
+        for ev in free:
+            ev.record(d2h_s)
+
         def e2e_step():
             for i, (kb, vb) in enumerate(bufs):
-                kb.copy_(hk[i], non_blocking=True)
-                vb.copy_(hv[i], non_blocking=True)
-                z.sort_pairs(kb, vb, opts=opts, check=False)
-                ok_k[i].copy_(kb, non_blocking=True)
-                ok_v[i].copy_(vb, non_blocking=True)
+                h2d_s.wait_event(free[i])
+                with torch.cuda.stream(h2d_s):
+                    kb.copy_(hk[i], non_blocking=True)
+                    vb.copy_(hv[i], non_blocking=True)
+                arrived = torch.cuda.Event()
+                arrived.record(h2d_s)
+                stream.wait_event(arrived)
+                z.sort_pairs(kb, vb, opts=opts, stream=stream, check=False)
+                sorted_ev = torch.cuda.Event()
+                sorted_ev.record(stream)
+                d2h_s.wait_event(sorted_ev)
+                with torch.cuda.stream(d2h_s):
+                    ok_k[i].copy_(kb, non_blocking=True)
+                    ok_v[i].copy_(vb, non_blocking=True)
+                free[i].record(d2h_s)
 
         for _ in range(2):
             e2e_step()
@@ -544,13 +564,22 @@ def main():
         e1 = torch.cuda.Event(enable_timing=True)
         e_steps = max(3, args.steps // 2)
         e0.record(stream)
+        h2d_s.wait_event(e0)
+        d2h_s.wait_event(e0)
         for _ in range(e_steps):
             e2e_step()
+        for ev in free:  # every result is back on the host
+            stream.wait_event(ev)
         e1.record(stream)
         torch.cuda.synchronize()
         rc = z.sync_status(stream)
         if rc != 0:
             raise z.ZsortError(rc, "bench e2e")
+        for i, (name, kd, _) in enumerate(pristine):  # the host copies hold the sorted result
+            hk_sorted = ok_k[i].numpy().view(np.uint64)
+            assert bool(np.all(hk_sorted[1:] >= hk_sorted[:-1])), f"e2e {name}: not sorted"
+            head = ok_v[i][:4096].to(dev).to(torch.int64) & 0xFFFFFFFF
+            assert bool(torch.equal(kd[head], ok_k[i][:4096].to(dev))), f"e2e {name}: payload does not follow its key"
         ems = replicas.max_over_ranks(e0.elapsed_time(e1), dev)  # the slowest rank
         e2e = {"value": world * pairs_per_step * e_steps / (ems / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": pairs_per_step * BYTES_PER_PAIR,

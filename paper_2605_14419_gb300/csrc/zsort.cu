@@ -174,8 +174,8 @@ __global__ void k_init_segments(Params P, const uint64_t *off, unsigned long lon
     if (len > P.large_min || P.plan_out) {
         const uint32_t kk = choose_k(P, (uint32_t)len);
         const uint32_t tiles = (uint32_t)((len + TILE - 1) / TILE);
-        const uint32_t ct = choose_chunk_tiles(P, tiles, (uint32_t)len);
-        const uint32_t chunks = (tiles + ct - 1) / ct;
+        const ChunkPlan cp = chunk_plan(P, tiles, (uint32_t)len);
+        const uint32_t chunks = cp.chunks;
         const unsigned long long need = 2ull * chunks * kk;
         const uint32_t sid = atomicAdd(&C->seg_alloc, 1u);
         unsigned long long sb = ~0ull;
@@ -191,7 +191,9 @@ __global__ void k_init_segments(Params P, const uint64_t *off, unsigned long lon
             S->len = (uint32_t)len;
             S->k = kk;
             S->tiles = tiles;
-            S->chunk_tiles = ct;
+            S->chunk_tiles = cp.ct;
+            S->chunk_tiles_small = cp.ct_small;
+            S->chunks_big = cp.big;
             S->chunks = chunks;
             S->level = 0;
             S->buf = 0;

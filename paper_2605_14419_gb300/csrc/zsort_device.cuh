@@ -77,8 +77,10 @@ struct Seg {
     uint32_t rshift, rmult;      // range map
     uint32_t train_slot;         // learned map training buffer, INVALID if none
     uint32_t max_learned, max_z; // load test: largest sample bucket per map
-    uint32_t chunk_tiles;        // tiles per chunk task
+    uint32_t chunk_tiles;        // tiles per chunk task (the first chunks_big chunks)
     uint32_t chunks;             // chunk tasks per phase
+    uint32_t chunks_big;         // chunks of chunk_tiles tiles; the rest have chunk_tiles_small
+    uint32_t chunk_tiles_small;
     uint32_t join;               // learned map: statistics + sample selection still running
     uint32_t runs_left;          // learned map: sample runs not yet sorted
     uint32_t next_type, next_nt; // learned map: the task the last of the two publishes
@@ -621,7 +623,7 @@ struct ChildList {
     uint32_t leaf_off[NB_MAX], leaf_len[NB_MAX];
     uint32_t med_off[NB_MAX], med_len[NB_MAX];
     uint32_t lg_off[NB_MAX], lg_len[NB_MAX], lg_need[NB_MAX], lg_slot[NB_MAX];
-    uint32_t lg_ct[NB_MAX], lg_chunks[NB_MAX], lg_k[NB_MAX];  // chunk tiles, chunks, buckets
+    uint32_t lg_chunks[NB_MAX], lg_k[NB_MAX];  // chunks, buckets
 };
 
 struct TileBuf {

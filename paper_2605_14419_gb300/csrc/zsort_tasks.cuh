@@ -228,6 +228,33 @@ __device__ __forceinline__ uint32_t choose_chunk_tiles(const Params &P, uint32_t
     return ct < 4u ? 4u : ct;
 }
 
+// Chunk geometry of a large (sub)array of `tiles` tiles: chunks of ct tiles,
+// except that a (sub)array spanning more than two rounds of chunks over the
+// grid has its last round's worth of tiles (nctas x ct) cut into chunks of
+// a quarter of that size, so that its phases end with short tasks and the
+// CTAs finish them close together.
+struct ChunkPlan {
+    uint32_t ct, ct_small, big, chunks;
+};
+__device__ __forceinline__ ChunkPlan chunk_plan(const Params &P, uint32_t tiles, uint32_t len)
+{
+    ChunkPlan c;
+    c.ct = choose_chunk_tiles(P, tiles, len);
+    const uint32_t whole = (tiles + c.ct - 1) / c.ct;
+    c.ct_small = c.ct;
+    c.big = whole;
+    c.chunks = whole;
+    const uint32_t small = max(4u, c.ct / 4u);
+    if (whole > 2u * P.nctas && small < c.ct) {
+        const uint32_t tail = P.nctas * c.ct;  // below tiles, as whole > 2 nctas
+        c.big = (tiles - tail) / c.ct;
+        const uint32_t rest = tiles - c.big * c.ct;
+        c.ct_small = small;
+        c.chunks = c.big + (rest + small - 1) / small;
+    }
+    return c;
+}
+
 // Fills the map for a (sub)array from its exact sums: Eq. 1 (z-score) unless
 // the depth reached the guard level or the parent's partition made poor
 // progress (force_range), in which cases the exact range map.
@@ -748,10 +775,8 @@ __device__ __noinline__ void classify_children(const Params &P, unsigned long lo
     for (uint32_t g = threadIdx.x; g < ng; g += BLOCK) {
         const uint32_t len = L.lg_len[g];
         const uint32_t tiles = (len + TILE - 1) / TILE;
-        const uint32_t ct = choose_chunk_tiles(P, tiles, len);
-        const uint32_t chunks = (tiles + ct - 1) / ct;
+        const uint32_t chunks = chunk_plan(P, tiles, len).chunks;
         const uint32_t kk = choose_k(P, len);
-        L.lg_ct[g] = ct;
         L.lg_chunks[g] = chunks;
         L.lg_k[g] = kk;
         L.lg_need[g] = 2u * chunks * kk;
@@ -823,8 +848,11 @@ __device__ __noinline__ void classify_children(const Params &P, unsigned long lo
         S->len = len;
         S->k = L.lg_k[g];
         S->tiles = (len + TILE - 1) / TILE;
-        S->chunk_tiles = L.lg_ct[g];
-        S->chunks = L.lg_chunks[g];
+        const ChunkPlan cp = chunk_plan(P, S->tiles, len);
+        S->chunk_tiles = cp.ct;
+        S->chunk_tiles_small = cp.ct_small;
+        S->chunks_big = cp.big;
+        S->chunks = cp.chunks;
         S->level = child_level;
         S->buf = child_buf;
         S->kind = MAP_Z;
@@ -894,8 +922,13 @@ __device__ __forceinline__ Chunk chunk_of(const Params &P, uint32_t sid, uint32_
     ch.k = __ldcg(&S->k);
     ch.chunks = __ldcg(&S->chunks);
     ch.sbase = __ldcg(&S->status_base);
-    const unsigned long long span = (unsigned long long)__ldcg(&S->chunk_tiles) * TILE;
-    const unsigned long long rel = (unsigned long long)c * span;
+    const unsigned long long big_span = (unsigned long long)__ldcg(&S->chunk_tiles) * TILE;
+    const uint32_t big = __ldcg(&S->chunks_big);
+    unsigned long long span = big_span, rel = (unsigned long long)c * big_span;
+    if (c >= big) {  // the short chunks at the end
+        span = (unsigned long long)__ldcg(&S->chunk_tiles_small) * TILE;
+        rel = (unsigned long long)big * big_span + (unsigned long long)(c - big) * span;
+    }
     ch.start = ch.off + rel;
     ch.len = min(span, (unsigned long long)ch.seglen - rel);
     return ch;

@@ -92,3 +92,46 @@ def test_untraced_call_reports_no_trace():
     assert count > 0
     _, rec, count = sort_traced(keys, vals, z.default_opts())
     assert count == 0 and rec.size == 0
+
+
+def _chunk_plan(n, ln, cpc, nctas, tile=2048):
+    """The chunk geometry of a large (sub)array: chunks of ct tiles, the last
+    round's worth of tiles in chunks of a quarter of that size."""
+    tiles = (ln + tile - 1) // tile
+    target = max(1, (cpc * nctas * ln + n - 1) // n)
+    ct = max(4, (tiles + target - 1) // target)
+    whole = (tiles + ct - 1) // ct
+    small = max(4, ct // 4)
+    if whole > 2 * nctas and small < ct:
+        big = (tiles - nctas * ct) // ct
+        return big + (tiles - big * ct + small - 1) // small
+    return whole
+
+
+@gpu
+@needs_cuda
+@pytest.mark.parametrize("cpc", [3, 8])
+def test_short_chunks_end_the_top_level_phases(cpc):
+    """A top-level array spanning several rounds of chunks ends each phase
+    with short chunks; the result stays the stable sort (duplicate-heavy keys,
+    checked by properties at 2^24) and the trace shows the planned count."""
+    n = 1 << 24
+    keys = inputs.zipf(n, 29)
+    dev = torch.device("cuda:0")
+    k_in = torch.from_numpy(keys.view(np.int64)).to(dev)
+    k = k_in.clone()
+    v = torch.arange(n, dtype=torch.int32, device=dev)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        z.sort_pairs(k, v, opts=z.default_opts(chunks_per_cta=cpc, flags=z.FLAG_TRACE), stream=stream)
+        st = z.last_stats(stream)
+        rec, count = z.last_trace(stream)
+    pos = v.to(torch.int64) & 0xFFFFFFFF
+    assert bool(torch.equal(k_in[pos], k))
+    assert bool((torch.bincount(pos, minlength=n) == 1).all())
+    s = k ^ torch.tensor(-(2 ** 63), dtype=torch.int64, device=dev)
+    assert bool((s[1:] >= s[:-1]).all())
+    eq = s[1:] == s[:-1]
+    assert bool((pos[1:][eq] > pos[:-1][eq]).all())
+    top = (rec["level"] == 0) & (rec["type"] == 4)
+    assert int(rec["count"][top].sum()) == _chunk_plan(n, n, cpc, st["persistent_ctas"])
