@@ -64,10 +64,11 @@ __global__ void __launch_bounds__(BLOCK, 2) k_persistent(const __grid_constant__
     Pipe pp;
     for (int w = 0; w < KEY_STAGES; w++) pp.uses[w] = 0;
     unsigned long long t_idle0 = 0, t_task0 = 0, t_task1 = 0;
+    const uint32_t ep = threadIdx.x < 32 ? call_epoch(P) : 0u;  // this call's queue epoch (set before launch)
     for (;;) {
         if (threadIdx.x < 32) {  // warp 0 finds the next work
             t_idle0 = globaltimer();
-            dequeue(P, s.task);
+            dequeue(P, ep, s.task);
             t_task0 = globaltimer();
             if (threadIdx.x == 0) {
                 atomicAdd(&P.ctl->idle_ns, t_task0 - t_idle0);

@@ -68,32 +68,39 @@ __device__ void q_release_all(const Params &P, uint32_t e, uint32_t count)
 }
 
 // Warp 0 of a CTA (all 32 lanes): claims the next tiles of a published entry,
-// partition queue first, else the leaf queue.  The lanes look at 32 entries
-// from the queue head at once: lane i reads entry head + i's ready word and
-// claim counter, the first entry with tiles left is claimed with one atomic,
-// and the head jumps over the leading run of published entries whose tiles
-// are all claimed (one compare-and-swap).  Lane 0 writes out = {type, arg,
-// first tile, entry, ntiles, count}; type T_NONE when all work is done or an
-// error was recorded.  A wait without any progress anywhere for longer than
-// P.wait_ns records ST_TIMEOUT.
-__device__ void dequeue(const Params &P, uint32_t *out)
+// partition queue first, else the leaf queue.  One round trip reads the
+// error word and every queue's head (one lane each); then the lanes look at
+// 32 entries from a queue's head at once: lane i reads entry head + i's
+// ready word (against this call's epoch `ep`) and claim counter, the first
+// entry with tiles left is claimed with one atomic, and the head jumps over
+// the leading run of published entries whose tiles are all claimed (one
+// compare-and-swap).  Lane 0 writes out = {type, arg, first tile, entry,
+// ntiles, count}; type T_NONE when all work is done or an error was
+// recorded.  A wait without any progress anywhere for longer than P.wait_ns
+// records ST_TIMEOUT.
+__device__ void dequeue(const Params &P, uint32_t ep, uint32_t *out)
 {
     const uint32_t full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     Ctl *C = P.ctl;
-    unsigned long long last = ld_relaxed64(&C->progress);
-    unsigned long long t0 = globaltimer();
-    const uint32_t ep = call_epoch(P);
+    const uint32_t qcap = P.qcap, nctas = P.nctas;
+    unsigned long long last = 0, t0 = 0;
+    bool waited = false;
     if (lane == 0) out[0] = T_NONE;
     for (;;) {
-        if (__shfl_sync(full, lane == 0 ? ld_relaxed(&C->error) : 0u, 0)) return;
+        uint32_t w = 0;
+        if (lane == 0)
+            w = ld_relaxed(&C->error);
+        else if (lane <= QUEUES)
+            w = ld_relaxed(&C->q_head[lane - 1]);
+        if (__shfl_sync(full, w, 0)) return;
         for (uint32_t q = 0; q < (uint32_t)QUEUES; q++) {
-            const uint32_t h = __shfl_sync(full, lane == 0 ? ld_relaxed(&C->q_head[q]) : 0u, 0);
+            const uint32_t h = __shfl_sync(full, w, (int)q + 1);
             uint32_t next_head = h;
-            for (uint32_t base = h; base < P.qcap; base += 32) {
+            for (uint32_t base = h; base < qcap; base += 32) {
                 const uint32_t i = base + lane;
-                const uint32_t e = q * P.qcap + i;
-                const bool rdy = i < P.qcap && ld_acquire(&P.ready[e]) == ep;
+                const uint32_t e = q * qcap + i;
+                const bool rdy = i < qcap && ld_acquire(&P.ready[e]) == ep;
                 uint32_t type = 0, arg = 0, nt = 0, tn = 0;
                 if (rdy) {
                     const uint4 en = __ldcg(reinterpret_cast<const uint4 *>(P.entries + e));
@@ -108,9 +115,17 @@ __device__ void dequeue(const Params &P, uint32_t *out)
                     const int f = __ffs(m) - 1;
                     uint32_t got = 0;
                     if (lane == f) {
-                        // leaves are claimed a few at a time, so that each can
-                        // be prefetched while its predecessor is sorted
-                        const uint32_t claim = type != T_FINISH ? 1u : (nt >= 64u ? 4u : (nt >= 16u ? 2u : 1u));
+                        // leaves a few at a time, so that each can be
+                        // prefetched while its predecessor is sorted; the
+                        // statistics and scatter chunks (which wait on no
+                        // other chunk) two at a time while many remain.  Never
+                        // histogram chunks: the look-back needs every
+                        // predecessor chunk running or done.
+                        uint32_t claim = 1u;
+                        if (type == T_FINISH)
+                            claim = nt >= 128u ? 8u : (nt >= 64u ? 4u : (nt >= 16u ? 2u : 1u));
+                        else if ((type == T_LSTATS || type == T_LSCATTER) && nt - tn >= 4u * nctas)
+                            claim = 2u;
                         const uint32_t t = atomicAdd(&P.tnext[e], claim);
                         if (t < nt) {
                             out[0] = type;
@@ -136,13 +151,15 @@ __device__ void dequeue(const Params &P, uint32_t *out)
             }
             if (lane == 0 && next_head > h) atomicCAS(&C->q_head[q], h, next_head);
         }
+        // nothing to claim: all work done, or wait for more
         uint32_t stop = 0;
         if (lane == 0) {
             if (ld_acquire(&C->pending) == 0) {
                 stop = 1;
             } else {
                 const unsigned long long pr = ld_relaxed64(&C->progress), now = globaltimer();
-                if (pr != last) {
+                if (!waited || pr != last) {
+                    waited = true;
                     last = pr;
                     t0 = now;
                 } else if (now - t0 > P.wait_ns) {
