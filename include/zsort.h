@@ -298,7 +298,7 @@ int zsort_map_buckets(const uint64_t *keys, uint64_t n, const zsort_opts *opts, 
  * start-up, or processes that must stay inside a fixed memory pool.  The
  * paper has no counterpart; it is a deployment variant.
  *   - Allocates nothing: no cudaMalloc/cudaFree and no allocating library
- *     call.  Its scratch is a static __device__ array of about 18 MB for up
+ *     call.  Its scratch is a static __device__ array of about 21 MB for up
  *     to ZSORT_NOALLOC_MAX_N (2^20) elements that every GPU which loads this
  *     library holds until the process exits.  n > ZSORT_NOALLOC_MAX_N is
  *     rejected with ZSORT_ERR_INVALID before anything is enqueued.

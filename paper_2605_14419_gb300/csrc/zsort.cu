@@ -330,7 +330,7 @@ size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 // Capacity plan for calls of up to n elements and nseg segments.
 struct Plan {
     unsigned long long qcap, segcap, itemcap, statuscap, traincap;
-    size_t off_skeys, off_svals, off_ctl, off_epoch, off_entries, off_ready, off_tnext, off_tdone, off_segs,
+    size_t off_skeys, off_svals, off_ids, off_ctl, off_epoch, off_entries, off_ready, off_tnext, off_tdone, off_segs,
         off_items, off_bstart, off_status, off_pwl, off_train, total;
 };
 
@@ -357,6 +357,7 @@ Plan make_plan(unsigned long long n, unsigned long long nseg, unsigned long long
     };
     p.off_skeys = take(n * 8);
     p.off_svals = take(n * 4);
+    p.off_ids = take(n * 2);
     p.off_ctl = take(sizeof(Ctl));
     p.off_epoch = take(16);
     p.off_entries = take(QUEUES * p.qcap * sizeof(Entry));
@@ -436,6 +437,7 @@ int get_workspace(cudaStream_t stream, unsigned long long n, unsigned long long 
         P = Params{};
         P.skeys = reinterpret_cast<uint64_t *>(b + p.off_skeys);
         P.svals = reinterpret_cast<uint32_t *>(b + p.off_svals);
+        P.ids = reinterpret_cast<uint16_t *>(b + p.off_ids);
         P.ctl = reinterpret_cast<Ctl *>(b + p.off_ctl);
         P.epoch_ctr = reinterpret_cast<uint32_t *>(b + p.off_epoch);
         P.entries = reinterpret_cast<Entry *>(b + p.off_entries);
@@ -639,7 +641,7 @@ constexpr size_t na_align(size_t x) { return (x + 255) & ~size_t(255); }
 // NA_MAX_N elements and one segment, with one learned-map training slot.
 struct NaLayout {
     unsigned long long qcap, segcap, itemcap, statuscap, traincap;
-    size_t skeys, svals, ctl, epoch, entries, ready, tnext, tdone, segs, items, bstart, status, pwl,
+    size_t skeys, svals, ids, ctl, epoch, entries, ready, tnext, tdone, segs, items, bstart, status, pwl,
         train, total;
 };
 constexpr NaLayout na_layout()
@@ -653,6 +655,7 @@ constexpr NaLayout na_layout()
     size_t o = 0;
     L.skeys = o; o = na_align(o + NA_MAX_N * 8);
     L.svals = o; o = na_align(o + NA_MAX_N * 4);
+    L.ids = o; o = na_align(o + NA_MAX_N * 2);
     L.ctl = o; o = na_align(o + sizeof(Ctl));
     L.epoch = o; o = na_align(o + 16);
     L.entries = o; o = na_align(o + QUEUES * L.qcap * sizeof(Entry));
@@ -1041,6 +1044,7 @@ int zsort_pairs_noalloc(uint64_t *keys, uint32_t *vals, uint64_t n, int32_t *sta
     P.n = n;
     P.skeys = reinterpret_cast<uint64_t *>(b + NA.skeys);
     P.svals = reinterpret_cast<uint32_t *>(b + NA.svals);
+    P.ids = reinterpret_cast<uint16_t *>(b + NA.ids);
     P.ctl = reinterpret_cast<Ctl *>(b + NA.ctl);
     P.epoch_ctr = reinterpret_cast<uint32_t *>(b + NA.epoch);
     P.entries = reinterpret_cast<Entry *>(b + NA.entries);

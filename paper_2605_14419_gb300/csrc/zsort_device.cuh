@@ -156,6 +156,7 @@ struct Params {
     Item *items;
     uint32_t itemcap;
     uint32_t *bstart;   // segcap * NB_MAX
+    uint16_t *ids;      // n: a learned map's bucket of every key, from histogram to scatter
     uint32_t *status;            // look-back words and chunk offsets: 2 * chunks * k per segment
     unsigned long long statuscap;
     uint32_t nctas;              // CTAs of the persistent launch

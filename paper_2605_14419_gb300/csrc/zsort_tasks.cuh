@@ -544,8 +544,9 @@ __device__ __forceinline__ void body_stats(LAcc &a, LAcc &b, uint32_t cnt, const
 
 // Histogram of the tile's buckets into s.hist: one shared-memory atomic per
 // key, except when a whole warp slot shares one bucket (duplicate runs).
-template <bool MLP>
-__device__ __forceinline__ void body_hist(SmemTile &s, const MapK &mk, uint32_t cnt, const unsigned long long *sk)
+template <bool MLP, bool IDS = false>
+__device__ __forceinline__ void body_hist(SmemTile &s, const MapK &mk, uint32_t cnt, const unsigned long long *sk,
+                                          uint16_t *ids = nullptr)
 {
     const int lane = threadIdx.x & 31;
     unsigned long long x[IPT];
@@ -556,6 +557,11 @@ __device__ __forceinline__ void body_hist(SmemTile &s, const MapK &mk, uint32_t 
         x[i] = p < cnt ? sk[p] : mk.mn;
     }
     map_tile<IPT, MLP>(mk, s.map, x, bb);
+    if (IDS) {  // a learned map's buckets, for the scatter to read back
+#pragma unroll
+        for (int i = 0; i < IPT; i++)
+            if (slot_index(i) < cnt) __stcg(ids + slot_index(i), (unsigned short)bb[i]);
+    }
 #pragma unroll
     for (int i = 0; i < IPT; i++) {
         const uint32_t b = slot_index(i) >= cnt ? INVALID : bb[i];
@@ -570,12 +576,17 @@ __device__ __forceinline__ void body_hist(SmemTile &s, const MapK &mk, uint32_t 
 
 // Histogram of [start, start+len) into s.hist (its own instantiation per map
 // family, so that each keeps its registers).
+// A learned map (piecewise-linear or MLP) also writes every key's bucket to
+// ids[start, start+len): the scatter of the same chunk reads them back
+// instead of evaluating the map a second time.
 template <bool MLP>
 __device__ __noinline__ void hist_stream(const Params &P, SmemTile &s, Pipe &pp, const uint64_t *src, bool bulk,
                                          unsigned long long start, unsigned long long len, const MapK mk)
 {
     stream_tiles<false>(P, s, pp, src, nullptr, bulk, start, len,
-                        [&](uint32_t, uint32_t cnt, unsigned long long *sk, uint32_t *) { body_hist<MLP>(s, mk, cnt, sk); });
+                        [&](uint32_t t, uint32_t cnt, unsigned long long *sk, uint32_t *) {
+                            body_hist<MLP, true>(s, mk, cnt, sk, P.ids + start + (unsigned long long)t * TILE);
+                        });
 }
 
 // Stable scatter of [start, start+len) of a (sub)array whose map is in s.map
@@ -586,7 +597,7 @@ __device__ __noinline__ void hist_stream(const Params &P, SmemTile &s, Pipe &pp,
 // than any map is to recompute).  Four barriers a tile: the
 // tile's bulk copy is issued once every thread has left the tile that last
 // used its buffer, and each warp clears its own bucket counters.
-template <int NBITS, bool MLP, bool KV>
+template <int NBITS, bool IDS, bool KV>
 __device__ __noinline__ void scatter_stream(const Params &P, SmemTile &s, Pipe &pp, const uint64_t *srck,
                                             const uint32_t *srcv, bool bulk, unsigned long long start,
                                             unsigned long long len, uint64_t *dstk, uint32_t *dstv, uint32_t seglen)
@@ -610,6 +621,14 @@ __device__ __noinline__ void scatter_stream(const Params &P, SmemTile &s, Pipe &
         unsigned long long *sk;
         uint32_t *sv;
         bool ok = true;
+        uint32_t b[IPT];
+        if (IDS) {  // the histogram pass's buckets: loads in flight during the tile's wait
+#pragma unroll
+            for (int i = 0; i < IPT; i++) {
+                const uint32_t p = slot_index(i);
+                b[i] = p < cnt ? (uint32_t)__ldcg(reinterpret_cast<const unsigned short *>(P.ids) + a + p) : 0u;
+            }
+        }
         if (bulk) {
             sk = s.u.buf[w].key + (a & 1ull);
             sv = s.u.buf[w].val + (a & 3ull);
@@ -629,7 +648,7 @@ __device__ __noinline__ void scatter_stream(const Params &P, SmemTile &s, Pipe &
             __syncthreads();
         }
         unsigned long long x[IPT];
-        uint32_t v[IPT], b[IPT], pos[IPT], peers[IPT];
+        uint32_t v[IPT], pos[IPT], peers[IPT];
 #pragma unroll
         for (int i = 0; i < IPT; i++) {
             const uint32_t p = slot_index(i);
@@ -637,7 +656,7 @@ __device__ __noinline__ void scatter_stream(const Params &P, SmemTile &s, Pipe &
             x[i] = in ? sk[p] : mk.mn;
             v[i] = in && kv ? sv[p] : 0u;
         }
-        map_tile<IPT, MLP>(mk, s.map, x, b);  // lanes past cnt: ignored by the ranking
+        if (!IDS) map_tile<IPT, false>(mk, s.map, x, b);  // lanes past cnt: ignored by the ranking
         rank_peers<IPT, NBITS>(b, cnt, peers);
         rank_leaders<IPT>(b, peers, pos, s);
         // every thread has left the previous tile: its buffer may be refilled
@@ -690,9 +709,14 @@ template <bool KV>
 __device__ __forceinline__ void scatter_pick(const Params &P, SmemTile &s, Pipe &pp, const uint64_t *srck,
                                              const uint32_t *srcv, bool bulk, unsigned long long start,
                                              unsigned long long len, uint64_t *dstk, uint32_t *dstv, uint32_t seglen,
-                                             uint32_t k)
+                                             uint32_t k, bool ids)
 {
-    if (s.map.kind == MAP_MLP) {  // k >= 256 for a learned map
+    const bool learned = s.map.kind == MAP_MLP || s.map.kind == MAP_PWL;
+    if (learned != ids) {  // only chunked partitions learn maps, and their histograms write ids
+        set_error(P, ST_INTERNAL);
+        return;
+    }
+    if (ids) {  // learned: buckets from the histogram pass; k >= 256
         switch (rank_bits(k)) {
         case 8: scatter_stream<8, true, KV>(P, s, pp, srck, srcv, bulk, start, len, dstk, dstv, seglen); break;
         case 9: scatter_stream<9, true, KV>(P, s, pp, srck, srcv, bulk, start, len, dstk, dstv, seglen); break;
@@ -708,14 +732,16 @@ __device__ __forceinline__ void scatter_pick(const Params &P, SmemTile &s, Pipe 
     }
 }
 
+// ids: the buckets of a learned map come from the histogram pass (chunked
+// partitions); otherwise the scatter evaluates the (z-score or range) map.
 __device__ void scatter_dispatch(const Params &P, SmemTile &s, Pipe &pp, const uint64_t *srck, const uint32_t *srcv,
                                  bool bulk, unsigned long long start, unsigned long long len, uint64_t *dstk,
-                                 uint32_t *dstv, uint32_t seglen, uint32_t k)
+                                 uint32_t *dstv, uint32_t seglen, uint32_t k, bool ids)
 {
     if (P.kv)
-        scatter_pick<true>(P, s, pp, srck, srcv, bulk, start, len, dstk, dstv, seglen, k);
+        scatter_pick<true>(P, s, pp, srck, srcv, bulk, start, len, dstk, dstv, seglen, k, ids);
     else
-        scatter_pick<false>(P, s, pp, srck, srcv, bulk, start, len, dstk, dstv, seglen, k);
+        scatter_pick<false>(P, s, pp, srck, srcv, bulk, start, len, dstk, dstv, seglen, k, ids);
 }
 
 // ------------------------------------------------------------ children
@@ -1503,6 +1529,8 @@ __device__ __noinline__ void task_lhist(const Params &P, uint32_t sid, uint32_t 
     const uint64_t *src = keys_of(P, ch.buf);
     if (mk.kind == MAP_MLP)
         hist_stream<true>(P, s, pp, src, bulk_ok(P, ch.buf), ch.start, ch.len, mk);
+    else if (mk.kind == MAP_PWL)
+        hist_stream<false>(P, s, pp, src, bulk_ok(P, ch.buf), ch.start, ch.len, mk);
     else
         stream_tiles<false>(P, s, pp, src, nullptr, bulk_ok(P, ch.buf), ch.start, ch.len,
                             [&](uint32_t, uint32_t cnt, unsigned long long *sk, uint32_t *) {
@@ -1615,7 +1643,7 @@ __device__ __noinline__ void task_lscatter(const Params &P, uint32_t sid, uint32
     uint64_t *dstk = keys_of(P, ch.buf ^ 1u) + ch.off;
     uint32_t *dstv = vals_of(P, ch.buf ^ 1u) + ch.off;
     scatter_dispatch(P, s, pp, keys_of(P, ch.buf), vals_of(P, ch.buf), bulk_ok(P, ch.buf), ch.start, ch.len, dstk,
-                     dstv, ch.seglen, k);
+                     dstv, ch.seglen, k, s.map.kind == MAP_MLP || s.map.kind == MAP_PWL);
     if (threadIdx.x == 0) atomicAdd(&P.ctl->bytes, 2ull * elem_bytes(P) * ch.len);
 }
 
@@ -1692,7 +1720,7 @@ __device__ __noinline__ void task_mpart(const Params &P, const Item it, SmemTile
     __syncthreads();
     uint64_t *dstk = keys_of(P, buf ^ 1u) + off;
     uint32_t *dstv = vals_of(P, buf ^ 1u) + off;
-    scatter_dispatch(P, s, pp, srck, srcv, bulk, off, len, dstk, dstv, len, k);
+    scatter_dispatch(P, s, pp, srck, srcv, bulk, off, len, dstk, dstv, len, k, false);
     if (threadIdx.x == 0) {
         atomicAdd(&P.ctl->n_small, 1ull);
         atomicAdd(&P.ctl->bytes, (16ull + 2ull * elem_bytes(P)) * len);
