@@ -110,20 +110,31 @@ __device__ void dequeue(const Params &P, uint32_t ep, uint32_t *out)
                     tn = ld_relaxed(&P.tnext[e]);
                 }
                 const uint32_t mr = __ballot_sync(full, rdy);
+                // the head may pass the leading run of published entries
+                // whose tiles are all claimed (seen here, even if this window
+                // still has tiles to give)
+                const uint32_t spent = __ballot_sync(full, rdy && tn >= nt);
+                if (next_head == base) next_head = base + (spent == full ? 32u : (uint32_t)(__ffs(~spent) - 1));
                 uint32_t m = __ballot_sync(full, rdy && tn < nt);
-                while (m) {  // claim from the first entry with tiles left
-                    const int f = __ffs(m) - 1;
+                // CTAs start at different entries of the window (by block
+                // index), so that they do not all race for the first one; the
+                // tiles of one entry are still handed out in order
+                const uint32_t rot = blockIdx.x & 31u;
+                m = rot ? (m >> rot) | (m << (32u - rot)) : m;
+                while (m) {
+                    const int f = (int)((__ffs(m) - 1 + rot) & 31u);
                     uint32_t got = 0;
                     if (lane == f) {
                         // leaves a few at a time, so that each can be
-                        // prefetched while its predecessor is sorted; the
+                        // prefetched while its predecessor is sorted (about a
+                        // quarter of what the entry has left, at most 8); the
                         // statistics and scatter chunks (which wait on no
                         // other chunk) two at a time while many remain.  Never
                         // histogram chunks: the look-back needs every
                         // predecessor chunk running or done.
                         uint32_t claim = 1u;
                         if (type == T_FINISH)
-                            claim = nt >= 128u ? 8u : (nt >= 64u ? 4u : (nt >= 16u ? 2u : 1u));
+                            claim = min(8u, max(1u, (nt - tn + 3u) / 4u));
                         else if ((type == T_LSTATS || type == T_LSCATTER) && nt - tn >= 4u * nctas)
                             claim = 2u;
                         const uint32_t t = atomicAdd(&P.tnext[e], claim);
@@ -143,10 +154,7 @@ __device__ void dequeue(const Params &P, uint32_t ep, uint32_t *out)
                     }
                     m &= m - 1;
                 }
-                // every published entry of this window is now fully claimed;
-                // the head may pass the leading run of them
-                const uint32_t lead = mr == full ? 32u : (uint32_t)(__ffs(~mr) - 1);
-                if (next_head == base) next_head = base + lead;
+                // every published entry of this window is now fully claimed
                 if (mr != full) break;  // an unpublished entry: look again later
             }
             if (lane == 0 && next_head > h) atomicCAS(&C->q_head[q], h, next_head);
