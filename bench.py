@@ -301,6 +301,7 @@ def main():
     ap.add_argument("--mapper", default="learned", choices=["learned", "zscore"])
     ap.add_argument("--sample", type=int, default=1 << 22, help="CPU oracle sample size")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-lanes", type=int, default=1, help="copy streams per direction in the e2e measurement")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the z-score comparison run")
     ap.add_argument("--workload", default="pairs", choices=["pairs", "batched"],
@@ -533,29 +534,48 @@ def main():
         # array's transfers overlap the other's sort and the two directions
         # overlap each other; a device buffer is refilled once its result has
         # been read back
-        h2d_s = torch.cuda.Stream(device=dev)
-        d2h_s = torch.cuda.Stream(device=dev)
+        # each direction's copies are split over --e2e-lanes streams, so that
+        # several copy engines share the link
+        E2E_LANES = max(1, args.e2e_lanes)
+        h2d_s = [torch.cuda.Stream(device=dev) for _ in range(E2E_LANES)]
+        d2h_s = [torch.cuda.Stream(device=dev) for _ in range(E2E_LANES)]
         free = [torch.cuda.Event() for _ in bufs]
         for ev in free:
-            ev.record(d2h_s)
+            ev.record(d2h_s[0])
+
+        def pieces(t):
+            step = (t.numel() + E2E_LANES - 1) // E2E_LANES
+            return [t[j * step:(j + 1) * step] for j in range(E2E_LANES)]
 
         def e2e_step():
             for i, (kb, vb) in enumerate(bufs):
-                h2d_s.wait_event(free[i])
-                with torch.cuda.stream(h2d_s):
-                    kb.copy_(hk[i], non_blocking=True)
-                    vb.copy_(hv[i], non_blocking=True)
-                arrived = torch.cuda.Event()
-                arrived.record(h2d_s)
-                stream.wait_event(arrived)
+                arrived = []
+                for j, (cs, dk, hk_j, dv, hv_j) in enumerate(zip(h2d_s, pieces(kb), pieces(hk[i]), pieces(vb),
+                                                                 pieces(hv[i]))):
+                    cs.wait_event(free[i])
+                    with torch.cuda.stream(cs):
+                        dk.copy_(hk_j, non_blocking=True)
+                        dv.copy_(hv_j, non_blocking=True)
+                    ev = torch.cuda.Event()
+                    ev.record(cs)
+                    arrived.append(ev)
+                for ev in arrived:
+                    stream.wait_event(ev)
                 z.sort_pairs(kb, vb, opts=opts, stream=stream, check=False)
                 sorted_ev = torch.cuda.Event()
                 sorted_ev.record(stream)
-                d2h_s.wait_event(sorted_ev)
-                with torch.cuda.stream(d2h_s):
-                    ok_k[i].copy_(kb, non_blocking=True)
-                    ok_v[i].copy_(vb, non_blocking=True)
-                free[i].record(d2h_s)
+                back = []
+                for cs, hk_j, dk, hv_j, dv in zip(d2h_s, pieces(ok_k[i]), pieces(kb), pieces(ok_v[i]), pieces(vb)):
+                    cs.wait_event(sorted_ev)
+                    with torch.cuda.stream(cs):
+                        hk_j.copy_(dk, non_blocking=True)
+                        hv_j.copy_(dv, non_blocking=True)
+                    ev = torch.cuda.Event()
+                    ev.record(cs)
+                    back.append(ev)
+                for ev in back[1:]:  # the buffer is free once every piece is back
+                    d2h_s[0].wait_event(ev)
+                free[i].record(d2h_s[0])
 
         for _ in range(2):
             e2e_step()
@@ -564,8 +584,8 @@ def main():
         e1 = torch.cuda.Event(enable_timing=True)
         e_steps = max(3, args.steps // 2)
         e0.record(stream)
-        h2d_s.wait_event(e0)
-        d2h_s.wait_event(e0)
+        for cs in h2d_s + d2h_s:
+            cs.wait_event(e0)
         for _ in range(e_steps):
             e2e_step()
         for ev in free:  # every result is back on the host
