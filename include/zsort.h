@@ -133,6 +133,17 @@ typedef struct {
  * keys/vals are not touched and the next call on the stream works as usual.
  * Not a sort: it exists to check the failure path without any GPU fault. */
 #define ZSORT_FLAG_TEST_STALL 2u
+
+/* Fault injection for failure-path tests, without any GPU fault: the
+ * environment variable ZSORT_FAULT, read at every sorting call.
+ *   "alloc"       the workspace allocation fails: the call returns
+ *                 ZSORT_ERR_NOMEM and enqueues nothing;
+ *   "timeout"     as ZSORT_FLAG_TEST_STALL with a 50 ms wait limit:
+ *                 zsort_sync_status returns ZSORT_ERR_TIMEOUT;
+ *   "badoffsets"  the segment check reports malformed offsets:
+ *                 zsort_sync_status returns ZSORT_ERR_BAD_OFFSETS.
+ * In every case keys and payloads are untouched and the next call without
+ * the variable works as usual. */
 /* Task trace: the persistent kernel records every task it runs (one record
  * per dequeued task: start and end time, CTA, task type, partition depth),
  * read back with zsort_last_trace.  The first traced call on a stream

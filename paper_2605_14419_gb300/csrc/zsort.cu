@@ -150,6 +150,10 @@ __global__ void k_init_segments(Params P, const uint64_t *off, unsigned long lon
 {
     const unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nseg) return;
+    if (P.test_badoff) {  // injected: as if the offsets had failed the check, nothing is published
+        if (i == 0) set_error(P, ST_BAD_OFFSETS);
+        return;
+    }
     const unsigned long long a = off ? off[i] : 0ull, b = off ? off[i + 1] : P.n;
     if (a > b || b > P.n) {
         set_error(P, ST_BAD_OFFSETS);
@@ -490,10 +494,36 @@ bool opts_valid(const zsort_opts &o)
     return true;
 }
 
+// Host-side fault injection for failure-path tests: the environment variable
+// ZSORT_FAULT, read at every call.  "alloc": the workspace allocation fails
+// (ZSORT_ERR_NOMEM, nothing enqueued); "timeout": the call publishes no work
+// and every device wait runs out after 50 ms (ZSORT_ERR_TIMEOUT from
+// zsort_sync_status, as ZSORT_FLAG_TEST_STALL); "badoffsets": the segment
+// check reports malformed offsets (ZSORT_ERR_BAD_OFFSETS).  No GPU fault is
+// involved in any of them; keys and payloads are left untouched.
+enum Fault { FAULT_NONE, FAULT_ALLOC, FAULT_TIMEOUT, FAULT_BADOFF };
+Fault injected_fault()
+{
+    const char *f = std::getenv("ZSORT_FAULT");
+    if (!f) return FAULT_NONE;
+    if (std::strcmp(f, "alloc") == 0) return FAULT_ALLOC;
+    if (std::strcmp(f, "timeout") == 0) return FAULT_TIMEOUT;
+    if (std::strcmp(f, "badoffsets") == 0) return FAULT_BADOFF;
+    return FAULT_NONE;
+}
+
 // Enqueues one sort (single array when off == nullptr).
 int launch(uint64_t *keys, uint32_t *vals, unsigned long long n, const uint64_t *off,
-           unsigned long long nseg, const zsort_opts &o, cudaStream_t stream, uint32_t *plan_out = nullptr)
+           unsigned long long nseg, const zsort_opts &o_in, cudaStream_t stream, uint32_t *plan_out = nullptr)
 {
+    const Fault fault = injected_fault();
+    if (fault == FAULT_ALLOC) return ZSORT_ERR_NOMEM;
+    zsort_opts o = o_in;
+    if (fault == FAULT_TIMEOUT) {
+        o.flags = (o.flags | ZSORT_FLAG_TEST_STALL) & ~ZSORT_FLAG_GRAPH;
+        o.wait_limit_ms = 50;
+    }
+    if (fault == FAULT_BADOFF) o.flags &= ~ZSORT_FLAG_GRAPH;
     std::lock_guard<std::mutex> lock(g_mu);
     Workspace *ws = nullptr;
     int rc = get_workspace(stream, n, nseg, o.large_min, o.chunks_per_cta, &ws);
@@ -518,6 +548,7 @@ int launch(uint64_t *keys, uint32_t *vals, unsigned long long n, const uint64_t 
     P.user_aligned = ((reinterpret_cast<uintptr_t>(keys) | reinterpret_cast<uintptr_t>(vals)) & 15u) == 0;
     P.kv = vals != nullptr;  // null vals: keys only
     P.test_stall = (o.flags & ZSORT_FLAG_TEST_STALL) ? 1u : 0u;
+    P.test_badoff = fault == FAULT_BADOFF ? 1u : 0u;
     if (o.flags & ZSORT_FLAG_TRACE) {
         if (!ws->trace) {
             void *t = nullptr;

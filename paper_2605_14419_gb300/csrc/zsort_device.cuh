@@ -164,6 +164,7 @@ struct Params {
     uint32_t user_aligned;       // caller's keys and vals 16-byte aligned: bulk copies allowed
     uint32_t kv;                 // 1: (key, payload) pairs; 0: keys only (vals == null)
     uint32_t test_stall;         // publish nothing, one entry pending: every wait runs out
+    uint32_t test_badoff;        // fault injection: the segment check reports bad offsets
     TraceRec *trace;             // task trace (null: not traced)
     uint32_t trace_cap;          // records trace can hold
     float *pwl;         // segcap * PWL_STRIDE: breakpoints q[0..P], reciprocals r[0..P), MLP table

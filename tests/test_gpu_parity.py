@@ -403,6 +403,41 @@ def test_bounded_wait_runs_out_and_the_context_recovers():
     assert np.array_equal(v.cpu().numpy().view(np.uint32), ov)
 
 
+@pytest.mark.parametrize("mode,code,when", [("alloc", z.ERR_NOMEM, "call"),
+                                            ("timeout", z.ERR_TIMEOUT, "status"),
+                                            ("badoffsets", z.ERR_BAD_OFFSETS, "status")])
+@pytest.mark.parametrize("segmented", [False, True])
+def test_fault_injection_env(monkeypatch, mode, code, when, segmented):
+    """ZSORT_FAULT injects a failure on the host: the call (alloc) or the
+    device status (timeout, bad offsets) reports it, the data is untouched,
+    and the next call without the variable sorts exactly."""
+    keys, vals, off, _ = inputs.segmented(40, 43, lo=32, hi=200_000) if segmented else \
+        (inputs.uniform(300_000, 42), None, None, None)
+    vals = inputs.index_payload(keys.size) if vals is None else vals
+    k, v = to_dev(keys, vals)
+    od = torch.from_numpy(off.view(np.int64)).to(DEV) if segmented else None
+
+    def run():
+        if segmented:
+            z.sort_segmented(k, v, od)
+        else:
+            z.sort_pairs(k, v)
+
+    monkeypatch.setenv("ZSORT_FAULT", mode)
+    with pytest.raises(z.ZsortError) as ei:
+        run()
+    assert ei.value.code == code
+    if when == "call":
+        assert z.sync_status() == z.OK
+    assert np.array_equal(k.cpu().numpy().view(np.uint64), keys)
+    assert np.array_equal(v.cpu().numpy().view(np.uint32), vals)
+    monkeypatch.delenv("ZSORT_FAULT")
+    run()
+    ok, ov = oracle.zsort_segmented(keys, vals, off) if segmented else oracle.zsort_pairs(keys, vals)
+    assert np.array_equal(k.cpu().numpy().view(np.uint64), ok)
+    assert np.array_equal(v.cpu().numpy().view(np.uint32), ov)
+
+
 # ---------------------------------------------------------------- 128-bit keys
 def u128_case(n, seed, hi_distinct=None, lo_distinct=None):
     rng = np.random.default_rng(seed)
