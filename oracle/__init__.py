@@ -41,6 +41,22 @@ class Trace(ctypes.Structure):
     ]
 
 
+class SubRec(ctypes.Structure):
+    """One zsortRec sub-problem (mirrors ``oracle_sub_rec`` in the C file)."""
+
+    _fields_ = [
+        ("depth", ctypes.c_uint64),
+        ("parent_bucket", ctypes.c_uint64),
+        ("size", ctypes.c_uint64),
+        ("min", ctypes.c_uint64),
+        ("parent_min", ctypes.c_uint64),
+        ("est_parent_d", ctypes.c_double),
+        ("mean", ctypes.c_double),
+        ("sd", ctypes.c_double),
+        ("zmin", ctypes.c_double),
+    ]
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc; returns the path of the shared library."""
     with _lock:
@@ -63,6 +79,11 @@ def _load():
         lib.oracle_zsort_pairs_ex.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
                                               ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64,
                                               ctypes.c_uint64, ctypes.POINTER(Trace)]
+        lib.oracle_zsort_pairs_rec.restype = ctypes.c_int
+        lib.oracle_zsort_pairs_rec.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
+                                               ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64,
+                                               ctypes.c_uint64, ctypes.POINTER(Trace),
+                                               ctypes.POINTER(SubRec), ctypes.c_uint64, u64p]
         lib.oracle_zsort_segmented.restype = ctypes.c_int
         lib.oracle_zsort_segmented.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                ctypes.c_uint64]
@@ -123,6 +144,22 @@ def zsort_pairs(keys, vals, alpha: float = 0.6, leaf: int = 96, count_range: int
     if rc != 0:
         raise MemoryError("oracle allocation failed")
     return (k, v, tr) if with_trace else (k, v)
+
+
+def zsort_pairs_records(keys, vals, alpha: float = 0.6, leaf: int = 96, count_range: int = 65000,
+                        guard_depth: int = 32, cap: int = 1 << 16):
+    """As zsort_pairs, and the list of zsortRec sub-problems (SubRec) the run
+    partitioned, in the order it visited them (R9: meanEst, mean, sd, Zmin)."""
+    k = np.ascontiguousarray(keys, dtype=np.uint64).copy()
+    v = np.ascontiguousarray(vals, dtype=np.uint32).copy()
+    tr = Trace()
+    recs = (SubRec * cap)()
+    cnt = ctypes.c_uint64()
+    rc = _load().oracle_zsort_pairs_rec(_ptr(k), _ptr(v), k.size, alpha, leaf, count_range, guard_depth,
+                                        ctypes.byref(tr), recs, cap, ctypes.byref(cnt))
+    if rc != 0:
+        raise MemoryError("oracle allocation failed")
+    return k, v, tr, [recs[i] for i in range(min(cnt.value, cap))]
 
 
 def zsort_segmented(keys, vals, offsets):

@@ -12,6 +12,8 @@
  *   oracle_stats             Alg. 1, statistics loops (min, mean, population sd)
  *   oracle_zsort_pairs       Alg. 1 + zsortRec (section "Proposed Work"), on
  *                            (uint64 key, uint32 payload) pairs, stable
+ *   oracle_zsort_pairs_rec   the same, also recording every zsortRec
+ *                            sub-problem's meanEst, mean, sd and Zmin (R9)
  *   oracle_zsort_segmented   the same, applied to each segment of a batch
  *   oracle_key_from_i64/f64  order-preserving key encodings (not in the paper;
  *                            definitions of two's-complement order and of the
@@ -52,6 +54,15 @@
  *       sub-problem with min < max into one cluster, or the depth reaches
  *       `guard_depth`, that level uses the range map
  *       b = floor(d * k / (range + 1)) in exact 128-bit integer arithmetic.
+ *   R11 The learned map is not in the paper; it is a fitted model whose
+ *       parameters are the breakpoints q[0..P] and one slope per piece,
+ *       r[s] = fl32(1 / (q[s+1] - q[s])), fixed when the model is trained.
+ *       Inference multiplies by the stored slope, frac = fl32(fl32(u - q[s])
+ *       * r[s]), instead of dividing by the width for every key.  Both forms
+ *       are monotone in u inside a piece (a rounded product or quotient by a
+ *       fixed positive number), so either sorts exactly; they can differ in
+ *       the last bit of frac and so in the bucket of a key that sits on a
+ *       sub-bucket edge.  The stored-slope form is the definition here.
  */
 #include <math.h>
 #include <stdint.h>
@@ -72,6 +83,15 @@ typedef struct {
     double scale;             /* Eq. 1 scale (R5)                            */
 } oracle_trace;
 
+/* One zsortRec sub-problem as it was partitioned (R9): the cluster j of the
+ * parent it came from, its size and minimum, meanEst in the parent's frame
+ * (d-units above the parent's minimum), and the mean (meanEst moved into
+ * its own frame), standard deviation about that mean and Zmin it used. */
+typedef struct {
+    uint64_t depth, parent_bucket, size, min, parent_min;
+    double est_parent_d, mean, sd, zmin;
+} oracle_sub_rec;
+
 typedef struct {
     uint64_t k;
     double scale;
@@ -80,6 +100,8 @@ typedef struct {
     uint64_t guard_depth; /* depth from which R10 always applies           */
     uint64_t *count;      /* counting-sort histogram, count_range entries  */
     oracle_trace *tr;
+    oracle_sub_rec *rec;  /* optional record of the sub-problems (R9)      */
+    uint64_t rec_cap, rec_n;
 } zs_ctx;
 
 /* ------------------------------------------------------------------------ */
@@ -172,7 +194,7 @@ static uint64_t rmap(uint64_t d, uint64_t range, uint64_t k)
 static void zs_rec(zs_ctx *c, uint64_t *sk, uint32_t *sv, uint64_t *dk,
                    uint32_t *dv, uint64_t *tk, uint32_t *tv, uint64_t size,
                    int have_est, double est_parent_d, uint64_t parent_min,
-                   uint64_t depth)
+                   uint64_t parent_bucket, uint64_t depth)
 {
     oracle_trace *tr = c->tr;
     if (depth > tr->max_depth) tr->max_depth = depth;
@@ -221,6 +243,21 @@ static void zs_rec(zs_ctx *c, uint64_t *sk, uint32_t *sv, uint64_t *dk,
     }
     double sd = sqrt(var / (double)size);
     double zmin = fabs((0.0 - mean) / sd); /* R3: Zmin = |(min - mean)/std| */
+    if (have_est && c->rec) {
+        if (c->rec_n < c->rec_cap) {
+            oracle_sub_rec *r = &c->rec[c->rec_n];
+            r->depth = depth;
+            r->parent_bucket = parent_bucket;
+            r->size = size;
+            r->min = mn;
+            r->parent_min = parent_min;
+            r->est_parent_d = est_parent_d;
+            r->mean = mean;
+            r->sd = sd;
+            r->zmin = zmin;
+        }
+        c->rec_n++;
+    }
     uint64_t k = c->k;
     double scale = c->scale;
 
@@ -278,7 +315,7 @@ static void zs_rec(zs_ctx *c, uint64_t *sk, uint32_t *sv, uint64_t *dk,
             /* The cluster in tmp is the child's source; src is free now and
              * serves as the child's auxiliary array. */
             zs_rec(c, tk + lb, tv + lb, dk + lb, dv + lb, sk + lb, sv + lb, cnt,
-                   1, est, mn, depth + 1);
+                   1, est, mn, b, depth + 1);
         } else {
             memcpy(dk + lb, tk + lb, (size_t)cnt * sizeof(uint64_t));
             memcpy(dv + lb, tv + lb, (size_t)cnt * sizeof(uint32_t));
@@ -298,13 +335,16 @@ static void zs_rec(zs_ctx *c, uint64_t *sk, uint32_t *sv, uint64_t *dk,
  * (65000); guard_depth: depth from which the range map is always used.
  * Returns 0, or -1 on allocation failure.
  */
-int oracle_zsort_pairs_ex(uint64_t *keys, uint32_t *vals, uint64_t n,
-                          double alpha, uint64_t leaf, uint64_t count_range,
-                          uint64_t guard_depth, oracle_trace *trace)
+int oracle_zsort_pairs_rec(uint64_t *keys, uint32_t *vals, uint64_t n,
+                           double alpha, uint64_t leaf, uint64_t count_range,
+                           uint64_t guard_depth, oracle_trace *trace,
+                           oracle_sub_rec *rec, uint64_t rec_cap,
+                           uint64_t *rec_count)
 {
     oracle_trace local;
     oracle_trace *tr = trace ? trace : &local;
     memset(tr, 0, sizeof(*tr));
+    if (rec_count) *rec_count = 0;
     if (n <= 1) return 0;
     zs_ctx c;
     uint64_t k = (uint64_t)floor(alpha * sqrt((double)n));
@@ -315,6 +355,9 @@ int oracle_zsort_pairs_ex(uint64_t *keys, uint32_t *vals, uint64_t n,
     c.count_range = count_range;
     c.guard_depth = guard_depth;
     c.tr = tr;
+    c.rec = rec;
+    c.rec_cap = rec ? rec_cap : 0;
+    c.rec_n = 0;
     tr->k = k;
     tr->scale = c.scale;
     c.count = (uint64_t *)malloc((size_t)(count_range ? count_range : 1) *
@@ -330,11 +373,20 @@ int oracle_zsort_pairs_ex(uint64_t *keys, uint32_t *vals, uint64_t n,
     /* src = a copy of the input (consumed), dst = the caller's arrays. */
     memcpy(bk, keys, (size_t)n * sizeof(uint64_t));
     memcpy(bv, vals, (size_t)n * sizeof(uint32_t));
-    zs_rec(&c, bk, bv, keys, vals, bk + n, bv + n, n, 0, 0.0, 0, 0);
+    zs_rec(&c, bk, bv, keys, vals, bk + n, bv + n, n, 0, 0.0, 0, 0, 0);
+    if (rec_count) *rec_count = c.rec_n;
     free(c.count);
     free(bk);
     free(bv);
     return 0;
+}
+
+int oracle_zsort_pairs_ex(uint64_t *keys, uint32_t *vals, uint64_t n,
+                          double alpha, uint64_t leaf, uint64_t count_range,
+                          uint64_t guard_depth, oracle_trace *trace)
+{
+    return oracle_zsort_pairs_rec(keys, vals, n, alpha, leaf, count_range,
+                                  guard_depth, trace, NULL, 0, NULL);
 }
 
 int oracle_zsort_pairs(uint64_t *keys, uint32_t *vals, uint64_t n,
@@ -458,8 +510,8 @@ void oracle_pwl_train(const uint64_t *sample, uint64_t m, uint64_t mn,
 }
 
 /* Inference: piece s = #{ 0 < j < P : q[j] <= u }; within it the linear
- * interpolation frac = (u - q[s]) * r[s] with the reciprocal width
- * r[s] = 1 / (q[s+1] - q[s]) (0 for an empty piece), clipped to
+ * interpolation frac = (u - q[s]) * r[s] with the stored slope (R11)
+ * r[s] = fl32(1 / (q[s+1] - q[s])) (0 for an empty piece), clipped to
  * [0, 1 - 2^-24]; bucket = s*K + min(K-1, floor(frac * K)), K = k / P.
  * All arithmetic is IEEE binary32 with round-to-nearest; frac is monotone
  * in u inside a piece and every piece owns its own K buckets, so the map is

@@ -144,17 +144,132 @@ def test_cluster_count_and_scale():
         assert tr.scale == k_expected / 4
 
 
-def test_level1_partition_invariant():
-    """max(C_j) <= min(C_{j+1}) (section "Proposed Work"): with the insertion
-    and counting shortcuts off and the guard depth at 1, level-1 clusters are
-    recursed with the range map, whose clusters are contiguous key ranges.
-    Here only the final order is checked plus the depth bound."""
-    keys = inputs.normal(30000, 11)
-    k, v, tr = oracle.zsort_pairs(keys, inputs.index_payload(keys.size), guard_depth=1,
-                                  with_trace=True)
-    rk, rv = stable_reference(keys)
-    assert np.array_equal(v, rv)
-    assert tr.guard_levels >= 1
+@pytest.mark.parametrize("gen", [inputs.uniform, inputs.normal, inputs.lognormal, inputs.gaussian_mixture,
+                                 inputs.zipf, inputs.descending])
+def test_level1_partition_invariant(gen):
+    """max(C_j) <= min(C_{j+1}) for the level-1 clusters of Eq. 1 (section
+    "Proposed Work": every key of a cluster is at most every key of the next
+    one), checked over the oracle's own cluster of every key: in key order
+    the cluster index never decreases, and every non-empty cluster's largest
+    key is at most the next non-empty cluster's smallest."""
+    keys = gen(40_000, 11)
+    for k in (7, 120, 1024):
+        b = oracle.level1_buckets(keys, k).astype(np.int64)
+        assert b.min() >= 0 and b.max() <= k - 1
+        order = np.argsort(keys, kind="stable")
+        assert np.all(np.diff(b[order]) >= 0)
+        used = np.unique(b)
+        lo = np.array([keys[b == j].min() for j in used], dtype=np.uint64)
+        hi = np.array([keys[b == j].max() for j in used], dtype=np.uint64)
+        assert np.all(hi[:-1] <= lo[1:])
+
+
+def test_level1_partition_invariant_catches_a_non_monotone_map():
+    """The check above fails for a map that is not monotone (a dropped
+    absolute value in Zmin folds the keys below the mean back up)."""
+    keys = inputs.normal(5000, 3)
+    mn, _mx, mean, sd = oracle.stats(keys)
+    d = (keys - np.uint64(mn)).astype(np.float64)
+    k = 64
+    h = ((d - mean) / sd - mean / sd) * (k / 4)  # Zmin with the wrong sign
+    b = np.clip(np.floor(np.abs(h)), 0, k - 1).astype(np.int64)
+    order = np.argsort(keys, kind="stable")
+    assert not np.all(np.diff(b[order]) >= 0)
+
+
+def test_meanest_closed_form_on_arithmetic_progression():
+    """R9 (zsortRec): a sub-problem takes mean = meanEst = ((j + 0.5)/scale -
+    Zmin) * sd + mean of its parent, moved into its own frame, and computes
+    its sd about that mean.  On keys base + i*step (i = 0..N-1) every quantity
+    has a closed form: the parent's sd = step*sqrt((N^2-1)/12), Zmin = mean/sd,
+    so meanEst = (j + 0.5) * sd / scale; cluster j holds the i with
+    floor(i*step*scale/sd) = j; the child's sd about m = meanEst - i_lo*step is
+    sqrt(sum_{t<c} (t*step - m)^2 / c).  Computed here in 40-digit decimals."""
+    from decimal import Decimal, getcontext
+
+    getcontext().prec = 40
+    N, step, base = 20000, 7, 2 ** 40
+    keys = np.uint64(base) + np.random.default_rng(0).permutation(N).astype(np.uint64) * np.uint64(step)
+    k_out, v_out, tr, recs = oracle.zsort_pairs_records(keys, inputs.index_payload(N), count_range=0)
+    assert np.all(k_out[:-1] <= k_out[1:])
+    k = int(np.floor(0.6 * np.sqrt(N)))
+    assert tr.k == k
+    D = Decimal
+    scale = D(k) / 4
+    sd_p = D(step) * ((D(N) * N - 1) / 12).sqrt()
+    depth1 = [r for r in recs if r.depth == 1]
+    # every child of the top level with more than 96 keys is recursed once
+    assert len(depth1) >= 60
+    seen = set()
+    for r in depth1:
+        j = r.parent_bucket
+        seen.add(j)
+        est = (D(j) + D("0.5")) * sd_p / scale
+        assert abs(D(r.est_parent_d) - est) <= D("1e-9") * est
+        # the child's keys: i in [i_lo, i_lo + c), all in cluster j of Eq. 1
+        i_lo = (r.min - base) // step
+        assert r.parent_min == base and (r.min - base) % step == 0
+        c = r.size
+        for i in (i_lo, i_lo + c - 1):
+            h = D(i * step) * scale / sd_p
+            # not within rounding distance of an edge (except the key 0 itself)
+            assert int(h) == j and (i == 0 or h - int(h) > D("1e-9")) and int(h) + 1 - h > D("1e-9")
+        if i_lo > 0:
+            assert int(D((i_lo - 1) * step) * scale / sd_p) == j - 1
+        m = est - D(i_lo * step)
+        assert abs(D(r.mean) - m) <= D("1e-9") * abs(m)
+        s1 = D(c) * (c - 1) / 2
+        s2 = D(c - 1) * c * (2 * c - 1) / 6
+        var = (D(step) * step * s2 - 2 * m * step * s1 + c * m * m) / c
+        assert abs(D(r.sd) - var.sqrt()) <= D("1e-9") * var.sqrt()
+        assert abs(D(r.zmin) - abs(m) / var.sqrt()) <= D("1e-9") * (abs(m) / var.sqrt() + 1)
+    assert len(seen) == len(depth1)
+
+
+def _f32(x):
+    """Round a positive Fraction to the nearest binary32 (ties to even);
+    normal range only."""
+    from fractions import Fraction
+
+    assert x > 0
+    e = x.numerator.bit_length() - x.denominator.bit_length()
+    if Fraction(2) ** e > x:
+        e -= 1
+    ulp = Fraction(2) ** (e - 23)
+    q, rem = divmod(x, ulp)
+    if rem * 2 > ulp or (rem * 2 == ulp and q % 2 == 1):
+        q += 1
+    return q * ulp
+
+
+def test_pwl_stored_slope_reading():
+    """R11: inside piece s the learned map takes frac = fl32(fl32(u - q_s) *
+    r_s) with the stored slope r_s = fl32(1 / (q_{s+1} - q_s)), not the
+    quotient fl32((u - q_s) / width).  The case below has a piece of width
+    82 * 2^-24 and a key exactly in its middle: the quotient is 1/2 exactly
+    (bucket 2s + 1 with K = 2), while the rounded slope is below 1/82 * 2^24,
+    so the product falls just short of 1/2 (bucket 2s).  Expected values are
+    computed here in exact rational arithmetic."""
+    from fractions import Fraction
+
+    two24 = 1 << 24
+    P, k = 4, 8  # K = k / P = 2 sub-buckets per piece
+    qi = [0, 100, 182, 1000, two24 - 1]  # breakpoints in units of 2^-24; piece 1 is 82 wide
+    q = np.array([x / two24 for x in qi], dtype=np.float32)
+    mn, mx = 0, two24 - 1  # E = 24: u = key * 2^-24 exactly
+    key = 100 + 41
+    width = Fraction(82, two24)
+    slope = _f32(1 / width)
+    assert slope < two24 / Fraction(82)
+    frac = _f32(Fraction(41, two24) * slope)
+    assert frac < Fraction(1, 2)
+    expect = 1 * 2 + int(frac * 2)
+    quotient_bucket = 1 * 2 + int(Fraction(41, two24) / width * 2)
+    assert (expect, quotient_bucket) == (2, 3)
+    assert oracle.pwl_buckets(np.array([key], dtype=np.uint64), mn, mx, q, k, P=P)[0] == expect
+    # the neighbours on either side land where both readings agree
+    b = oracle.pwl_buckets(np.array([100, 140, 142, 181, 182], dtype=np.uint64), mn, mx, q, k, P=P)
+    assert list(b) == [2, 2, 3, 3, 4]
 
 
 def _exact_stats(keys):
