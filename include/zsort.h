@@ -304,12 +304,12 @@ int zsort_map_buckets(const uint64_t *keys, uint64_t n, const zsort_opts *opts, 
 #define ZSORT_NOALLOC_MAX_N ((uint64_t)1 << 20)
 
 /* zsort_pairs_noalloc -- the sort of zsort_pairs (default options, uint64
- * keys) for callers that cannot allocate device memory: code running while
- * a CUDA graph is being captured, hosts that forbid device allocation after
- * start-up, or processes that must stay inside a fixed memory pool.  The
- * paper has no counterpart; it is a deployment variant.
+ * keys) for callers that cannot allocate device memory: real-time or
+ * embedded hosts that forbid device allocation once they have started, and
+ * processes that must stay inside a fixed memory pool they may not grow.
+ * The paper has no counterpart; it is a deployment variant.
  *   - Allocates nothing: no cudaMalloc/cudaFree and no allocating library
- *     call.  Its scratch is a static __device__ array of about 21 MB for up
+ *     call.  Its scratch is a static __device__ array of about 24 MB for up
  *     to ZSORT_NOALLOC_MAX_N (2^20) elements that every GPU which loads this
  *     library holds until the process exits.  n > ZSORT_NOALLOC_MAX_N is
  *     rejected with ZSORT_ERR_INVALID before anything is enqueued.

@@ -327,19 +327,24 @@ std::vector<Workspace *> g_ws;
 bool g_attr_set[64] = {false};
 const size_t SMEM_BYTES = sizeof(SmemTile);
 
-unsigned long long div_up(unsigned long long a, unsigned long long b) { return (a + b - 1) / b; }
+constexpr unsigned long long div_up(unsigned long long a, unsigned long long b) { return (a + b - 1) / b; }
 
-size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+constexpr size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
-// Capacity plan for calls of up to n elements and nseg segments.
+constexpr unsigned long long min_u64(unsigned long long a, unsigned long long b) { return a < b ? a : b; }
+
+// Capacity plan for calls of up to n elements and nseg segments on a device
+// of `sms` SMs (at most two persistent CTAs each).  The one source of the
+// workspace capacities: the cached workspaces and the static scratch of
+// zsort_pairs_noalloc are both laid out by it.
 struct Plan {
     unsigned long long qcap, segcap, itemcap, statuscap, traincap;
     size_t off_skeys, off_svals, off_ids, off_ctl, off_epoch, off_entries, off_ready, off_tnext, off_tdone, off_segs,
         off_items, off_bstart, off_status, off_pwl, off_train, total;
 };
 
-Plan make_plan(unsigned long long n, unsigned long long nseg, unsigned long long large_min, int sms,
-               unsigned long long chunks_per_cta)
+constexpr Plan make_plan(unsigned long long n, unsigned long long nseg, unsigned long long large_min, int sms,
+                         unsigned long long chunks_per_cta, unsigned long long traincap_max = 32)
 {
     Plan p{};
     p.qcap = n / 128 + 4 * nseg + 4096;
@@ -350,12 +355,11 @@ Plan make_plan(unsigned long long n, unsigned long long nseg, unsigned long long
     // (sub)array; room for two such levels
     const unsigned long long nctas = 2ull * (unsigned long long)(sms > 0 ? sms : 160);
     p.statuscap = 2ull * NB_MAX *
-                  (std::min<unsigned long long>(2 * chunks_per_cta * nctas, n / TILE + 64) +
-                   std::min<unsigned long long>(2 * p.segcap, 16384));
-    p.traincap = std::min<unsigned long long>(p.segcap, 32);
+                  (min_u64(2 * chunks_per_cta * nctas, n / TILE + 64) + min_u64(2 * p.segcap, 16384));
+    p.traincap = min_u64(p.segcap, traincap_max);
     size_t o = 0;
-    auto take = [&](size_t bytes) {
-        size_t r = o;
+    auto take = [&o](size_t bytes) {
+        const size_t r = o;
         o = align_up(o + bytes);
         return r;
     };
@@ -376,6 +380,31 @@ Plan make_plan(unsigned long long n, unsigned long long nseg, unsigned long long
     p.off_train = take(p.traincap * 2 * SAMPLE_MAX * 8);
     p.total = o;
     return p;
+}
+
+// Points a launch's bookkeeping pointers into a block laid out by make_plan.
+void bind_plan(Params &P, char *b, const Plan &p)
+{
+    P.skeys = reinterpret_cast<uint64_t *>(b + p.off_skeys);
+    P.svals = reinterpret_cast<uint32_t *>(b + p.off_svals);
+    P.ids = reinterpret_cast<uint16_t *>(b + p.off_ids);
+    P.ctl = reinterpret_cast<Ctl *>(b + p.off_ctl);
+    P.epoch_ctr = reinterpret_cast<uint32_t *>(b + p.off_epoch);
+    P.entries = reinterpret_cast<Entry *>(b + p.off_entries);
+    P.ready = reinterpret_cast<uint32_t *>(b + p.off_ready);
+    P.tnext = reinterpret_cast<uint32_t *>(b + p.off_tnext);
+    P.tdone = reinterpret_cast<uint32_t *>(b + p.off_tdone);
+    P.qcap = (uint32_t)p.qcap;
+    P.segs = reinterpret_cast<Seg *>(b + p.off_segs);
+    P.segcap = (uint32_t)p.segcap;
+    P.items = reinterpret_cast<Item *>(b + p.off_items);
+    P.itemcap = (uint32_t)p.itemcap;
+    P.bstart = reinterpret_cast<uint32_t *>(b + p.off_bstart);
+    P.status = reinterpret_cast<uint32_t *>(b + p.off_status);
+    P.statuscap = p.statuscap;
+    P.pwl = reinterpret_cast<float *>(b + p.off_pwl);
+    P.trainbuf = reinterpret_cast<unsigned long long *>(b + p.off_train);
+    P.traincap = (uint32_t)p.traincap;
 }
 
 int cuda_err(cudaError_t e)
@@ -436,29 +465,9 @@ int get_workspace(cudaStream_t stream, unsigned long long n, unsigned long long 
         ws->nseg_cap = scap;
         ws->large_min = large_min;
         ws->chunks_cap = ccap;
-        char *b = static_cast<char *>(blk);
         Params &P = ws->P;
         P = Params{};
-        P.skeys = reinterpret_cast<uint64_t *>(b + p.off_skeys);
-        P.svals = reinterpret_cast<uint32_t *>(b + p.off_svals);
-        P.ids = reinterpret_cast<uint16_t *>(b + p.off_ids);
-        P.ctl = reinterpret_cast<Ctl *>(b + p.off_ctl);
-        P.epoch_ctr = reinterpret_cast<uint32_t *>(b + p.off_epoch);
-        P.entries = reinterpret_cast<Entry *>(b + p.off_entries);
-        P.ready = reinterpret_cast<uint32_t *>(b + p.off_ready);
-        P.tnext = reinterpret_cast<uint32_t *>(b + p.off_tnext);
-        P.tdone = reinterpret_cast<uint32_t *>(b + p.off_tdone);
-        P.qcap = (uint32_t)p.qcap;
-        P.segs = reinterpret_cast<Seg *>(b + p.off_segs);
-        P.segcap = (uint32_t)p.segcap;
-        P.items = reinterpret_cast<Item *>(b + p.off_items);
-        P.itemcap = (uint32_t)p.itemcap;
-        P.bstart = reinterpret_cast<uint32_t *>(b + p.off_bstart);
-        P.status = reinterpret_cast<uint32_t *>(b + p.off_status);
-        P.statuscap = p.statuscap;
-        P.pwl = reinterpret_cast<float *>(b + p.off_pwl);
-        P.trainbuf = reinterpret_cast<unsigned long long *>(b + p.off_train);
-        P.traincap = (uint32_t)p.traincap;
+        bind_plan(P, static_cast<char *>(blk), p);
         ws->epoch = 0;
     }
     if (!ws->sms) {
@@ -656,53 +665,22 @@ Workspace *find_ws(cudaStream_t stream)
 }  // namespace
 
 // ---------------------------------------------------------------- no-alloc entry
-// Some callers cannot call cudaMalloc at all: code that runs while a CUDA
-// graph is being captured, real-time or embedded hosts that forbid device
-// allocation after start-up, and processes whose device memory is owned by
-// a pool they may not grow.  zsort_pairs_noalloc serves them: its scratch
-// is one file-scope __device__ array, sized for NA_MAX_N elements and held by
-// every GPU that loads this library until the process exits.
+// Some callers cannot call cudaMalloc at all: real-time or embedded hosts
+// that forbid device allocation once they have started, and processes whose
+// device memory is owned by a fixed pool they may not grow.
+// zsort_pairs_noalloc serves them: its scratch is one file-scope __device__
+// array, sized for NA_MAX_N elements and held by every GPU that loads this
+// library until the process exits.
 namespace {
 
 constexpr unsigned long long NA_MAX_N = ZSORT_NOALLOC_MAX_N;
 constexpr unsigned long long NA_LARGE_MIN = 65536;  // the default large_min
-constexpr size_t na_align(size_t x) { return (x + 255) & ~size_t(255); }
+constexpr unsigned long long NA_CHUNKS = 8;         // the default chunks_per_cta
+constexpr int NA_MAX_SMS = 192;                     // launches use at most 2 x this many CTAs
 
-// Layout of the static scratch: the same regions as a regular workspace for
-// NA_MAX_N elements and one segment, with one learned-map training slot.
-struct NaLayout {
-    unsigned long long qcap, segcap, itemcap, statuscap, traincap;
-    size_t skeys, svals, ids, ctl, epoch, entries, ready, tnext, tdone, segs, items, bstart, status, pwl,
-        train, total;
-};
-constexpr NaLayout na_layout()
-{
-    NaLayout L{};
-    L.qcap = NA_MAX_N / 128 + 4 + 4096;
-    L.segcap = 3 * (NA_MAX_N / (NA_LARGE_MIN + 1)) + 64;
-    L.itemcap = 2 + NA_MAX_N / 32 + 4096;
-    L.statuscap = 4ull * NB_MAX * (NA_MAX_N / (4 * TILE) + 64);
-    L.traincap = 1;
-    size_t o = 0;
-    L.skeys = o; o = na_align(o + NA_MAX_N * 8);
-    L.svals = o; o = na_align(o + NA_MAX_N * 4);
-    L.ids = o; o = na_align(o + NA_MAX_N * 2);
-    L.ctl = o; o = na_align(o + sizeof(Ctl));
-    L.epoch = o; o = na_align(o + 16);
-    L.entries = o; o = na_align(o + QUEUES * L.qcap * sizeof(Entry));
-    L.ready = o; o = na_align(o + QUEUES * L.qcap * 4);
-    L.tnext = o; o = na_align(o + QUEUES * L.qcap * 4);
-    L.tdone = o; o = na_align(o + QUEUES * L.qcap * 4);
-    L.segs = o; o = na_align(o + L.segcap * sizeof(Seg));
-    L.items = o; o = na_align(o + L.itemcap * sizeof(Item));
-    L.bstart = o; o = na_align(o + L.segcap * NB_MAX * 4);
-    L.status = o; o = na_align(o + L.statuscap * 4);
-    L.pwl = o; o = na_align(o + L.segcap * PWL_STRIDE * 4);
-    L.train = o; o = na_align(o + L.traincap * 2 * SAMPLE_MAX * 8);
-    L.total = o;
-    return L;
-}
-constexpr NaLayout NA = na_layout();
+// Layout of the static scratch: make_plan's regions for NA_MAX_N elements and
+// one segment, with one learned-map training slot.
+constexpr Plan NA = make_plan(NA_MAX_N, 1, NA_LARGE_MIN, NA_MAX_SMS, NA_CHUNKS, 1);
 
 // Per-device set-up of the no-alloc path (the symbol's device address).
 struct NaDevice {
@@ -718,6 +696,7 @@ NaDevice g_na_dev[64];
 
 // The scratch itself: zero at module load, reused (not cleared) by every call.
 static __device__ __align__(256) unsigned char g_na_scratch[NA.total];
+static_assert(NA.total < (32ull << 20), "the no-alloc scratch stays modest");
 
 // Copies a call's device status word to the caller's int.
 __global__ void k_na_status(const Ctl *ctl, int32_t *out)
@@ -1068,31 +1047,11 @@ int zsort_pairs_noalloc(uint64_t *keys, uint32_t *vals, uint64_t n, int32_t *sta
     }
     zsort_opts o;
     zsort_default_opts(&o);
-    char *b = D.base;
     Params P{};
     P.ukeys = keys;
     P.uvals = vals;
     P.n = n;
-    P.skeys = reinterpret_cast<uint64_t *>(b + NA.skeys);
-    P.svals = reinterpret_cast<uint32_t *>(b + NA.svals);
-    P.ids = reinterpret_cast<uint16_t *>(b + NA.ids);
-    P.ctl = reinterpret_cast<Ctl *>(b + NA.ctl);
-    P.epoch_ctr = reinterpret_cast<uint32_t *>(b + NA.epoch);
-    P.entries = reinterpret_cast<Entry *>(b + NA.entries);
-    P.ready = reinterpret_cast<uint32_t *>(b + NA.ready);
-    P.tnext = reinterpret_cast<uint32_t *>(b + NA.tnext);
-    P.tdone = reinterpret_cast<uint32_t *>(b + NA.tdone);
-    P.qcap = (uint32_t)NA.qcap;
-    P.segs = reinterpret_cast<Seg *>(b + NA.segs);
-    P.segcap = (uint32_t)NA.segcap;
-    P.items = reinterpret_cast<Item *>(b + NA.items);
-    P.itemcap = (uint32_t)NA.itemcap;
-    P.bstart = reinterpret_cast<uint32_t *>(b + NA.bstart);
-    P.status = reinterpret_cast<uint32_t *>(b + NA.status);
-    P.statuscap = NA.statuscap;
-    P.pwl = reinterpret_cast<float *>(b + NA.pwl);
-    P.trainbuf = reinterpret_cast<unsigned long long *>(b + NA.train);
-    P.traincap = (uint32_t)NA.traincap;
+    bind_plan(P, D.base, NA);
     P.kmax = o.kmax;
     P.leaf_target = o.leaf_target;
     P.large_min = o.large_min;
@@ -1107,7 +1066,8 @@ int zsort_pairs_noalloc(uint64_t *keys, uint32_t *vals, uint64_t n, int32_t *sta
     P.wait_ns = (unsigned long long)o.wait_limit_ms * 1000000ull;
     P.user_aligned = ((reinterpret_cast<uintptr_t>(keys) | reinterpret_cast<uintptr_t>(vals)) & 15u) == 0;
     P.kv = vals != nullptr;  // null vals: keys only
-    P.nctas = (uint32_t)(D.sms * D.occ);
+    // the plan's look-back rows are sized for at most 2 x NA_MAX_SMS CTAs
+    P.nctas = (uint32_t)std::min(D.sms * D.occ, 2 * NA_MAX_SMS);
     ce = cudaMemsetAsync(P.ctl, 0, sizeof(Ctl), st);  // the control block must start at zero
     if (ce != cudaSuccess) return cuda_err(ce);
     k_init_segments<<<1, 256, 0, st>>>(P, nullptr, 1);

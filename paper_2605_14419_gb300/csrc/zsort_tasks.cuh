@@ -1590,7 +1590,10 @@ __device__ __noinline__ void task_lhist(const Params &P, uint32_t sid, uint32_t 
 #pragma unroll
         for (int r = 0; r < PER; r++) all = all && done[r];
         if (all) break;
-        if (!moved && (++spins & 31u) == 0) {
+        if (moved) {  // the limit counts from the last progress, not from the first stall
+            t0 = 0;
+            spins = 0;
+        } else if ((++spins & 31u) == 0) {
             const unsigned long long now = globaltimer();
             if (t0 == 0)
                 t0 = now;
