@@ -98,7 +98,7 @@ enum {
 typedef struct {
     uint32_t struct_size;    /* sizeof(zsort_opts)                            */
     uint32_t mapper;         /* ZSORT_MAP_ZSCORE or ZSORT_MAP_LEARNED          */
-    uint32_t kmax;           /* most buckets per partition, power of 2, 16..1024 */
+    uint32_t kmax;           /* most buckets per partition, power of 2, 16..512 */
     uint32_t leaf_target;    /* k = clamp(pow2ceil(len / leaf_target), 16, kmax) */
     uint32_t large_min;      /* longer (sub)arrays are partitioned by all SMs
                                 with a decoupled look-back; shorter ones by
@@ -152,11 +152,22 @@ typedef struct {
  * 32-byte store per task. */
 #define ZSORT_FLAG_TRACE 4u
 #define ZSORT_TRACE_CAP (1u << 20)
+/* Exact statistics at every level.  By default a large sub-array below the
+ * top level (one that a partition pass produced) takes its Eq. 1 statistics
+ * from ZSORT_SUB_SAMPLE keys at stratified positions instead of a pass over
+ * all its keys: the sub-problems of zsortRec (section "Proposed Work") keep
+ * the top level's map form and estimate its inputs, and the map only has to
+ * be monotone for the sort to be exact.  The top level, sub-arrays that use
+ * the range map (progress guard) or a learned map, and sub-arrays whose
+ * sample keys are all equal always take the exact pass.  This flag makes
+ * every level take it. */
+#define ZSORT_FLAG_EXACT_SUBSTATS 8u
+#define ZSORT_SUB_SAMPLE 4096u
 
 /* One record of the task trace.  type is the task type of zsort_stats.task_ns
  * (1 statistics chunk, 2 learned-map sample run, 3 histogram chunk, 4
  * scatter chunk, 5 single-CTA partition, 6 finish, 7 copy, 8 map inspection,
- * 9 learned-map fit), or ZSORT_TRACE_HANDLER + t for the phase-completion
+ * 9 learned-map fit, 10 sampled statistics), or ZSORT_TRACE_HANDLER + t for the phase-completion
  * work that the last task of a phase of type t ran right after it (the
  * bucket scan after a histogram, the classification of the children after
  * a scatter; count 0).  Times are the device's globaltimer in ns.  A CTA's
@@ -193,7 +204,7 @@ typedef struct {
     uint32_t top_k;             /* top level: buckets                           */
     uint32_t top_map;           /* top level: map used (ZSORT_MAP_*, 2 = range) */
     /* device time of the persistent kernel's tasks, summed over CTAs (ns);
-       index = task type: 1 statistics tile, 2 learned-map training, 3
+       index = task type: 1 statistics tile or sample, 2 learned-map training, 3
        histogram tile, 4 look-back scatter tile, 5 single-CTA partition,
        6 shared-memory finish, 7 copy */
     uint64_t task_ns[8];
@@ -201,6 +212,7 @@ typedef struct {
     uint64_t handler_ns;        /* tasks whose phase-completion work ran (incl.)  */
     uint64_t idle_ns;           /* time CTAs spent waiting for work               */
     uint64_t busy_window_ns;    /* first task start to last task end              */
+    uint64_t sampled_stats;     /* sub-arrays whose statistics came from a sample */
 } zsort_stats;
 
 /* Fills *o with the defaults (z-score map, kmax 512, leaf target 2048, ...). */
@@ -299,6 +311,10 @@ typedef struct {
  * *info.  2 <= n <= ZSORT_MAX_N. */
 int zsort_map_buckets(const uint64_t *keys, uint64_t n, const zsort_opts *opts, uint32_t *buckets,
                       zsort_map_info *info, zsort_stream_t stream);
+
+/* Pairs per streamed tile: the unit in which a large (sub)array is cut into
+ * chunk tasks (each chunk is at least four tiles). */
+#define ZSORT_TILE_PAIRS 3072u
 
 /* Largest n accepted by zsort_pairs_noalloc. */
 #define ZSORT_NOALLOC_MAX_N ((uint64_t)1 << 20)

@@ -8,7 +8,7 @@
  * gives the same, uniquely defined sorted output.
  *
  * Knobs searched (fields of zsort_opts):
- *   kmax            bucket count per partition pass   {256, 512, 1024}
+ *   kmax            bucket count per partition pass   {128, 256, 512}
  *   leaf_target     elements per bucket aimed at       {1024, 2048, 4096}
  *   leaf_cap        small-bucket cutoff (items per thread = leaf_cap / 256)
  *                                                      {2048, 3072, 4096}

@@ -37,9 +37,12 @@ MAX_SEG_TOTAL = 1 << 34
 FLAG_GRAPH = 1
 FLAG_TEST_STALL = 2
 FLAG_TRACE = 4
+FLAG_EXACT_SUBSTATS = 8
+TILE_PAIRS = 3072
+SUB_SAMPLE = 4096
 TRACE_CAP = 1 << 20
 TASK_TYPES = {1: "stats", 2: "train", 3: "hist", 4: "scatter", 5: "mpart", 6: "finish", 7: "copy",
-              8: "dump", 9: "fit"}
+              8: "dump", 9: "fit", 10: "sampled stats"}
 TRACE_HANDLER = 16
 NOALLOC_MAX_N = 1 << 20
 
@@ -100,6 +103,7 @@ class Stats(ctypes.Structure):
         ("handler_ns", ctypes.c_uint64),
         ("idle_ns", ctypes.c_uint64),
         ("busy_window_ns", ctypes.c_uint64),
+        ("sampled_stats", ctypes.c_uint64),
     ]
 
     def as_dict(self) -> dict:

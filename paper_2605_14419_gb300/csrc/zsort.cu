@@ -22,6 +22,8 @@
 #include "zsort_tasks.cuh"
 
 static_assert(sizeof(zsort_trace_rec) == sizeof(zs::TraceRec), "trace record layout");
+static_assert(ZSORT_TILE_PAIRS == zs::TILE, "tile size in the header");
+static_assert(ZSORT_SUB_SAMPLE == zs::SUB_SAMPLE, "sub-array sample size in the header");
 
 using namespace zs;
 
@@ -86,6 +88,7 @@ __global__ void __launch_bounds__(BLOCK, 2) k_persistent(const __grid_constant__
             case T_LSTATS: task_lstats(P, arg, tile, s, pp); break;
             case T_LSAMPLE: task_lsample(P, arg, tile, s); break;
             case T_LFIT: task_lfit(P, arg, s); break;
+            case T_SSTATS: task_sstats(P, arg, s); break;
             case T_LHIST: task_lhist(P, arg, tile, s, pp); break;
             case T_LSCATTER: task_lscatter(P, arg, tile, s, pp); break;
             case T_MPART: task_mpart(P, load_item(P, arg + tile), s, pp); break;
@@ -106,7 +109,9 @@ __global__ void __launch_bounds__(BLOCK, 2) k_persistent(const __grid_constant__
         if (threadIdx.x == 0) {
             const unsigned long long t1 = globaltimer();
             t_task1 = t1;
-            const uint32_t ti = type == T_LFIT ? (uint32_t)T_LSAMPLE : (type & 7u);  // both: learned map
+            // the learned map's fit counts as its training, a sampled
+            // statistics task as statistics
+            const uint32_t ti = type == T_LFIT ? (uint32_t)T_LSAMPLE : type == T_SSTATS ? (uint32_t)T_LSTATS : (type & 7u);
             atomicAdd(&P.ctl->task_ns[ti], t1 - t_task0);
             atomicAdd(&P.ctl->task_cnt[ti], (unsigned long long)count);
             __threadfence();
@@ -122,7 +127,7 @@ __global__ void __launch_bounds__(BLOCK, 2) k_persistent(const __grid_constant__
             case T_LSTATS: lstats_done(P, arg, s); break;
             case T_LHIST: lhist_done(P, arg, s); break;
             case T_LSCATTER: lscatter_done(P, arg, s); break;
-            default: break;  // LSAMPLE and LFIT publish their successors themselves
+            default: break;  // LSAMPLE, LFIT and SSTATS publish their successors themselves
             }
             __syncthreads();
             if (threadIdx.x == 0) {
@@ -551,6 +556,7 @@ int launch(uint64_t *keys, uint32_t *vals, unsigned long long n, const uint64_t 
     P.guard_level = o.guard_level;
     P.leaf_cap = o.leaf_cap;
     P.chunks_per_cta = o.chunks_per_cta;
+    P.sub_sample = (o.flags & ZSORT_FLAG_EXACT_SUBSTATS) ? 0u : 1u;
     P.fallback_ratio = o.fallback_ratio;
     P.seed = o.seed;
     P.wait_ns = (unsigned long long)o.wait_limit_ms * 1000000ull;
@@ -928,6 +934,7 @@ int zsort_last_stats(zsort_stream_t stream, zsort_stats *out)
     out->handler_ns = c.handler_ns;
     out->idle_ns = c.idle_ns;
     out->busy_window_ns = (c.t_last > c.t_first && c.t_first != ~0ull) ? c.t_last - c.t_first : 0;
+    out->sampled_stats = c.n_sampled;
     return ZSORT_OK;
 }
 
@@ -1061,6 +1068,7 @@ int zsort_pairs_noalloc(uint64_t *keys, uint32_t *vals, uint64_t n, int32_t *sta
     P.guard_level = o.guard_level;
     P.leaf_cap = o.leaf_cap;
     P.chunks_per_cta = o.chunks_per_cta;
+    P.sub_sample = 1u;
     P.fallback_ratio = o.fallback_ratio;
     P.seed = o.seed;
     P.wait_ns = (unsigned long long)o.wait_limit_ms * 1000000ull;

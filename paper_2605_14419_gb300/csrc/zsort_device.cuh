@@ -16,15 +16,17 @@ namespace zs {
 // ---------------------------------------------------------------- constants
 constexpr int BLOCK = 256;                // threads per CTA
 constexpr int WARPS = BLOCK / 32;
-constexpr int IPT = 8;                    // items per thread of a streamed tile
-constexpr int TILE = BLOCK * IPT;         // 2048 pairs per streamed tile
+constexpr int IPT = 12;                   // items per thread of a streamed tile
+constexpr int TILE = BLOCK * IPT;         // 3072 pairs per streamed tile
 constexpr int WARP_SPAN = 32 * IPT;       // contiguous elements per warp and tile
 constexpr int LEAF_IPT = 16;              // items per thread of a leaf
 constexpr int LEAF_CAP = BLOCK * LEAF_IPT;  // 4096: a bucket (group) this small is finished in smem
 constexpr int LEAF_SPAN = 32 * LEAF_IPT;
 constexpr int PAD = 8;                    // smem slack for 16-byte aligned bulk copies
-constexpr int NB_MAX = 1024;              // buckets per partition pass
+constexpr int NB_MAX = 512;               // buckets per partition pass
 constexpr int RANK_SMALL = BLOCK;         // leaves this small are ranked by counting
+constexpr int SC_STAGES = 2;              // streamed (key, payload) tile buffers per CTA
+constexpr uint32_t LEAF_M2_MAX = 2048;    // sub-buckets of the fast leaf path
 constexpr int PWL_P = 256;                // pieces of the learned map
 constexpr int SAMPLE_MAX = 65536;         // largest training sample
 constexpr int SAMPLE_RUNS = 8;            // the sample is sorted as this many runs, one CTA each
@@ -56,9 +58,11 @@ enum TaskType : uint32_t {
     T_FINISH = 6,    // leaf (group of small buckets): shared-memory sort
     T_COPY = 7,      // all-equal large segment living in scratch: copy back
     T_DUMP = 8,      // map inspection: bucket of every key of a chunk
-    T_LFIT = 9       // large segment: learned-map breakpoints and load test (one CTA,
+    T_LFIT = 9,      // large segment: learned-map breakpoints and load test (one CTA,
                      // after both the statistics and the sample)
+    T_SSTATS = 10    // large sub-array: statistics and Eq. 1 map from a sample (one CTA)
 };
+constexpr uint32_t SUB_SAMPLE = 4096;     // keys of a sub-array's statistics sample
 
 // ---------------------------------------------------------------- records
 // A large segment: partitioned by many CTAs, phase by phase.
@@ -126,6 +130,7 @@ struct Ctl {
     unsigned long long task_ns[8], task_cnt[8], handler_ns, idle_ns;
     unsigned long long t_first, t_last;
     unsigned long long trace_n;    // task records written (or attempted) to the trace
+    unsigned long long n_sampled;  // sub-arrays whose statistics came from a sample
 };
 
 // Trace type of the phase-completion work a task triggered (type | this).
@@ -173,6 +178,7 @@ struct Params {
     // options
     uint32_t kmax, leaf_target, large_min, learn_min, sample, mapper, guard_level;
     uint32_t leaf_cap, chunks_per_cta;
+    uint32_t sub_sample;         // 1: large sub-arrays below the top take sampled statistics
     float fallback_ratio;
     unsigned long long seed;
     unsigned long long wait_ns;
@@ -541,8 +547,14 @@ __device__ __forceinline__ uint32_t map_key(const MapK &r, const MapSm &m, unsig
     const unsigned long long d = key - r.mn;
     if (r.kind == MAP_Z) {
         // Eq. 1 with |z_min| = (mean - min)/sd: h = (key - min) * (k/4) / sd,
-        // on d >> zsh (a 32-bit value; zc carries the 2^zsh back).
-        const float f = __fmul_rn(__uint2float_rz((uint32_t)(d >> r.zsh)), r.zc);
+        // on d >> zsh (a 32-bit value; zc carries the 2^zsh back).  Keys
+        // below mn go to bucket 0 and shifted values above 32 bits saturate
+        // (statistics from a sample need not bound every key); both clamps
+        // keep the map monotone, and neither acts when mn and the shift come
+        // from the exact min and max.
+        const unsigned long long e = key > r.mn ? d >> r.zsh : 0ull;
+        const uint32_t e32 = e > 0xffffffffull ? 0xffffffffu : (uint32_t)e;
+        const float f = __fmul_rn(__uint2float_rz(e32), r.zc);
         const uint32_t b = __float2uint_rz(f);
         return b < r.k ? b : r.k - 1;
     }
@@ -626,6 +638,7 @@ struct ChildList {
     uint32_t med_off[NB_MAX], med_len[NB_MAX];
     uint32_t lg_off[NB_MAX], lg_len[NB_MAX], lg_need[NB_MAX], lg_slot[NB_MAX];
     uint32_t lg_chunks[NB_MAX], lg_k[NB_MAX];  // chunks, buckets
+    uint32_t lg_sampled[NB_MAX];               // statistics from a sample
 };
 
 struct TileBuf {
@@ -636,6 +649,13 @@ struct LeafBuf {
     unsigned long long key[LEAF_CAP + 2 * PAD];
     uint32_t val[LEAF_CAP + 2 * PAD];
 };
+// A leaf: its pairs, the leaf position of each staged pair (also the index
+// array of the sorting network), and the sub-bucket counters.
+struct LeafArea {
+    LeafBuf leaf;
+    uint16_t sidx[LEAF_CAP];
+    uint32_t cnt[LEAF_M2_MAX + 1];
+};
 
 constexpr int KEY_STAGES = 3;  // key-only streams: tiles in flight per CTA
 struct KeyRing {
@@ -644,13 +664,13 @@ struct KeyRing {
 
 struct SmemTile {
     union {
-        TileBuf buf[2];   // double-buffered streamed tiles (bulk-copy targets)
+        TileBuf buf[SC_STAGES];  // ring of streamed tiles (bulk-copy targets)
         KeyRing ring;     // key-only streams: three stages of keys
-        LeafBuf leaf;     // one leaf of up to LEAF_CAP pairs
+        LeafArea la;      // one leaf of up to LEAF_CAP pairs
         ChildList children;
     } u;
-    uint16_t bkt[LEAF_CAP];          // bucket of each staged element / bitonic index
-    __align__(16) uint16_t wcnt[NB_MAX * WARPS];  // [bucket][warp] counts, then warp prefixes
+    uint16_t bkt[TILE];              // bucket of each staged element
+    __align__(16) uint16_t wcnt[WARPS * NB_MAX];  // [warp][bucket] counts, then warp prefixes
     uint32_t tcount[NB_MAX];         // tile count per bucket
     uint32_t tstart[NB_MAX];         // tile-local exclusive start per bucket
     uint32_t gdelta[NB_MAX];         // global position - tile position (mod 2^32)
@@ -665,9 +685,12 @@ struct SmemTile {
     uint32_t flag, flag2, n_leaf, n_med, n_large, n_large_ok, item_base, e_base, span_max;
     unsigned long long red64[WARPS * 2];
 };
-static_assert(sizeof(LeafBuf) <= sizeof(TileBuf) * 2, "leaf fits the tile buffers");
-static_assert(sizeof(KeyRing) <= sizeof(TileBuf) * 2, "the key stages fit the tile buffers");
-static_assert(sizeof(ChildList) <= sizeof(TileBuf) * 2, "child lists fit the tile buffers");
+static_assert(SC_STAGES <= KEY_STAGES, "one mbarrier per streamed tile buffer");
+static_assert(sizeof(LeafArea) <= sizeof(TileBuf) * SC_STAGES, "a leaf fits the tile buffers");
+static_assert(sizeof(KeyRing) <= sizeof(TileBuf) * SC_STAGES, "the key stages fit the tile buffers");
+static_assert(sizeof(ChildList) <= sizeof(TileBuf) * SC_STAGES, "child lists fit the tile buffers");
+static_assert(sizeof(SmemTile) <= 112 * 1024, "two CTAs per SM");
+static_assert(IPT % 2 == 0, "the statistics loop takes the slots in pairs");
 
 // ------------------------------------------------------------ block scan
 // Exclusive scan of in[0..nb) into out (may alias); returns the total.
@@ -716,6 +739,41 @@ __device__ uint32_t block_exclusive_scan(const uint32_t *in, uint32_t *out, uint
     return total;
 }
 
+// In-place exclusive scan of a[0..nb) that keeps no partial sums in
+// registers (each thread re-reads its own run of entries); returns the total.
+__device__ uint32_t block_exclusive_scan_inplace(uint32_t *a, uint32_t nb, uint32_t *wsum)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t per = (nb + BLOCK - 1) / BLOCK;
+    const uint32_t base = threadIdx.x * per;
+    const uint32_t end = min(base + per, nb);
+    uint32_t sum = 0;
+    for (uint32_t idx = base; idx < end; idx++) sum += a[idx];
+    uint32_t x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    uint32_t wofs = 0, total = 0;
+#pragma unroll
+    for (int w = 0; w < WARPS; w++) {
+        const uint32_t ws = wsum[w];
+        wofs += w < warp ? ws : 0u;
+        total += ws;
+    }
+    uint32_t run = wofs + x - sum;
+    for (uint32_t idx = base; idx < end; idx++) {
+        const uint32_t v = a[idx];
+        a[idx] = run;
+        run += v;
+    }
+    __syncthreads();
+    return total;
+}
+
 // ------------------------------------------------------------ tile ranking
 // Stable multisplit of one tile of N = BLOCK * NI elements, cnt of them
 // valid.  Element (warp w, slot i, lane l) is the tile's element
@@ -730,7 +788,9 @@ __device__ uint32_t block_exclusive_scan(const uint32_t *in, uint32_t *out, uint
 // The ranking in steps, so that a tile loop can place its own barriers:
 //   rank_peers    (registers)  lanes of the warp with an equal bucket, per slot
 //   rank_leaders  (smem)       the group leader reads and advances the warp's
-//                              counter of the bucket; wcnt must start at zero
+//                              counter of the bucket (row warp of wcnt, so the
+//                              leaders of one slot spread over the banks);
+//                              wcnt must start at zero
 //   -- barrier --
 //   rank_scan                  per bucket: exclusive prefix over the warps
 //                              (written back into wcnt), tile count, and the
@@ -772,7 +832,7 @@ __device__ __forceinline__ void rank_leaders(const uint32_t (&b)[NI], const uint
         const int leader = valid ? __ffs(peers[i]) - 1 : lane;
         uint32_t before = 0;
         if (valid && lane == leader) {
-            uint16_t *c = s.wcnt + b[i] * WARPS + warp;
+            uint16_t *c = s.wcnt + warp * NB_MAX + b[i];
             before = *c;
             *c = (uint16_t)(before + __popc(peers[i]));
         }
@@ -786,10 +846,8 @@ __device__ __forceinline__ void rank_leaders(const uint32_t (&b)[NI], const uint
 template <bool SCATTER>
 __device__ __forceinline__ void rank_scan(uint32_t nb, SmemTile &s)
 {
-    static_assert(WARPS == 8, "per-bucket warp counters are packed in 16 bytes");
     constexpr int MAXPER = NB_MAX / BLOCK;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint4 *w4 = reinterpret_cast<uint4 *>(s.wcnt);
     const uint32_t per = nb >= (uint32_t)BLOCK ? nb / BLOCK : 1u;
     const uint32_t q0 = threadIdx.x * per;
     uint32_t tot[MAXPER], loc[MAXPER];
@@ -799,14 +857,18 @@ __device__ __forceinline__ void rank_scan(uint32_t nb, SmemTile &s)
         tot[j] = 0;
         loc[j] = sum;
         if ((uint32_t)j < per && q0 + j < nb) {
-            const uint4 c = w4[q0 + j];
-            const uint32_t c0 = c.x & 0xffffu, c1 = c.x >> 16, c2 = c.y & 0xffffu, c3 = c.y >> 16;
-            const uint32_t c4 = c.z & 0xffffu, c5 = c.z >> 16, c6 = c.w & 0xffffu, c7 = c.w >> 16;
-            const uint32_t p1 = c0, p2 = p1 + c1, p3 = p2 + c2, p4 = p3 + c3, p5 = p4 + c4, p6 = p5 + c5,
-                           p7 = p6 + c6;
-            w4[q0 + j] = make_uint4(p1 << 16, p2 | (p3 << 16), p4 | (p5 << 16), p6 | (p7 << 16));
-            tot[j] = p7 + c7;
-            sum += tot[j];
+            // column q of the [warp][bucket] counters: the warps' counts,
+            // replaced by their exclusive prefix over the warps
+            uint32_t run = 0;
+#pragma unroll
+            for (int w = 0; w < WARPS; w++) {
+                uint16_t *c = s.wcnt + w * NB_MAX + q0 + j;
+                const uint32_t v = *c;
+                *c = (uint16_t)run;
+                run += v;
+            }
+            tot[j] = run;
+            sum += run;
         }
     }
     uint32_t x = sum;
@@ -844,15 +906,17 @@ __device__ __forceinline__ void rank_place(const uint32_t (&b)[NI], uint32_t (&p
     const int warp = threadIdx.x >> 5;
 #pragma unroll
     for (int i = 0; i < NI; i++)
-        if (pos[i] != INVALID) pos[i] += s.tstart[b[i]] + s.wcnt[b[i] * WARPS + warp];
+        if (pos[i] != INVALID) pos[i] += s.tstart[b[i]] + s.wcnt[warp * NB_MAX + b[i]];
 }
 
-// Zeroes this warp's counter of every bucket (its own column of wcnt).
+// Zeroes this warp's counter of every bucket (its own row of wcnt, eight
+// counters per 16-byte store; nb is a multiple of 8).
 __device__ __forceinline__ void rank_zero_warp(uint32_t nb, SmemTile &s)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint4 *row = reinterpret_cast<uint4 *>(s.wcnt + warp * NB_MAX);
     __syncwarp();
-    for (uint32_t q = lane; q < nb; q += 32) s.wcnt[q * WARPS + warp] = 0;
+    for (uint32_t q = lane; q < nb / 8; q += 32) row[q] = make_uint4(0u, 0u, 0u, 0u);
     __syncwarp();
 }
 
@@ -861,8 +925,7 @@ __device__ __forceinline__ void rank_zero_warp(uint32_t nb, SmemTile &s)
 template <int NI, int NBITS>
 __device__ void tile_rank(const uint32_t (&b)[NI], uint32_t (&pos)[NI], uint32_t nb, uint32_t cnt, SmemTile &s)
 {
-    uint4 *w4 = reinterpret_cast<uint4 *>(s.wcnt);
-    for (uint32_t q = threadIdx.x; q < nb; q += BLOCK) w4[q] = make_uint4(0u, 0u, 0u, 0u);
+    rank_zero_warp(nb, s);
     __syncthreads();
     uint32_t peers[NI];
     rank_peers<NI, NBITS>(b, cnt, peers);

@@ -602,9 +602,11 @@ __device__ __noinline__ void hist_stream(const Params &P, SmemTile &s, Pipe &pp,
 // pairs by (bucket, position) with ballots, stage them in that order in the
 // tile's own buffer with their buckets, then write each bucket's run at its
 // cursor (coalesced within runs; a staged bucket is cheaper to read back
-// than any map is to recompute).  Four barriers a tile: the
-// tile's bulk copy is issued once every thread has left the tile that last
-// used its buffer, and each warp clears its own bucket counters.
+// than any map is to recompute).  Tiles stream through a ring of SC_STAGES
+// buffers: once every thread has left tile t - 1 (the first of the tile's
+// four barriers), its buffer takes the bulk copy of tile t + SC_STAGES - 1,
+// which streams in while tile t is ranked, staged and written.  Each warp
+// clears its own bucket counters.
 template <int NBITS, bool IDS, bool KV>
 __device__ __noinline__ void scatter_stream(const Params &P, SmemTile &s, Pipe &pp, const uint64_t *srck,
                                             const uint32_t *srcv, bool bulk, unsigned long long start,
@@ -618,14 +620,18 @@ __device__ __noinline__ void scatter_stream(const Params &P, SmemTile &s, Pipe &
     // the runs written per tile end inside lines that the next tile (or the
     // neighbouring chunk) completes: keep those lines in L2 until then
     const unsigned long long pol_front = policy_evict_last();
+    auto tile_cnt = [&](uint32_t t) {
+        return (uint32_t)min((unsigned long long)TILE, len - (unsigned long long)t * TILE);
+    };
     rank_zero_warp(k, s);
     if (bulk && threadIdx.x == 0)
-        stream_issue<KV>(P, s, 0, srck, srcv, start, (uint32_t)min(len, (unsigned long long)TILE));
+        for (uint32_t t = 0; t < SC_STAGES - 1 && t < nt; t++)
+            stream_issue<KV>(P, s, (int)t, srck, srcv, start + (unsigned long long)t * TILE, tile_cnt(t));
     bool err = false;
     for (uint32_t t = 0; t < nt; t++) {
-        const int w = t & 1;
+        const int w = (int)(t % SC_STAGES);
         const unsigned long long a = start + (unsigned long long)t * TILE;
-        const uint32_t cnt = (uint32_t)min((unsigned long long)TILE, len - (unsigned long long)t * TILE);
+        const uint32_t cnt = tile_cnt(t);
         unsigned long long *sk;
         uint32_t *sv;
         bool ok = true;
@@ -669,15 +675,23 @@ __device__ __noinline__ void scatter_stream(const Params &P, SmemTile &s, Pipe &
         rank_leaders<IPT>(b, peers, pos, s);
         // every thread has left the previous tile: its buffer may be refilled
         if (__syncthreads_or(!ok)) {
-            // a copy did not complete in time: give it one more bounded wait
-            // before leaving, so that no copy lands in a reused buffer
-            mbar_wait(&s.bar[w], (pp.uses[w] - 1u) & 1u, P.wait_ns);
+            // a copy did not complete in time: give every copy that may still
+            // be in flight (this tile's and the next ones') one more bounded
+            // wait before leaving, so that no copy lands in a reused buffer
+            if (bulk) {
+                mbar_wait(&s.bar[w], (pp.uses[w] - 1u) & 1u, P.wait_ns);
+                for (uint32_t tn = t + 1; tn < nt && tn < t + SC_STAGES - 1; tn++) {
+                    const int wn = (int)(tn % SC_STAGES);
+                    mbar_wait(&s.bar[wn], pp.uses[wn] & 1u, P.wait_ns);
+                }
+            }
             err = true;
             break;
         }
-        if (bulk && t + 1 < nt && threadIdx.x == 0) {
-            const unsigned long long an = a + TILE;
-            stream_issue<KV>(P, s, w ^ 1, srck, srcv, an, (uint32_t)min((unsigned long long)TILE, start + len - an));
+        if (bulk && t + SC_STAGES - 1 < nt && threadIdx.x == 0) {
+            const uint32_t tn = t + SC_STAGES - 1;
+            stream_issue<KV>(P, s, (int)(tn % SC_STAGES), srck, srcv, start + (unsigned long long)tn * TILE,
+                             tile_cnt(tn));
         }
         rank_scan<true>(k, s);
         rank_place<IPT>(b, pos, s);
@@ -727,16 +741,14 @@ __device__ __forceinline__ void scatter_pick(const Params &P, SmemTile &s, Pipe 
     if (ids) {  // learned: buckets from the histogram pass; k >= 256
         switch (rank_bits(k)) {
         case 8: scatter_stream<8, true, KV>(P, s, pp, srck, srcv, bulk, start, len, dstk, dstv, seglen); break;
-        case 9: scatter_stream<9, true, KV>(P, s, pp, srck, srcv, bulk, start, len, dstk, dstv, seglen); break;
-        default: scatter_stream<10, true, KV>(P, s, pp, srck, srcv, bulk, start, len, dstk, dstv, seglen); break;
+        default: scatter_stream<9, true, KV>(P, s, pp, srck, srcv, bulk, start, len, dstk, dstv, seglen); break;
         }
         return;
     }
     switch (rank_bits(k)) {
     case 7: scatter_stream<7, false, KV>(P, s, pp, srck, srcv, bulk, start, len, dstk, dstv, seglen); break;
     case 8: scatter_stream<8, false, KV>(P, s, pp, srck, srcv, bulk, start, len, dstk, dstv, seglen); break;
-    case 9: scatter_stream<9, false, KV>(P, s, pp, srck, srcv, bulk, start, len, dstk, dstv, seglen); break;
-    default: scatter_stream<10, false, KV>(P, s, pp, srck, srcv, bulk, start, len, dstk, dstv, seglen); break;
+    default: scatter_stream<9, false, KV>(P, s, pp, srck, srcv, bulk, start, len, dstk, dstv, seglen); break;
     }
 }
 
@@ -910,6 +922,9 @@ __device__ __noinline__ void classify_children(const Params &P, unsigned long lo
         S->range_map = 2ull * len > plen;
         const uint32_t slot = S->range_map ? INVALID : take_train_slot(P, len, S->k, child_level);
         S->train_slot = slot;
+        // Eq. 1 sub-arrays take their statistics from a sample (the range
+        // map and the learned map keep the exact pass)
+        L.lg_sampled[g] = P.sub_sample && !S->range_map && slot == INVALID && child_level < P.guard_level;
         S->join = 2;
         S->runs_left = SAMPLE_RUNS;
         S->max_learned = S->max_z = 0;
@@ -946,8 +961,12 @@ __device__ __noinline__ void classify_children(const Params &P, unsigned long lo
     __syncthreads();
     const uint32_t e = (uint32_t)s.red64[2], nsample = (uint32_t)s.red64[3], cnt = (uint32_t)(s.red64[3] >> 32);
     if (e != INVALID) {
-        for (uint32_t g = threadIdx.x; g < nok; g += BLOCK)
-            q_write(P, e + nsample + g, T_LSTATS, sid0 + g, L.lg_chunks[g]);
+        for (uint32_t g = threadIdx.x; g < nok; g += BLOCK) {
+            if (L.lg_sampled[g])
+                q_write(P, e + nsample + g, T_SSTATS, sid0 + g, 1);
+            else
+                q_write(P, e + nsample + g, T_LSTATS, sid0 + g, L.lg_chunks[g]);
+        }
         __threadfence();
         __syncthreads();
         const uint32_t ep = call_epoch(P);
@@ -1093,6 +1112,70 @@ __device__ __noinline__ void lstats_done(const Params &P, uint32_t sid, SmemTile
         } else {
             publish1(P, next, sid, nt);
         }
+    }
+}
+
+// ------------------------------------------------------------ SSTATS
+// Statistics of a large sub-array from a sample.  zsortRec (section
+// "Proposed Work") keeps the top level's map form on every sub-problem and
+// estimates its inputs (meanEst) instead of computing them; here a sub-array
+// below the top takes min, max, mean and sd from SUB_SAMPLE keys at
+// stratified positions (exact sums of the sample, as the statistics pass
+// computes them), which replaces its whole statistics pass.  Eq. 1 then
+// clamps keys outside the sampled [min, max] (map_key), so the map stays
+// monotone on every key and the sort stays exact; the sampled min is below
+// the sampled max, so the map still splits the sub-array.  A sample whose
+// keys are all equal says nothing about the others: then the exact
+// statistics pass runs after all.  Also clears the look-back rows, which the
+// statistics chunks clear otherwise.
+__device__ __noinline__ void task_sstats(const Params &P, uint32_t sid, SmemTile &s)
+{
+    Seg *S = &P.segs[sid];
+    const unsigned long long off = __ldcg(&S->off), sbase = __ldcg(&S->status_base);
+    const uint32_t len = __ldcg(&S->len), buf = __ldcg(&S->buf), k = __ldcg(&S->k);
+    const uint32_t chunks = __ldcg(&S->chunks), level = __ldcg(&S->level);
+    for (uint32_t q = threadIdx.x; q < chunks * k; q += BLOCK) __stcg(P.status + sbase + q, 0u);
+    const uint32_t m = min(SUB_SAMPLE, len);
+    const unsigned long long seed = P.seed + ((unsigned long long)sid << 32);
+    const uint64_t *src = keys_of(P, buf) + off;
+    constexpr int U = (SUB_SAMPLE + BLOCK - 1) / BLOCK;  // independent loads in flight per thread
+    unsigned long long x[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        const uint32_t i = threadIdx.x + u * BLOCK;
+        x[u] = i < m ? __ldcg(src + sample_pos(seed, len, m, i)) : 0ull;
+    }
+    LAcc la;
+    lacc_init(la);
+#pragma unroll
+    for (int u = 0; u < U; u++)
+        if (threadIdx.x + u * BLOCK < m) lacc_key(la, x[u]);
+    Acc a = lacc_sums(la);
+    acc_block_reduce(a, s.acc);
+    if (threadIdx.x == 0) {
+        atomicAdd(&P.ctl->bytes, 8ull * m);
+        if (a.mn == a.mx) {  // no spread in the sample: the exact pass decides
+            publish1(P, T_LSTATS, sid, chunks);
+            return;
+        }
+        unsigned long long s1[2] = {(unsigned long long)a.s1, (unsigned long long)(a.s1 >> 64)};
+        unsigned long long s2[3] = {(unsigned long long)a.s2lo, (unsigned long long)(a.s2lo >> 64), a.s2hi};
+        MapSm mp;
+        double mean_d, sd;
+        map_from_sums(P, m, a.mn, a.mx, s1, s2, k, level, false, mp, &mean_d, &sd);
+        S->mn = a.mn;
+        S->mx = a.mx;
+        S->mean_d = mean_d;
+        S->sd = sd;
+        S->kind = mp.kind;
+        S->zc = mp.zc;
+        S->zsh = mp.zsh;
+        S->escale = mp.escale;
+        S->rshift = mp.rshift;
+        S->rmult = mp.rmult;
+        atomicAdd(&P.ctl->n_sampled, 1ull);
+        __threadfence();  // the map before the histogram tasks are published
+        publish1(P, T_LHIST, sid, chunks);
     }
 }
 
@@ -1779,16 +1862,17 @@ __device__ bool insertion_sort_budget(unsigned long long *k, uint32_t *v, uint32
 __device__ void bitonic_range(SmemTile &s, unsigned long long *key, uint32_t *val, uint32_t a, uint32_t c)
 {
     const uint32_t L = pow2ceil32(c);
-    for (uint32_t i = threadIdx.x; i < c; i += BLOCK) s.bkt[a + i] = (uint16_t)i;
+    uint16_t *ix = s.u.la.sidx;  // current position of each item (the tie-break)
+    for (uint32_t i = threadIdx.x; i < c; i += BLOCK) ix[a + i] = (uint16_t)i;
     __syncthreads();
     auto cmpswap = [&](uint32_t i, uint32_t j) {
         const unsigned long long ki = key[a + i], kj = key[a + j];
-        const uint16_t ii = s.bkt[a + i], ij = s.bkt[a + j];
+        const uint16_t ii = ix[a + i], ij = ix[a + j];
         if (ki > kj || (ki == kj && ii > ij)) {
             key[a + i] = kj;
             key[a + j] = ki;
-            s.bkt[a + i] = ij;
-            s.bkt[a + j] = ii;
+            ix[a + i] = ij;
+            ix[a + j] = ii;
             const uint32_t tv = val[a + i];
             val[a + i] = val[a + j];
             val[a + j] = tv;
@@ -1821,7 +1905,6 @@ __device__ __forceinline__ uint32_t leaf_sub(unsigned long long key, unsigned lo
     return rm == 0 ? (uint32_t)d : __umulhi((uint32_t)(d >> rs), rm);
 }
 
-constexpr uint32_t LEAF_M2_MAX = 2048;  // sub-buckets of the fast leaf path
 constexpr uint32_t LEAF_FAST_MAX = 32;  // largest sub-bucket the fast path ranks by counting
 
 // Fast leaf path.  Every thread holds its pairs (leaf positions threadIdx.x +
@@ -1838,8 +1921,8 @@ __device__ __forceinline__ void finish_fast(SmemTile &s, unsigned long long *key
                                          const unsigned long long (&kk)[LEAF_IPT], const uint32_t (&vv)[LEAF_IPT],
                                          const uint32_t (&a)[LEAF_IPT], uint64_t *dk, uint32_t *dv)
 {
-    uint32_t *cnt = reinterpret_cast<uint32_t *>(s.wcnt);
-    uint16_t *sidx = s.bkt;  // leaf position of each staged pair
+    uint32_t *cnt = s.u.la.cnt;
+    uint16_t *sidx = s.u.la.sidx;  // leaf position of each staged pair
     if (threadIdx.x == 0) cnt[M2] = len;  // sentinel: end of the last sub-bucket
     block_exclusive_scan<LEAF_M2_MAX / BLOCK>(cnt, cnt, M2, s.wsum);
 #pragma unroll
@@ -1898,7 +1981,7 @@ __device__ __noinline__ void finish_stable(const Params &P, SmemTile &s, unsigne
         v[i] = p < len ? val[p] : 0u;
         b[i] = p < len ? leaf_sub(x[i], mn, rshift, rmult) : 0u;
     }
-    tile_rank<LEAF_IPT, 10>(b, pos, M, len, s);
+    tile_rank<LEAF_IPT, 9>(b, pos, M, len, s);
 #pragma unroll
     for (int i = 0; i < LEAF_IPT; i++) {
         if (pos[i] != INVALID) {
@@ -1968,11 +2051,11 @@ __device__ __noinline__ void task_finish(const Params &P, const Item it, SmemTil
             const uint32_t bk = a1 > a0 ? (uint32_t)(a1 - a0) * 8u : 0u;
             const uint32_t bv = KV && b1 > b0 ? (uint32_t)(b1 - b0) * 4u : 0u;
             mbar_expect_arrive(&s.bar[0], bk + bv);
-            if (bk) bulk_g2s(s.u.leaf.key, srck + a0, bk, &s.bar[0]);
-            if (bv) bulk_g2s(s.u.leaf.val, srcv + b0, bv, &s.bar[0]);
+            if (bk) bulk_g2s(s.u.la.leaf.key, srck + a0, bk, &s.bar[0]);
+            if (bv) bulk_g2s(s.u.la.leaf.val, srcv + b0, bv, &s.bar[0]);
         }
-        key = s.u.leaf.key + (off & 1ull);
-        val = s.u.leaf.val + (off & 3ull);
+        key = s.u.la.leaf.key + (off & 1ull);
+        val = s.u.la.leaf.val + (off & 3ull);
         const bool ok = mbar_wait(&s.bar[0], pp.uses[0] & 1u, P.wait_ns);
         pp.uses[0]++;
         if (__syncthreads_or(!ok)) {  // CTA-uniform: every thread leaves together
@@ -1987,8 +2070,8 @@ __device__ __noinline__ void task_finish(const Params &P, const Item it, SmemTil
             for (unsigned long long e = max(off, P.n & ~3ull) + threadIdx.x; e < end; e += BLOCK)
                 val[e - off] = __ldcg(srcv + e);
     } else {
-        key = s.u.leaf.key;
-        val = s.u.leaf.val;
+        key = s.u.la.leaf.key;
+        val = s.u.la.leaf.val;
         for (uint32_t i = threadIdx.x; i < len; i += BLOCK) {
             key[i] = __ldcg(srck + off + i);
             if (KV) val[i] = __ldcg(srcv + off + i);
@@ -2010,7 +2093,7 @@ __device__ __noinline__ void task_finish(const Params &P, const Item it, SmemTil
         }
     }
     const uint32_t M2 = min(LEAF_M2_MAX, pow2ceil32(len) / 2);
-    uint32_t *cnt = reinterpret_cast<uint32_t *>(s.wcnt);
+    uint32_t *cnt = s.u.la.cnt;
     for (uint32_t q = threadIdx.x; q < M2; q += BLOCK) cnt[q] = 0u;
 #pragma unroll
     for (int o = 16; o; o >>= 1) {

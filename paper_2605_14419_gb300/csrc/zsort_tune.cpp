@@ -32,7 +32,7 @@ struct Knob {
 std::vector<Knob> knobs()
 {
     return {
-        {"kmax", &zsort_opts::kmax, {256, 512, 1024}},
+        {"kmax", &zsort_opts::kmax, {128, 256, 512}},
         {"leaf_target", &zsort_opts::leaf_target, {1024, 2048, 4096}},
         {"leaf_cap", &zsort_opts::leaf_cap, {2048, 3072, 4096}},
         {"large_min", &zsort_opts::large_min, {32768, 65536, 131072, 262144}},
@@ -43,7 +43,7 @@ std::vector<Knob> knobs()
 // Range checks of the five tuned fields (as the library validates them).
 bool tuned_fields_valid(const zsort_opts &o)
 {
-    if (o.kmax < 16 || o.kmax > 1024 || (o.kmax & (o.kmax - 1))) return false;
+    if (o.kmax < 16 || o.kmax > 512 || (o.kmax & (o.kmax - 1))) return false;
     if (o.leaf_target < 16 || o.leaf_target > (1u << 24)) return false;
     if (o.leaf_cap < 256 || o.leaf_cap > 4096) return false;
     if (o.large_min < 4096 || o.large_min >= (1u << 30)) return false;

@@ -196,7 +196,7 @@ def test_learned_map_buckets_bit_exact(gen):
     load-test numbers the device reports."""
     n, m = 400_000, 65536
     keys, kd = _map_case(gen, n, 13)
-    opts = z.default_opts(mapper=z.MAP_LEARNED, learn_min=m, sample=m, kmax=1024)
+    opts = z.default_opts(mapper=z.MAP_LEARNED, learn_min=m, sample=m, kmax=512)
     gb, info = z.map_buckets(kd, opts)
     mn, mx = int(keys.min()), int(keys.max())
     assert info.min == mn and info.max == mx
@@ -350,7 +350,7 @@ def test_mlp_map_bit_exact(gen):
     order); a rejected map is checked by the load-test rule."""
     n, m = 400_000, 65536
     keys, kd = _map_case(gen, n, 23)
-    opts = z.default_opts(mapper=z.MAP_MLP, learn_min=m, sample=m, kmax=1024)
+    opts = z.default_opts(mapper=z.MAP_MLP, learn_min=m, sample=m, kmax=512)
     gb, info = z.map_buckets(kd, opts)
     mn, mx = int(keys.min()), int(keys.max())
     assert info.trained == 1
@@ -493,3 +493,58 @@ def test_leaf_with_interleaved_repeated_keys_takes_the_network():
     assert np.array_equal(k.cpu().numpy().view(np.uint64), ok)
     assert np.array_equal(v.cpu().numpy().view(np.uint32), ov)
     assert fb > 0
+
+
+def _child_stress(n_bulk, n_run, n_out, seed):
+    """Uniform keys over [0, 2^40) plus, inside one top-level bucket, a run
+    of n_run copies of one value V with a few distinct keys right beside it
+    and a few far outliers on both sides (still below the next bucket),
+    shuffled: the sub-array of that bucket is large, its 4096-key sample
+    sees V alone or a narrow spread, and its true min and max lie outside
+    what the sample saw."""
+    rng = np.random.default_rng(seed)
+    V = 10 ** 11
+    bulk = rng.integers(0, 2 ** 40, n_bulk, dtype=np.uint64)
+    run = np.full(n_run, V, dtype=np.uint64)
+    near = (V + rng.integers(1, 1000, n_out)).astype(np.uint64)
+    far = np.array([V - 500, V - 499, V + 10 ** 6, V + 10 ** 6 + 1][: max(2, n_out)], dtype=np.uint64)
+    keys = np.concatenate([bulk, run, near, far])
+    return keys[rng.permutation(keys.size)]
+
+
+@pytest.mark.parametrize("n_run,n_out", [(300_000, 3), (300_000, 0), (150_000, 40)])
+def test_sampled_substats_with_unseen_extremes(n_run, n_out):
+    """Sub-array statistics from a sample: a sample without spread falls
+    back to the exact pass, and keys outside the sampled [min, max] are
+    clamped into the end buckets; the output is the oracle's in every case,
+    and the same as with exact statistics at every level."""
+    keys = _child_stress(1_000_000, n_run, n_out, 7 + n_run + n_out)
+    vals = inputs.index_payload(keys.size)
+    ok_k, ok_v = oracle.zsort_pairs(keys, vals)
+    for flags in (0, z.FLAG_EXACT_SUBSTATS):
+        k, v = gpu_sort(keys, vals, z.default_opts(flags=flags))
+        assert np.array_equal(k, ok_k) and np.array_equal(v, ok_v)
+
+
+@pytest.mark.parametrize("gen", [inputs.uniform, inputs.lognormal, inputs.zipf, inputs.nearly_sorted])
+def test_sampled_substats_count_and_bytes(gen):
+    """Two partition levels: the second level's sub-arrays take sampled
+    statistics (counted in zsort_stats.sampled_stats), which saves their
+    8 B/pair statistics pass; ZSORT_FLAG_EXACT_SUBSTATS restores it; both
+    outputs equal the oracle's."""
+    n = 6_000_000
+    keys = gen(n, 23)
+    vals = inputs.index_payload(n)
+    ok_k, ok_v = oracle.zsort_pairs(keys, vals)
+    got = {}
+    for flags in (0, z.FLAG_EXACT_SUBSTATS):
+        kd, vd = to_dev(keys, vals)
+        z.sort_pairs(kd, vd, opts=z.default_opts(flags=flags))
+        st = z.last_stats()
+        assert np.array_equal(kd.cpu().numpy().view(np.uint64), ok_k)
+        assert np.array_equal(vd.cpu().numpy().view(np.uint32), ok_v)
+        got[flags] = st
+    assert got[z.FLAG_EXACT_SUBSTATS]["sampled_stats"] == 0
+    if got[0]["partitions_large"] > 1:
+        assert got[0]["sampled_stats"] >= 1
+        assert got[0]["bytes_algorithmic"] < got[z.FLAG_EXACT_SUBSTATS]["bytes_algorithmic"]

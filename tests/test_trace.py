@@ -81,6 +81,9 @@ def test_trace_accounts_for_every_task(family, mapper):
     assert int(rec["level"].max()) <= st["max_level"] + 1
     if mapper == 1:
         assert np.any(rec["type"] == 9)  # the learned map was fitted
+    # sub-arrays below the top took sampled statistics (one task each), or
+    # the exact pass after a sample without spread
+    assert int((rec["type"] == 10).sum()) >= st["sampled_stats"]
 
 
 @gpu
@@ -94,7 +97,7 @@ def test_untraced_call_reports_no_trace():
     assert count == 0 and rec.size == 0
 
 
-def _chunk_plan(n, ln, cpc, nctas, tile=2048):
+def _chunk_plan(n, ln, cpc, nctas, tile=z.TILE_PAIRS):
     """The chunk geometry of a large (sub)array: chunks of ct tiles, the last
     round's worth of tiles in chunks of a quarter of that size."""
     tiles = (ln + tile - 1) // tile

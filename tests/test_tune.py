@@ -101,10 +101,10 @@ def test_cache_missing_file_and_entry(lib, tmp_path):
 
 def test_cache_round_trip_and_update(lib, tmp_path):
     path = str(tmp_path / "tune.json")
-    z.tune_cache_put(path, "sm152/n28/s0/flat", tuned(kmax=1024, chunks=16), 14.25)
+    z.tune_cache_put(path, "sm152/n28/s0/flat", tuned(kmax=512, chunks=16), 14.25)
     z.tune_cache_put(path, "sm152/n31/s14/flat", tuned(leaf_cap=3072, large_min=131072), 203.5)
     o, ms = z.tune_cache_get(path, "sm152/n28/s0/flat")
-    assert (o.kmax, o.chunks_per_cta, o.leaf_cap, ms) == (1024, 16, 4096, 14.25)
+    assert (o.kmax, o.chunks_per_cta, o.leaf_cap, ms) == (512, 16, 4096, 14.25)
     # other fields come from the base, not the file
     assert o.mapper == z.MAP_ZSCORE and o.struct_size == ctypes.sizeof(z.Opts)
     z.tune_cache_put(path, "sm152/n28/s0/flat", tuned(kmax=256, leaf_target=1024), 13.0)
