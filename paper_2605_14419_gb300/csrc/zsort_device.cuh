@@ -26,6 +26,7 @@ constexpr int PAD = 8;                    // smem slack for 16-byte aligned bulk
 constexpr int NB_MAX = 512;               // buckets per partition pass
 constexpr int RANK_SMALL = BLOCK;         // leaves this small are ranked by counting
 constexpr int SC_STAGES = 2;              // streamed (key, payload) tile buffers per CTA
+static_assert(8 * WARP_SPAN >= 16 + 4 * NB_MAX, "a warp's peer table fits its span of the tile's keys");
 constexpr uint32_t LEAF_M2_MAX = 2048;    // sub-buckets of the fast leaf path
 constexpr int PWL_P = 256;                // pieces of the learned map
 constexpr int SAMPLE_MAX = 65536;         // largest training sample
@@ -739,39 +740,58 @@ __device__ uint32_t block_exclusive_scan(const uint32_t *in, uint32_t *out, uint
     return total;
 }
 
-// In-place exclusive scan of a[0..nb) that keeps no partial sums in
-// registers (each thread re-reads its own run of entries); returns the total.
-__device__ uint32_t block_exclusive_scan_inplace(uint32_t *a, uint32_t nb, uint32_t *wsum)
+// In-place exclusive scan of a[0..nb) by rows of 32 consecutive entries:
+// every warp takes a run of rows, lane l reads entry l of a row (no bank
+// conflicts), first summing its warp's rows, then -- once the warps' totals
+// are known -- scanning them with a running offset.  Returns the total.
+__device__ uint32_t block_exclusive_scan_rows(uint32_t *a, uint32_t nb, uint32_t *wsum)
 {
+    const uint32_t full = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t per = (nb + BLOCK - 1) / BLOCK;
-    const uint32_t base = threadIdx.x * per;
-    const uint32_t end = min(base + per, nb);
-    uint32_t sum = 0;
-    for (uint32_t idx = base; idx < end; idx++) sum += a[idx];
-    uint32_t x = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
+    const uint32_t rows = (nb + 31) / 32, per = (rows + WARPS - 1) / WARPS;
+    const uint32_t r0 = min(rows, warp * per), r1 = min(rows, r0 + per);
+    uint32_t tot = 0;
+    for (uint32_t r = r0; r < r1; r++) {
+        const uint32_t idx = r * 32 + lane;
+        tot += __reduce_add_sync(full, idx < nb ? a[idx] : 0u);
     }
-    if (lane == 31) wsum[warp] = x;
+    if (lane == 0) wsum[warp] = tot;
     __syncthreads();
-    uint32_t wofs = 0, total = 0;
+    uint32_t run = 0, total = 0;
 #pragma unroll
     for (int w = 0; w < WARPS; w++) {
         const uint32_t ws = wsum[w];
-        wofs += w < warp ? ws : 0u;
+        run += w < warp ? ws : 0u;
         total += ws;
     }
-    uint32_t run = wofs + x - sum;
-    for (uint32_t idx = base; idx < end; idx++) {
-        const uint32_t v = a[idx];
-        a[idx] = run;
-        run += v;
+    for (uint32_t r = r0; r < r1; r++) {
+        const uint32_t idx = r * 32 + lane;
+        const uint32_t v = idx < nb ? a[idx] : 0u;
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(full, x, o);
+            if (lane >= o) x += y;
+        }
+        if (idx < nb) a[idx] = run + x - v;
+        run += __shfl_sync(full, x, 31);
     }
     __syncthreads();
     return total;
+}
+
+// Warp-wide min and max of 64-bit values by 32-bit reductions: the high
+// words first, then the low words of the lanes that hold the extreme high
+// word.  Every lane gets the result.
+__device__ __forceinline__ void warp_minmax64(unsigned long long &mn, unsigned long long &mx)
+{
+    const uint32_t full = 0xffffffffu;
+    const uint32_t hmin = __reduce_min_sync(full, (uint32_t)(mn >> 32));
+    const uint32_t lmin = __reduce_min_sync(full, (uint32_t)(mn >> 32) == hmin ? (uint32_t)mn : 0xffffffffu);
+    const uint32_t hmax = __reduce_max_sync(full, (uint32_t)(mx >> 32));
+    const uint32_t lmax = __reduce_max_sync(full, (uint32_t)(mx >> 32) == hmax ? (uint32_t)mx : 0u);
+    mn = ((unsigned long long)hmin << 32) | lmin;
+    mx = ((unsigned long long)hmax << 32) | lmax;
 }
 
 // ------------------------------------------------------------ tile ranking
@@ -817,6 +837,46 @@ __device__ __forceinline__ void rank_peers(const uint32_t (&b)[NI], uint32_t cnt
         const int nv = (int)cnt - first;
         const uint32_t vmask = nv >= 32 ? 0xffffffffu : (nv <= 0 ? 0u : (1u << nv) - 1u);
         peers[i] = p & vmask;
+    }
+}
+
+// rank_peers by a shared-memory table instead of ballots: each valid lane
+// ORs its bit into the word of its bucket in the warp's own table of nb
+// words (nb a multiple of 4, tbl 16-byte aligned, private to the warp), and
+// reads the word back: the mask of the lanes with its bucket.  The lowest
+// of them clears the word for the next slot.  A slot whose valid lanes all
+// share one bucket (a run of equal keys) skips the table, so that its lanes
+// do not serialise on one word.  The table is zeroed first; the warp's lanes
+// must be done with whatever the table's memory held.
+template <int NI>
+__device__ __forceinline__ void rank_peers_tbl(const uint32_t (&b)[NI], uint32_t cnt, uint32_t *tbl, uint32_t nb,
+                                               uint32_t (&peers)[NI])
+{
+    const uint32_t full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint4 *t4 = reinterpret_cast<uint4 *>(tbl);
+    __syncwarp();
+    for (uint32_t q = lane; q < nb / 4; q += 32) t4[q] = make_uint4(0u, 0u, 0u, 0u);
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < NI; i++) {
+        const int first = warp * 32 * NI + i * 32;
+        const int nv = (int)cnt - first;
+        const uint32_t vmask = nv >= 32 ? full : (nv <= 0 ? 0u : (1u << nv) - 1u);
+        const bool valid = (vmask >> lane) & 1u;
+        const uint32_t bi = b[i];
+        const uint32_t b0 = __shfl_sync(full, bi, 0);
+        if (__all_sync(full, !valid || bi == b0)) {  // one bucket (or no valid lane)
+            peers[i] = vmask;
+            continue;
+        }
+        if (valid) atomicOr(tbl + bi, 1u << lane);
+        __syncwarp();
+        const uint32_t pe = valid ? tbl[bi] : 0u;
+        __syncwarp();
+        if (valid && (pe & ((1u << lane) - 1u)) == 0u) tbl[bi] = 0u;
+        __syncwarp();
+        peers[i] = pe;
     }
 }
 

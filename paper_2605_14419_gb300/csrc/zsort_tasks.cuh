@@ -607,7 +607,7 @@ __device__ __noinline__ void hist_stream(const Params &P, SmemTile &s, Pipe &pp,
 // four barriers), its buffer takes the bulk copy of tile t + SC_STAGES - 1,
 // which streams in while tile t is ranked, staged and written.  Each warp
 // clears its own bucket counters.
-template <int NBITS, bool IDS, bool KV>
+template <bool IDS, bool KV>
 __device__ __noinline__ void scatter_stream(const Params &P, SmemTile &s, Pipe &pp, const uint64_t *srck,
                                             const uint32_t *srcv, bool bulk, unsigned long long start,
                                             unsigned long long len, uint64_t *dstk, uint32_t *dstv, uint32_t seglen)
@@ -671,7 +671,12 @@ __device__ __noinline__ void scatter_stream(const Params &P, SmemTile &s, Pipe &
             v[i] = in && kv ? sv[p] : 0u;
         }
         if (!IDS) map_tile<IPT, false>(mk, s.map, x, b);  // lanes past cnt: ignored by the ranking
-        rank_peers<IPT, NBITS>(b, cnt, peers);
+        // the peer table lies inside this warp's own span of the tile's keys
+        // (16 bytes in: past the alignment offset, so clear of the previous
+        // warp's last key), which the warp has just loaded into registers;
+        // the tile is staged there only after the scan's barriers
+        rank_peers_tbl<IPT>(b, cnt, reinterpret_cast<uint32_t *>(s.u.buf[w].key + (threadIdx.x >> 5) * WARP_SPAN + 2), k,
+                            peers);
         rank_leaders<IPT>(b, peers, pos, s);
         // every thread has left the previous tile: its buffer may be refilled
         if (__syncthreads_or(!ok)) {
@@ -725,8 +730,8 @@ __device__ __noinline__ void scatter_stream(const Params &P, SmemTile &s, Pipe &
     __syncthreads();
 }
 
-// One instantiation per payload mode, map family (MLP or not) and ballot
-// width, so that each keeps its own registers.
+// One instantiation per payload mode and bucket source, so that each keeps
+// its own registers.
 template <bool KV>
 __device__ __forceinline__ void scatter_pick(const Params &P, SmemTile &s, Pipe &pp, const uint64_t *srck,
                                              const uint32_t *srcv, bool bulk, unsigned long long start,
@@ -738,18 +743,10 @@ __device__ __forceinline__ void scatter_pick(const Params &P, SmemTile &s, Pipe 
         set_error(P, ST_INTERNAL);
         return;
     }
-    if (ids) {  // learned: buckets from the histogram pass; k >= 256
-        switch (rank_bits(k)) {
-        case 8: scatter_stream<8, true, KV>(P, s, pp, srck, srcv, bulk, start, len, dstk, dstv, seglen); break;
-        default: scatter_stream<9, true, KV>(P, s, pp, srck, srcv, bulk, start, len, dstk, dstv, seglen); break;
-        }
-        return;
-    }
-    switch (rank_bits(k)) {
-    case 7: scatter_stream<7, false, KV>(P, s, pp, srck, srcv, bulk, start, len, dstk, dstv, seglen); break;
-    case 8: scatter_stream<8, false, KV>(P, s, pp, srck, srcv, bulk, start, len, dstk, dstv, seglen); break;
-    default: scatter_stream<9, false, KV>(P, s, pp, srck, srcv, bulk, start, len, dstk, dstv, seglen); break;
-    }
+    if (ids)  // learned: buckets from the histogram pass
+        scatter_stream<true, KV>(P, s, pp, srck, srcv, bulk, start, len, dstk, dstv, seglen);
+    else
+        scatter_stream<false, KV>(P, s, pp, srck, srcv, bulk, start, len, dstk, dstv, seglen);
 }
 
 // ids: the buckets of a learned map come from the histogram pass (chunked
@@ -1924,7 +1921,7 @@ __device__ __forceinline__ void finish_fast(SmemTile &s, unsigned long long *key
     uint32_t *cnt = s.u.la.cnt;
     uint16_t *sidx = s.u.la.sidx;  // leaf position of each staged pair
     if (threadIdx.x == 0) cnt[M2] = len;  // sentinel: end of the last sub-bucket
-    block_exclusive_scan<LEAF_M2_MAX / BLOCK>(cnt, cnt, M2, s.wsum);
+    block_exclusive_scan_rows(cnt, M2, s.wsum);
 #pragma unroll
     for (int j = 0; j < LEAF_IPT; j++) {
         const uint32_t p = threadIdx.x + j * BLOCK;
@@ -2095,12 +2092,7 @@ __device__ __noinline__ void task_finish(const Params &P, const Item it, SmemTil
     const uint32_t M2 = min(LEAF_M2_MAX, pow2ceil32(len) / 2);
     uint32_t *cnt = s.u.la.cnt;
     for (uint32_t q = threadIdx.x; q < M2; q += BLOCK) cnt[q] = 0u;
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-        const unsigned long long a = shfl_down64(mn, o), b2 = shfl_down64(mx, o);
-        mn = a < mn ? a : mn;
-        mx = b2 > mx ? b2 : mx;
-    }
+    warp_minmax64(mn, mx);
     if ((threadIdx.x & 31) == 0) {
         s.red64[threadIdx.x >> 5] = mn;
         s.red64[WARPS + (threadIdx.x >> 5)] = mx;
