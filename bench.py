@@ -87,6 +87,79 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
+def host_info():
+    """Host cores and CPU model of this machine (the oracle's baseline runs here)."""
+    import platform
+
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model Name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith(("model name", "cpu model")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return {"nproc": os.cpu_count(), "cpu_model": model or platform.processor() or platform.machine(),
+            "machine": platform.machine()}
+
+
+def link_bandwidth(torch, dev, nbytes: int = 2 << 30, reps: int = 3):
+    """Pinned host <-> device copy bandwidth on this machine: one large copy each
+    way alone, then both directions at once (two streams), best of `reps`,
+    CUDA events.  GB/s counts the bytes of one direction."""
+    h = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    h2 = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    d = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    d2 = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    s1, s2 = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+
+    def timed(fn):
+        best = None
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        return best
+
+    def both():
+        ev = torch.cuda.Event()
+        ev.record()
+        s1.wait_event(ev)
+        s2.wait_event(ev)
+        with torch.cuda.stream(s1):
+            d.copy_(h, non_blocking=True)
+        with torch.cuda.stream(s2):
+            h2.copy_(d2, non_blocking=True)
+        torch.cuda.current_stream().wait_stream(s1)
+        torch.cuda.current_stream().wait_stream(s2)
+
+    h2d = timed(lambda: d.copy_(h, non_blocking=True))
+    d2h = timed(lambda: h2.copy_(d2, non_blocking=True))
+    bi = timed(both)
+    gb = nbytes / 1e9
+    out = {"bytes": nbytes, "h2d_gbs": round(gb / (h2d / 1e3), 1), "d2h_gbs": round(gb / (d2h / 1e3), 1),
+           "both_directions_gbs_each": round(gb / (bi / 1e3), 1)}
+    del h, h2, d, d2
+    torch.cuda.empty_cache()
+    return out
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons, sampled during the timed region."""
 
@@ -154,14 +227,14 @@ def make_workload(n: int, rank: int = 0):
 
 
 def batched_measure(z, torch, dev, nseg: int, seed: int, steps: int, warmup: int, plain_segments: int,
-                    tune_cache=None, tune_budget_ms: int = 60_000):
+                    tune_cache=None, tune_budget_ms: int = 60_000, cpu_segments: int = 0):
     """zsort_segmented on a batch of nseg log-uniform (32..2^20) segments, one
     persistent launch replayed from a CUDA graph, with the knobs chosen by the
     library's autotuner (untimed; served from tune_cache when it has the
     class); beside it the plain path, one zsort_pairs call per segment on the
     same data with default options (first plain_segments segments, scaled to
     pairs/s)."""
-    keys, vals, off, _ = inputs.segmented(nseg, seed)
+    keys, vals, off, _ = inputs.segmented_parallel(nseg, seed) if nseg >= 4000 else inputs.segmented(nseg, seed)
     n = keys.size
     kp = torch.from_numpy(keys.view(np.int64)).to(dev)
     vp = torch.from_numpy(vals.view(np.int32)).to(dev)
@@ -201,6 +274,10 @@ def batched_measure(z, torch, dev, nseg: int, seed: int, steps: int, warmup: int
         assert bool((sk[1:][same] >= sk[:-1][same]).all()), "batched: not sorted"
         src = od[:-1][seg_id] + (vb.to(torch.int64) & 0xFFFFFFFF)
         assert bool(torch.equal(kp[src], kb)), "batched: payload does not follow its key"
+        # stability: equal keys of a segment keep their input order
+        eq = same & (kb[1:] == kb[:-1])
+        assert bool((vb[1:][eq].to(torch.int64) > vb[:-1][eq].to(torch.int64)).all()), "batched: not stable"
+        del seg_id, sk, same, src, eq
         # plain path: one zsort_pairs call per segment
         m = min(plain_segments, nseg)
         a, b = int(off[0]), int(off[m])
@@ -218,14 +295,86 @@ def batched_measure(z, torch, dev, nseg: int, seed: int, steps: int, warmup: int
         stream.synchronize()
         plain_ms = e0.elapsed_time(e1)
     ms = sum(times) / len(times)
-    return {"segments": nseg, "pairs": n, "value": n / (ms / 1e3), "unit": UNIT, "ms": ms,
-            "graph": True, "bytes_per_pair": st["bytes_algorithmic"] / n, "autotuned": tuned,
-            "plain_per_segment_calls": {"segments": m, "pairs": b - a,
-                                        "value": (b - a) / (plain_ms / 1e3), "unit": UNIT}}
+    out = {"segments": nseg, "pairs": n, "value": n / (ms / 1e3), "unit": UNIT, "ms": ms,
+           "graph": True, "bytes_per_pair": st["bytes_algorithmic"] / n, "autotuned": tuned,
+           "checked": "sorted, payload follows its key, stable, in every segment",
+           "plain_per_segment_calls": {"segments": m, "pairs": b - a,
+                                       "value": (b - a) / (plain_ms / 1e3), "unit": UNIT}}
+    if cpu_segments:
+        out["cpu_thread_pool"] = cpu_batched_rate(keys, vals, off, cpu_segments)
+    return out
+
+
+def _signed_order(torch, k, key_type: str):
+    """int64 values whose signed order is the key order of k (int64 storage)."""
+    sign = torch.tensor(-(2 ** 63), dtype=torch.int64, device=k.device)
+    if key_type == "u64":
+        return k ^ sign
+    if key_type == "i64":
+        return k
+    return torch.where(k >= 0, k, k ^ torch.tensor(2 ** 63 - 1, dtype=torch.int64, device=k.device))  # totalOrder
+
+
+def configs_measure(z, torch, dev, stream, reps: int = 3):
+    """The other workloads at their stated sizes, one line each (pairs/s from
+    CUDA events around each sort, inputs restored between sorts):
+    five laws at n = 10^7 with Eq. 1 (the plain path at the paper's scale),
+    and the adversarial laws at n = 10^8 with the learned map and its Eq. 1
+    fallback at 4x the mean bucket load (u64 dense interval, int64 recentred,
+    float64 N(0,1) with +-inf and +-0).  Each output is checked: ordered, and
+    every payload still names its key."""
+    def run(name, keys_np, key_type, opts):
+        n = keys_np.size
+        kd = torch.from_numpy(keys_np.view(np.int64)).to(dev)
+        vd = torch.arange(n, dtype=torch.int32, device=dev)
+        kb, vb = torch.empty_like(kd), torch.empty_like(vd)
+        ts = []
+        for r in range(reps + 1):
+            kb.copy_(kd)
+            vb.copy_(vd)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            z.sort_pairs(kb, vb, key_type=key_type, opts=opts, stream=stream, check=False)
+            e1.record(stream)
+            rc = z.sync_status(stream)
+            if rc != 0:
+                raise z.ZsortError(rc, f"bench {name}")
+            if r:
+                ts.append(e0.elapsed_time(e1))
+        st = z.last_stats(stream)
+        o = _signed_order(torch, kb, key_type)
+        assert bool((o[1:] >= o[:-1]).all()), f"{name}: not sorted"
+        assert bool(torch.equal(kd[vb.to(torch.int64) & 0xFFFFFFFF], kb)), f"{name}: payload does not follow its key"
+        ms = statistics.median(ts)
+        row = {"n": n, "key_type": key_type, "value": n / (ms / 1e3), "unit": UNIT, "ms": round(ms, 3),
+               "bytes_per_pair": round(st["bytes_algorithmic"] / n, 2), "max_level": st["max_level"],
+               "top_map": ["zscore", "learned_pwl", "range", "mlp"][st["top_map"]],
+               "learned_accepted": st["learned_accepted"], "learned_rejected": st["learned_rejected"],
+               "sampled_stats": st["sampled_stats"], "guard_levels": st["guard_levels"]}
+        del kd, vd, kb, vb, o
+        return row
+
+    out = {"paper_scale_1e7_eq1": {}, "adversarial_1e8_learned": {}}
+    plain = z.default_opts(mapper=z.MAP_ZSCORE)
+    for fam, gen in inputs.FAMILIES.items():
+        out["paper_scale_1e7_eq1"][fam] = run(fam, gen(10 ** 7, 2), "u64", plain)
+    learned = z.default_opts(mapper=z.MAP_LEARNED, fallback_ratio=4.0)
+    n4 = 10 ** 8
+    out["adversarial_1e8_learned"]["u64_dense_interval"] = run("u64 dense", inputs.dense_interval_u64(n4, 4), "u64",
+                                                                learned)
+    out["adversarial_1e8_learned"]["i64_recentred"] = run("i64", inputs.dense_interval_i64(n4, 4).view(np.uint64),
+                                                           "i64", learned)
+    out["adversarial_1e8_learned"]["f64_specials"] = run("f64", inputs.normal_f64_specials(n4, 4).view(np.uint64),
+                                                          "f64", learned)
+    torch.cuda.empty_cache()
+    return out
 
 
 def cpu_oracle_rate(n_sample: int, budget_s: float = 12.0):
-    """Oracle pairs/s on bounded samples of the same two distributions."""
+    """Oracle pairs/s on bounded samples of the same two distributions, and
+    std::stable_sort (one thread) on the same samples."""
     import oracle
 
     samples = [inputs.lognormal(n_sample, 40), inputs.gaussian_mixture(n_sample, 41)]
@@ -240,7 +389,32 @@ def cpu_oracle_rate(n_sample: int, budget_s: float = 12.0):
         reps += 1
         if t_total >= budget_s or reps >= 8:
             break
-    return done / t_total, t_total, reps
+    sdone, st_total = 0, 0.0
+    for keys in samples:
+        t0 = time.perf_counter()
+        oracle.stdsort_pairs(keys, vals)
+        st_total += time.perf_counter() - t0
+        sdone += n_sample
+    return done / t_total, t_total, reps, sdone / st_total
+
+
+def cpu_batched_rate(keys, vals, off, nseg_sample: int):
+    """The oracle's zSort over the first nseg_sample segments of a batch,
+    shared out over a pool of one std::thread per host core, and the same
+    segments on one thread (the thread pool's baseline)."""
+    import oracle
+
+    m = min(nseg_sample, off.size - 1)
+    a, b = 0, int(off[m])
+    k, v, o = keys[a:b], vals[a:b], off[: m + 1]
+    t0 = time.perf_counter()
+    _, _, threads = oracle.zsort_segmented_mt(k, v, o)
+    t_mt = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.zsort_segmented_mt(k, v, o, threads=1)
+    t_1 = time.perf_counter() - t0
+    return {"segments": m, "pairs": b - a, "threads": threads, "value": (b - a) / t_mt,
+            "value_one_thread": (b - a) / t_1, "unit": UNIT, "seconds": round(t_mt + t_1, 2)}
 
 
 def pairs_config(logn: int, mapper_name: str, world: int = 1) -> dict:
@@ -281,8 +455,10 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
         "data": "synthetic (seeded numpy PCG64)",
-        "config": pairs_config(args.logn, args.mapper),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "config": dict(pairs_config(args.logn, args.mapper), pairs_per_step=len(arrays) * n_sample,
+                       sample=f"each step sorts n={n_sample} pairs of each of the two laws (the GPU arm sorts "
+                              f"2^{args.logn} of each)"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", **host_info(),
                          "sample": f"each step sorts the two arrays' laws at n={n_sample} (lognormal and "
                                    f"8-component mixture) with the sequential C oracle on one host core; "
                                    f"pairs/s of that sample stand for the 2 x 2^{args.logn} workload"},
@@ -310,8 +486,11 @@ def main():
     ap.add_argument("--tune-cache", default=os.environ.get("ZSORT_TUNE_CACHE"),
                     help="autotuner cache file for the batched workload (default: $ZSORT_TUNE_CACHE, else none)")
     ap.add_argument("--tune-budget-ms", type=int, default=60_000)
-    ap.add_argument("--batched-side", type=int, default=2000,
+    ap.add_argument("--batched-side", type=int, default=20_000,
                     help="segments of the batched measurement reported beside the pairs workload (0: none)")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the 10^7 and 10^8 workload lines")
+    ap.add_argument("--no-link", action="store_true", help="skip the pinned host-link bandwidth measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -532,27 +711,34 @@ def main():
 
         # the copies run on their own streams, one per direction, so that one
         # array's transfers overlap the other's sort and the two directions
-        # overlap each other; a device buffer is refilled once its result has
-        # been read back
-        # each direction's copies are split over --e2e-lanes streams, so that
-        # several copy engines share the link
+        # overlap each other.  Steps alternate between two sets of device
+        # buffers: the next step's upload of an array goes into the other set
+        # while this step's result is still being read back, so neither
+        # direction waits for the other (with one set, each array's upload,
+        # sort and read-back formed one serial chain per step).  Each
+        # direction's copies can also be split over --e2e-lanes streams.
         E2E_LANES = max(1, args.e2e_lanes)
         h2d_s = [torch.cuda.Stream(device=dev) for _ in range(E2E_LANES)]
         d2h_s = [torch.cuda.Stream(device=dev) for _ in range(E2E_LANES)]
-        free = [torch.cuda.Event() for _ in bufs]
-        for ev in free:
-            ev.record(d2h_s[0])
+        bufsets = [bufs, [(torch.empty_like(kb), torch.empty_like(vb)) for kb, vb in bufs]]
+        free = [[torch.cuda.Event() for _ in bufs] for _ in bufsets]
+        for row in free:
+            for ev in row:
+                ev.record(d2h_s[0])
+        step_no = [0]
 
         def pieces(t):
             step = (t.numel() + E2E_LANES - 1) // E2E_LANES
             return [t[j * step:(j + 1) * step] for j in range(E2E_LANES)]
 
         def e2e_step():
-            for i, (kb, vb) in enumerate(bufs):
+            bset = step_no[0] % 2
+            step_no[0] += 1
+            for i, (kb, vb) in enumerate(bufsets[bset]):
                 arrived = []
                 for j, (cs, dk, hk_j, dv, hv_j) in enumerate(zip(h2d_s, pieces(kb), pieces(hk[i]), pieces(vb),
                                                                  pieces(hv[i]))):
-                    cs.wait_event(free[i])
+                    cs.wait_event(free[bset][i])
                     with torch.cuda.stream(cs):
                         dk.copy_(hk_j, non_blocking=True)
                         dv.copy_(hv_j, non_blocking=True)
@@ -575,7 +761,7 @@ def main():
                     back.append(ev)
                 for ev in back[1:]:  # the buffer is free once every piece is back
                     d2h_s[0].wait_event(ev)
-                free[i].record(d2h_s[0])
+                free[bset][i].record(d2h_s[0])
 
         for _ in range(2):
             e2e_step()
@@ -588,8 +774,9 @@ def main():
             cs.wait_event(e0)
         for _ in range(e_steps):
             e2e_step()
-        for ev in free:  # every result is back on the host
-            stream.wait_event(ev)
+        for row in free:  # every result is back on the host
+            for ev in row:
+                stream.wait_event(ev)
         e1.record(stream)
         torch.cuda.synchronize()
         rc = z.sync_status(stream)
@@ -604,19 +791,43 @@ def main():
         e2e = {"value": world * pairs_per_step * e_steps / (ems / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": pairs_per_step * BYTES_PER_PAIR,
                "d2h_bytes_per_step": pairs_per_step * BYTES_PER_PAIR}
+        del hk, hv, ok_k, ok_v, bufsets
 
+    link = None
+    if not args.no_e2e and not args.no_link:
+        link = link_bandwidth(torch, dev)
+        if e2e is not None:
+            # the bound the e2e step time has to respect: both arrays' pairs
+            # each way per step over the measured link
+            per_dir = pairs_per_step * BYTES_PER_PAIR / 1e9
+            link["e2e_copy_bound_ms"] = round(1e3 * per_dir / min(link["h2d_gbs"], link["d2h_gbs"]), 2)
+            link["e2e_ms_per_step"] = round(1e3 * pairs_per_step / e2e["value"] * world, 2)
+
+    array_names = [name for name, _, _ in pristine]
+    del bufs
+    torch.cuda.empty_cache()
+    configs = None
+    if not args.no_configs:
+        configs = configs_measure(z, torch, dev, stream)
+
+    del pristine
+    torch.cuda.empty_cache()
     batched = None
     if args.batched_side > 0:
-        del bufs
-        torch.cuda.empty_cache()
         batched = batched_measure(z, torch, dev, args.batched_side, 5, 5, 3, min(args.batched_side, 2000),
-                                  args.tune_cache, min(args.tune_budget_ms, 20_000))
+                                  args.tune_cache, min(args.tune_budget_ms, 20_000),
+                                  cpu_segments=4000 if (rank == 0 and not args.no_cpu) else 0)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        rate, secs, reps = cpu_oracle_rate(args.sample)
+        rate, secs, reps, std_rate = cpu_oracle_rate(args.sample)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"lognormal + gmm8, {args.sample} pairs each, {reps} rounds, {secs:.1f} s"}
+               "sample": f"lognormal + gmm8, {args.sample} pairs each, {reps} rounds, {secs:.1f} s, one thread",
+               "std_stable_sort": {"value": std_rate, "unit": UNIT, "cores": 1,
+                                   "sample": "the same two samples, std::stable_sort by key, one thread"},
+               **host_info()}
+        if batched and "cpu_thread_pool" in batched:
+            cpu["batched_thread_pool"] = batched["cpu_thread_pool"]
 
     if rank != 0:
         return
@@ -641,12 +852,14 @@ def main():
                        "top_map": last_stats[i]["top_map"],
                        "leaves": last_stats[i]["leaves"],
                        "learned_accepted": last_stats[i]["learned_accepted"]}
-                      for i, (name, _, _) in enumerate(pristine)],
+                      for i, name in enumerate(array_names)],
         "plain_zscore": plain,
         "keys_only": keys_only,
         "u128": u128,
         "mappers": mappers,
         "batched": batched,
+        "configs": configs,
+        "link": link,
     }
     print(json.dumps(line), flush=True)
     if world > 1:

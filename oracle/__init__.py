@@ -6,7 +6,9 @@ benchmark's CPU-baseline leg (``bench.py --impl reference`` and the
 does, and the two share no code: see ``zsort_oracle.c`` for the citations.
 
 The C file is compiled with plain ``gcc -O2`` (no fast-math, no FP
-contraction) into ``oracle/liboracle.so`` on first use, or by ``build()``.
+contraction), and ``baseline_cpu.cpp`` (std::stable_sort and a std::thread
+pool over segments, the CPU comparison sorts of the benchmark) with ``g++
+-O2``, into ``oracle/liboracle.so`` on first use, or by ``build()``.
 """
 from __future__ import annotations
 
@@ -19,6 +21,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "zsort_oracle.c")
+_SRC_CPP = os.path.join(_HERE, "baseline_cpu.cpp")
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -58,14 +61,22 @@ class SubRec(ctypes.Structure):
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc; returns the path of the shared library."""
+    """Compile the oracle with gcc/g++; returns the path of the shared library."""
     with _lock:
-        if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-            tmp = _LIB + f".tmp{os.getpid()}"
-            cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-                   "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
-            subprocess.run(cmd, check=True)
-            os.replace(tmp, _LIB)
+        newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_CPP))
+        if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
+            tag = f".tmp{os.getpid()}"
+            obj_c, obj_cpp, tmp = _LIB + tag + ".c.o", _LIB + tag + ".cpp.o", _LIB + tag
+            try:
+                subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-c",
+                                "-o", obj_c, _SRC], check=True)
+                subprocess.run(["g++", "-O2", "-std=c++17", "-fPIC", "-c", "-o", obj_cpp, _SRC_CPP], check=True)
+                subprocess.run(["g++", "-shared", "-o", tmp, obj_c, obj_cpp, "-lm", "-pthread"], check=True)
+                os.replace(tmp, _LIB)
+            finally:
+                for f in (obj_c, obj_cpp):
+                    if os.path.exists(f):
+                        os.remove(f)
     return _LIB
 
 
@@ -87,6 +98,11 @@ def _load():
         lib.oracle_zsort_segmented.restype = ctypes.c_int
         lib.oracle_zsort_segmented.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                ctypes.c_uint64]
+        lib.oracle_stdsort_pairs.restype = ctypes.c_int
+        lib.oracle_stdsort_pairs.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64]
+        lib.oracle_zsort_segmented_mt.restype = ctypes.c_int
+        lib.oracle_zsort_segmented_mt.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                  ctypes.c_uint64, ctypes.c_int]
         lib.oracle_stats.restype = None
         lib.oracle_stats.argtypes = [ctypes.c_void_p, ctypes.c_uint64, u64p, u64p,
                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
@@ -171,6 +187,27 @@ def zsort_segmented(keys, vals, offsets):
     if rc != 0:
         raise ValueError(f"oracle_zsort_segmented failed: {rc}")
     return k, v
+
+
+def stdsort_pairs(keys, vals):
+    """std::stable_sort of the pairs by key, one thread (a comparison sort)."""
+    k = np.ascontiguousarray(keys, dtype=np.uint64).copy()
+    v = np.ascontiguousarray(vals, dtype=np.uint32).copy()
+    _load().oracle_stdsort_pairs(_ptr(k), _ptr(v), k.size)
+    return k, v
+
+
+def zsort_segmented_mt(keys, vals, offsets, threads: int = 0):
+    """The oracle's zSort of every segment, segments shared out over a pool
+    of `threads` host threads (0: one per core).  Returns (keys, vals,
+    threads used)."""
+    k = np.ascontiguousarray(keys, dtype=np.uint64).copy()
+    v = np.ascontiguousarray(vals, dtype=np.uint32).copy()
+    off = np.ascontiguousarray(offsets, dtype=np.uint64)
+    t = _load().oracle_zsort_segmented_mt(_ptr(k), _ptr(v), _ptr(off), off.size - 1, threads)
+    if t < 0:
+        raise ValueError(f"oracle_zsort_segmented_mt failed: {t}")
+    return k, v, t
 
 
 def stats(keys):

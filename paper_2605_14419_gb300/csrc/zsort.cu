@@ -462,7 +462,11 @@ int get_workspace(cudaStream_t stream, unsigned long long n, unsigned long long 
             cudaGetLastError();
             return ZSORT_ERR_NOMEM;
         }
-        ce = cudaMemset(blk, 0, p.total);  // zero ready flags (epoch 0 never used)
+        // zero ready flags (epoch 0 is never used) on the call's own stream:
+        // a plain cudaMemset runs on the legacy default stream, which a
+        // non-blocking stream does not wait for, so it could still be
+        // clearing the block while this call's kernels publish their work
+        ce = cudaMemsetAsync(blk, 0, p.total, stream);
         if (ce != cudaSuccess) return cuda_err(ce);
         ws->block = blk;
         ws->bytes = p.total;
@@ -888,9 +892,10 @@ int zsort_sync_status(zsort_stream_t stream)
     unsigned int err = 0;
     ce = cudaMemcpy(&err, &ws->P.ctl->error, sizeof(err), cudaMemcpyDeviceToHost);
     if (ce != cudaSuccess) return cuda_err(ce);
-    if (err) {
-        unsigned int zero = 0;
-        cudaMemcpy(&ws->P.ctl->error, &zero, sizeof(zero), cudaMemcpyHostToDevice);
+    if (err) {  // cleared on the workspace's stream, ahead of its next call
+        ce = cudaMemsetAsync(&ws->P.ctl->error, 0, sizeof(unsigned int), st);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+        if (ce != cudaSuccess) return cuda_err(ce);
     }
     return (int)err;
 }
@@ -980,9 +985,10 @@ int zsort_map_buckets(const uint64_t *keys, uint64_t n, const zsort_opts *opts, 
     unsigned int err = 0;
     ce = cudaMemcpy(&err, &ws->P.ctl->error, sizeof(err), cudaMemcpyDeviceToHost);
     if (ce != cudaSuccess) return cuda_err(ce);
-    if (err) {
-        unsigned int zero = 0;
-        cudaMemcpy(&ws->P.ctl->error, &zero, sizeof(zero), cudaMemcpyHostToDevice);
+    if (err) {  // cleared on the workspace's stream, ahead of its next call
+        ce = cudaMemsetAsync(&ws->P.ctl->error, 0, sizeof(unsigned int), st);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+        if (ce != cudaSuccess) return cuda_err(ce);
         return (int)err;
     }
     Seg S;

@@ -28,6 +28,7 @@ constexpr int RANK_SMALL = BLOCK;         // leaves this small are ranked by cou
 constexpr int SC_STAGES = 2;              // streamed (key, payload) tile buffers per CTA
 static_assert(8 * WARP_SPAN >= 16 + 4 * NB_MAX, "a warp's peer table fits its span of the tile's keys");
 constexpr uint32_t LEAF_M2_MAX = 2048;    // sub-buckets of the fast leaf path
+constexpr int LEAF_RANK_U = 4;            // staged pairs per thread and round of the leaf's rank count
 constexpr int PWL_P = 256;                // pieces of the learned map
 constexpr int SAMPLE_MAX = 65536;         // largest training sample
 constexpr int SAMPLE_RUNS = 8;            // the sample is sorted as this many runs, one CTA each
@@ -743,7 +744,10 @@ __device__ uint32_t block_exclusive_scan(const uint32_t *in, uint32_t *out, uint
 // In-place exclusive scan of a[0..nb) by rows of 32 consecutive entries:
 // every warp takes a run of rows, lane l reads entry l of a row (no bank
 // conflicts), first summing its warp's rows, then -- once the warps' totals
-// are known -- scanning them with a running offset.  Returns the total.
+// are known -- scanning them with a running offset.  SCAN_ROWS rows are in
+// flight at a time, so their loads, reductions and shuffles overlap.
+// Returns the total.
+constexpr int SCAN_ROWS = 4;
 __device__ uint32_t block_exclusive_scan_rows(uint32_t *a, uint32_t nb, uint32_t *wsum)
 {
     const uint32_t full = 0xffffffffu;
@@ -751,9 +755,15 @@ __device__ uint32_t block_exclusive_scan_rows(uint32_t *a, uint32_t nb, uint32_t
     const uint32_t rows = (nb + 31) / 32, per = (rows + WARPS - 1) / WARPS;
     const uint32_t r0 = min(rows, warp * per), r1 = min(rows, r0 + per);
     uint32_t tot = 0;
-    for (uint32_t r = r0; r < r1; r++) {
-        const uint32_t idx = r * 32 + lane;
-        tot += __reduce_add_sync(full, idx < nb ? a[idx] : 0u);
+    for (uint32_t r = r0; r < r1; r += SCAN_ROWS) {
+        uint32_t v[SCAN_ROWS];
+#pragma unroll
+        for (int g = 0; g < SCAN_ROWS; g++) {
+            const uint32_t idx = (r + g) * 32 + lane;
+            v[g] = r + g < r1 && idx < nb ? a[idx] : 0u;
+        }
+#pragma unroll
+        for (int g = 0; g < SCAN_ROWS; g++) tot += __reduce_add_sync(full, v[g]);
     }
     if (lane == 0) wsum[warp] = tot;
     __syncthreads();
@@ -764,17 +774,28 @@ __device__ uint32_t block_exclusive_scan_rows(uint32_t *a, uint32_t nb, uint32_t
         run += w < warp ? ws : 0u;
         total += ws;
     }
-    for (uint32_t r = r0; r < r1; r++) {
-        const uint32_t idx = r * 32 + lane;
-        const uint32_t v = idx < nb ? a[idx] : 0u;
-        uint32_t x = v;
+    for (uint32_t r = r0; r < r1; r += SCAN_ROWS) {
+        uint32_t v[SCAN_ROWS], x[SCAN_ROWS];
+#pragma unroll
+        for (int g = 0; g < SCAN_ROWS; g++) {
+            const uint32_t idx = (r + g) * 32 + lane;
+            v[g] = r + g < r1 && idx < nb ? a[idx] : 0u;
+            x[g] = v[g];
+        }
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(full, x, o);
-            if (lane >= o) x += y;
+#pragma unroll
+            for (int g = 0; g < SCAN_ROWS; g++) {
+                const uint32_t y = __shfl_up_sync(full, x[g], o);
+                if (lane >= o) x[g] += y;
+            }
         }
-        if (idx < nb) a[idx] = run + x - v;
-        run += __shfl_sync(full, x, 31);
+#pragma unroll
+        for (int g = 0; g < SCAN_ROWS; g++) {
+            const uint32_t idx = (r + g) * 32 + lane;
+            if (r + g < r1 && idx < nb) a[idx] = run + x[g] - v[g];
+            run += __shfl_sync(full, x[g], 31);
+        }
     }
     __syncthreads();
     return total;

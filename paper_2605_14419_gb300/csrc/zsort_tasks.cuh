@@ -1934,25 +1934,44 @@ __device__ __forceinline__ void finish_fast(SmemTile &s, unsigned long long *key
     }
     __syncthreads();
     // the warp's lanes walk their sub-buckets in lockstep (warp-uniform trip
-    // count, clamped reads): no divergence in the counting loop
-    for (uint32_t p0 = 0; p0 < len; p0 += BLOCK) {
-        const uint32_t p = p0 + threadIdx.x;
-        const uint32_t pc = p < len ? p : len - 1;
-        const unsigned long long xk = key[pc];
-        const uint32_t me = sidx[pc];
-        const uint32_t q = leaf_sub(xk, mn, rs, rm);
-        const uint32_t lo = cnt[q], hi = cnt[q + 1];
-        const uint32_t m = __reduce_max_sync(0xffffffffu, hi - lo);
-        uint32_t r = lo;
-        for (uint32_t t = 0; t < m; t++) {
-            const uint32_t j = min(lo + t, hi - 1);
-            const unsigned long long kj = key[j];
-            const uint32_t sj = sidx[j];
-            r += (uint32_t)(lo + t < hi) & ((uint32_t)(kj < xk) | ((uint32_t)(kj == xk) & (uint32_t)(sj < me)));
+    // count, clamped reads): no divergence in the counting loop.  Each thread
+    // takes LEAF_RANK_U staged pairs per round, so that their loads and
+    // compares overlap.
+    constexpr int U = LEAF_RANK_U;
+    for (uint32_t p0 = 0; p0 < len; p0 += U * BLOCK) {
+        unsigned long long xk[U];
+        uint32_t me[U], lo[U], hi[U], r[U];
+        uint32_t widest = 0;
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const uint32_t p = p0 + u * BLOCK + threadIdx.x;
+            const uint32_t pc = p < len ? p : len - 1;
+            xk[u] = key[pc];
+            me[u] = sidx[pc];
+            const uint32_t q = leaf_sub(xk[u], mn, rs, rm);
+            lo[u] = cnt[q];
+            hi[u] = cnt[q + 1];
+            r[u] = lo[u];
+            widest = max(widest, hi[u] - lo[u]);
         }
-        if (p < len) {
-            __stcg(dk + r, xk);
-            if (KV) __stcg(dv + r, val[p]);
+        const uint32_t m = __reduce_max_sync(0xffffffffu, widest);
+        for (uint32_t t = 0; t < m; t++) {
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const uint32_t j = min(lo[u] + t, hi[u] - 1);
+                const unsigned long long kj = key[j];
+                const uint32_t sj = sidx[j];
+                r[u] += (uint32_t)(lo[u] + t < hi[u]) &
+                        ((uint32_t)(kj < xk[u]) | ((uint32_t)(kj == xk[u]) & (uint32_t)(sj < me[u])));
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const uint32_t p = p0 + u * BLOCK + threadIdx.x;
+            if (p < len) {
+                __stcg(dk + r[u], xk[u]);
+                if (KV) __stcg(dv + r[u], val[p]);
+            }
         }
     }
 }

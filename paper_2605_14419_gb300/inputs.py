@@ -167,3 +167,69 @@ def segmented(nseg: int, seed: int, lo: int = 32, hi: int = 2 ** 20):
         keys[a:b] = FAMILIES[names[fam[i]]](b - a, seed * 1_000_003 + i)
         vals[a:b] = np.arange(b - a, dtype=np.uint32)
     return keys, vals, off, [names[f] for f in fam]
+
+
+def _fill_segments(args):
+    """Worker of segmented_parallel: draws segments [i0, i1) into the shared
+    key and payload buffers (same per-segment seeds as segmented)."""
+    from multiprocessing import shared_memory
+
+    shm_name, total, off, fam, seed, i0, i1 = args
+    shm = shared_memory.SharedMemory(name=shm_name)
+    try:
+        keys = np.ndarray((total,), dtype=np.uint64, buffer=shm.buf)
+        vals = np.ndarray((total,), dtype=np.uint32, buffer=shm.buf, offset=8 * total)
+        names = list(FAMILIES)
+        for i in range(i0, i1):
+            a, b = int(off[i]), int(off[i + 1])
+            keys[a:b] = FAMILIES[names[fam[i]]](b - a, seed * 1_000_003 + i)
+            vals[a:b] = np.arange(b - a, dtype=np.uint32)
+        del keys, vals
+    finally:
+        shm.close()
+    return i1 - i0
+
+
+def segmented_parallel(nseg: int, seed: int, lo: int = 32, hi: int = 2 ** 20, workers: int = 0):
+    """segmented(nseg, seed, lo, hi), bit for bit, drawn by a pool of worker
+    processes (started with spawn) into shared memory; for batches of
+    billions of pairs.  Falls back to segmented() if shared memory cannot be
+    had."""
+    import multiprocessing as mp
+    import os
+    from multiprocessing import shared_memory
+
+    sizes = segment_sizes(nseg, seed, lo, hi)
+    rng = _rng(seed + 1)
+    names = list(FAMILIES)
+    fam = rng.integers(0, len(names), nseg)
+    off = np.zeros(nseg + 1, dtype=np.uint64)
+    off[1:] = np.cumsum(sizes).astype(np.uint64)
+    total = int(off[-1])
+    workers = workers or min(32, os.cpu_count() or 1)
+    try:
+        shm = shared_memory.SharedMemory(create=True, size=max(12 * total, 1))
+    except OSError:
+        return segmented(nseg, seed, lo, hi)
+    try:
+        # share the work out by pairs, not by segments (sizes span 2^15)
+        bounds = [0]
+        target = total / (4 * workers)
+        acc = 0
+        for i in range(nseg):
+            acc += int(sizes[i])
+            if acc >= target:
+                bounds.append(i + 1)
+                acc = 0
+        if bounds[-1] != nseg:
+            bounds.append(nseg)
+        jobs = [(shm.name, total, off, fam, seed, bounds[j], bounds[j + 1]) for j in range(len(bounds) - 1)]
+        with mp.get_context("spawn").Pool(workers) as pool:
+            done = sum(pool.map(_fill_segments, jobs))
+        assert done == nseg
+        keys = np.ndarray((total,), dtype=np.uint64, buffer=shm.buf).copy()
+        vals = np.ndarray((total,), dtype=np.uint32, buffer=shm.buf, offset=8 * total).copy()
+    finally:
+        shm.close()
+        shm.unlink()
+    return keys, vals, off, [names[f] for f in fam]

@@ -548,3 +548,112 @@ def test_sampled_substats_count_and_bytes(gen):
     if got[0]["partitions_large"] > 1:
         assert got[0]["sampled_stats"] >= 1
         assert got[0]["bytes_algorithmic"] < got[z.FLAG_EXACT_SUBSTATS]["bytes_algorithmic"]
+
+
+def _signed_order(t, key_type):
+    """int64 values whose signed order is the key order (int64 storage)."""
+    sign = torch.tensor(-(2 ** 63), dtype=torch.int64, device=t.device)
+    if key_type == "u64":
+        return t ^ sign
+    if key_type == "i64":
+        return t
+    return torch.where(t >= 0, t, t ^ torch.tensor(2 ** 63 - 1, dtype=torch.int64, device=t.device))
+
+
+def _check_order_payload_stability(k_in, k_out, v_out, key_type):
+    o = _signed_order(k_out, key_type)
+    assert bool((o[1:] >= o[:-1]).all()), "not sorted"
+    pos = v_out.to(torch.int64) & 0xFFFFFFFF
+    assert bool(torch.equal(k_in[pos], k_out)), "a payload does not name its key"
+    assert int(torch.bincount(pos, minlength=k_in.numel()).max()) == 1, "payloads are not a permutation"
+    eq = k_out[1:] == k_out[:-1]
+    assert bool((pos[1:][eq] > pos[:-1][eq]).all()), "equal keys out of input order"
+
+
+@pytest.mark.parametrize("key_type,gen", [("u64", inputs.dense_interval_u64),
+                                          ("i64", lambda n, s: inputs.dense_interval_i64(n, s).view(np.uint64)),
+                                          ("f64", lambda n, s: inputs.normal_f64_specials(n, s).view(np.uint64))])
+def test_config4_full_size_adversarial_1e8(key_type, gen):
+    """The adversarial workload at its stated size: n = 10^8, learned map with
+    the Eq. 1 fallback at 4x the mean bucket load; u64 with 90% of the keys in
+    one interval of width 2^20, the int64 law recentred on 0, and float64
+    N(0,1) with 1% +-inf and 1% signed zeros (IEEE totalOrder: -0.0 first).
+    Checked at full size by the properties that fix the stable sort: order,
+    the payloads a permutation that names each key, equal keys in input
+    order.  The float64 specials are also checked by count and place."""
+    n = 10 ** 8
+    keys = gen(n, 4)
+    kd = torch.from_numpy(keys.view(np.int64)).to(DEV)
+    vd = torch.arange(n, dtype=torch.int32, device=DEV)
+    kb, vb = kd.clone(), vd.clone()
+    z.sort_pairs(kb, vb, key_type=key_type, opts=z.default_opts(mapper=z.MAP_LEARNED, fallback_ratio=4.0))
+    st = z.last_stats()
+    assert st["max_level"] <= 48
+    _check_order_payload_stability(kd, kb, vb, key_type)
+    if key_type == "f64":
+        x = kb.view(torch.float64)
+        ninf, pinf = int(torch.isneginf(x).sum()), int(torch.isposinf(x).sum())
+        assert bool(torch.isneginf(x[:ninf]).all()) and bool(torch.isposinf(x[n - pinf:]).all())
+        zeros = (x == 0).nonzero().flatten()
+        zbits = kb[zeros]
+        negz = int((zbits < 0).sum())  # -0.0 has the sign bit
+        assert bool((zbits[:negz] < 0).all()) and bool((zbits[negz:] == 0).all())
+    del kd, vd, kb, vb
+    torch.cuda.empty_cache()
+
+
+def test_config5_full_size_20000_segments():
+    """The batched workload at its stated size: 20,000 arrays with
+    log-uniform sizes 32..2^20 (about 2e9 pairs), each from one of the five
+    laws, sorted by one persistent launch under a CUDA graph; every segment
+    checked for order, payloads (within-segment index) naming their keys,
+    and stability."""
+    nseg = 20_000
+    keys, vals, off, _ = inputs.segmented_parallel(nseg, 5)
+    n = keys.size
+    kd = torch.from_numpy(keys.view(np.int64)).to(DEV)
+    vd = torch.from_numpy(vals.view(np.int32)).to(DEV)
+    od = torch.from_numpy(off.view(np.int64)).to(DEV)
+    del keys, vals
+    kb, vb = kd.clone(), vd.clone()
+    stream = torch.cuda.Stream(device=DEV)
+    with torch.cuda.stream(stream):
+        z.sort_segmented(kb, vb, od, opts=z.default_opts(flags=z.FLAG_GRAPH), stream=stream)
+    stream.synchronize()
+    starts = torch.zeros(n, dtype=torch.bool, device=DEV)
+    starts[od[:-1][od[:-1] < n]] = True
+    same = ~starts[1:]
+    del starts
+    o = kb ^ torch.tensor(-(2 ** 63), dtype=torch.int64, device=DEV)
+    assert bool((o[1:] >= o[:-1])[same].all()), "a segment is not sorted"
+    del o
+    seg = torch.repeat_interleave(torch.arange(nseg, device=DEV, dtype=torch.int32), (od[1:] - od[:-1]))
+    src = od[:-1][seg.to(torch.int64)] + (vb.to(torch.int64) & 0xFFFFFFFF)
+    del seg
+    assert bool(torch.equal(kd[src], kb)), "a payload does not name its key"
+    del src
+    eq = same & (kb[1:] == kb[:-1])
+    assert bool((vb[1:][eq].to(torch.int64) > vb[:-1][eq].to(torch.int64)).all()), "equal keys out of input order"
+    del kd, vd, kb, vb, od, eq, same
+    torch.cuda.empty_cache()
+
+
+def test_fresh_workspace_on_a_side_stream_sorts_at_once():
+    """A workspace allocated by a call on a non-blocking stream is cleared
+    in that stream's order: right after zsort_release, a first call on a
+    new side stream (a workspace of several GB, so clearing it takes
+    milliseconds) must see its own published work and sort exactly, with
+    and without graph capture."""
+    n = 1 << 27
+    keys = inputs.uniform(n, 61)
+    kd = torch.from_numpy(keys.view(np.int64)).to(DEV)
+    vd = torch.arange(n, dtype=torch.int32, device=DEV)
+    for flags in (0, z.FLAG_GRAPH):
+        z.release()
+        kb, vb = kd.clone(), vd.clone()
+        stream = torch.cuda.Stream(device=DEV)
+        with torch.cuda.stream(stream):
+            z.sort_pairs(kb, vb, opts=z.default_opts(flags=flags), stream=stream)
+        _check_order_payload_stability(kd, kb, vb, "u64")
+    del kd, vd, kb, vb
+    torch.cuda.empty_cache()

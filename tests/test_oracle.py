@@ -488,3 +488,22 @@ def test_mlp_balance_on_uniform_keys():
     mn, mx, q, sample = oracle.learned_map(keys, seed=13, m=65536, k=512)
     b = oracle.mlp_buckets(sample, mn, mx, oracle.mlp_train(q, 128), 512)
     assert np.bincount(b, minlength=512).max() <= 2 * 65536 // 512
+
+
+# ---------------------------------------------------------------- CPU comparison sorts
+@pytest.mark.parametrize("gen", [inputs.uniform, inputs.zipf, inputs.descending])
+def test_stdsort_comparator_is_the_stable_sort(gen):
+    keys = gen(30_000, 5)
+    vals = inputs.index_payload(keys.size)
+    k, v = oracle.stdsort_pairs(keys, vals)
+    rk, rv = stable_reference(keys)
+    assert np.array_equal(k, rk) and np.array_equal(v, rv)
+
+
+def test_threaded_segmented_oracle_matches_sequential():
+    keys, vals, off, _ = inputs.segmented(120, 8, lo=2, hi=20_000)
+    k1, v1 = oracle.zsort_segmented(keys, vals, off)
+    k2, v2, t = oracle.zsort_segmented_mt(keys, vals, off, threads=4)
+    assert t == 4 and np.array_equal(k1, k2) and np.array_equal(v1, v2)
+    _, _, tall = oracle.zsort_segmented_mt(keys, vals, off)
+    assert tall >= 1
