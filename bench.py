@@ -768,7 +768,7 @@ def main():
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        e_steps = max(3, args.steps // 2)
+        e_steps = max(6, args.steps)  # enough steps that the pipeline fill and drain amortise
         e0.record(stream)
         for cs in h2d_s + d2h_s:
             cs.wait_event(e0)
