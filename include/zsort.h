@@ -119,6 +119,9 @@ typedef struct {
                                 leaf_cap / 256 items each)                    */
     uint32_t chunks_per_cta; /* look-back chunk tasks per CTA over one level
                                 of large partitions, 1..64                    */
+    uint32_t ipt;            /* items per thread of a streamed tile: 12 (tiles
+                                of 3072 pairs) or 8 (2048); the statistics,
+                                histogram and scatter passes all use it       */
 } zsort_opts;
 
 /* flags: capture the call's launch sequence (control-block reset, two set-up
@@ -312,8 +315,9 @@ typedef struct {
 int zsort_map_buckets(const uint64_t *keys, uint64_t n, const zsort_opts *opts, uint32_t *buckets,
                       zsort_map_info *info, zsort_stream_t stream);
 
-/* Pairs per streamed tile: the unit in which a large (sub)array is cut into
- * chunk tasks (each chunk is at least four tiles). */
+/* Pairs per streamed tile at the default zsort_opts.ipt (12 per thread): the
+ * unit in which a large (sub)array is cut into chunk tasks (each chunk is at
+ * least four tiles); 256 * ipt in general. */
 #define ZSORT_TILE_PAIRS 3072u
 
 /* Largest n accepted by zsort_pairs_noalloc. */

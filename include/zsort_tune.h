@@ -15,6 +15,7 @@
  *   large_min       single-CTA / multi-CTA partition threshold
  *                                                      {32768, 65536, 131072, 262144}
  *   chunks_per_cta  look-back chunks per CTA and level {4, 8, 16}
+ *   ipt             items per thread of a streamed tile {8, 12}
  * by coordinate descent from the caller's base options (each knob in turn,
  * every candidate value timed on a device copy of the caller's data, the
  * fastest kept; passes repeat until nothing changes or the budget is spent).
@@ -32,7 +33,7 @@
  * Cache file.  A JSON object, one entry per line, written by this library:
  *   {
  *   "sm152/n28/s0/flat": {"kmax": 512, "leaf_target": 2048, "leaf_cap": 4096,
- *                         "large_min": 65536, "chunks_per_cta": 8, "ms": 14.3},
+ *                         "large_min": 65536, "chunks_per_cta": 8, "ipt": 12, "ms": 14.3},
  *   ...
  *   }
  * (each entry on a single line).  Writes replace the whole file through a

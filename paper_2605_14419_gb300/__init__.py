@@ -38,7 +38,7 @@ FLAG_GRAPH = 1
 FLAG_TEST_STALL = 2
 FLAG_TRACE = 4
 FLAG_EXACT_SUBSTATS = 8
-TILE_PAIRS = 3072
+TILE_PAIRS = 3072  # at the default ipt (12 items per thread); 256 * ipt in general
 SUB_SAMPLE = 4096
 TRACE_CAP = 1 << 20
 TASK_TYPES = {1: "stats", 2: "train", 3: "hist", 4: "scatter", 5: "mpart", 6: "finish", 7: "copy",
@@ -72,6 +72,7 @@ class Opts(ctypes.Structure):
         ("flags", ctypes.c_uint32),
         ("leaf_cap", ctypes.c_uint32),
         ("chunks_per_cta", ctypes.c_uint32),
+        ("ipt", ctypes.c_uint32),
     ]
 
 

@@ -183,7 +183,7 @@ __global__ void k_init_segments(Params P, const uint64_t *off, unsigned long lon
     }
     if (len > P.large_min || P.plan_out) {
         const uint32_t kk = choose_k(P, (uint32_t)len);
-        const uint32_t tiles = (uint32_t)((len + TILE - 1) / TILE);
+        const uint32_t tiles = (uint32_t)((len + P.tile - 1) / P.tile);
         const ChunkPlan cp = chunk_plan(P, tiles, (uint32_t)len);
         const uint32_t chunks = cp.chunks;
         const unsigned long long need = 2ull * chunks * kk;
@@ -360,7 +360,7 @@ constexpr Plan make_plan(unsigned long long n, unsigned long long nseg, unsigned
     // (sub)array; room for two such levels
     const unsigned long long nctas = 2ull * (unsigned long long)(sms > 0 ? sms : 160);
     p.statuscap = 2ull * NB_MAX *
-                  (min_u64(2 * chunks_per_cta * nctas, n / TILE + 64) + min_u64(2 * p.segcap, 16384));
+                  (min_u64(2 * chunks_per_cta * nctas, n / TILE_MIN + 64) + min_u64(2 * p.segcap, 16384));
     p.traincap = min_u64(p.segcap, traincap_max);
     size_t o = 0;
     auto take = [&o](size_t bytes) {
@@ -509,6 +509,7 @@ bool opts_valid(const zsort_opts &o)
     if (o.guard_level < 1) return false;
     if (o.leaf_cap < (uint32_t)RANK_SMALL || o.leaf_cap > (uint32_t)LEAF_CAP) return false;
     if (o.chunks_per_cta < 1 || o.chunks_per_cta > 64) return false;
+    if (o.ipt != (uint32_t)IPT && o.ipt != (uint32_t)IPT_SMALL) return false;
     return true;
 }
 
@@ -560,6 +561,8 @@ int launch(uint64_t *keys, uint32_t *vals, unsigned long long n, const uint64_t 
     P.guard_level = o.guard_level;
     P.leaf_cap = o.leaf_cap;
     P.chunks_per_cta = o.chunks_per_cta;
+    P.ipt = o.ipt;
+    P.tile = (uint32_t)BLOCK * o.ipt;
     P.sub_sample = (o.flags & ZSORT_FLAG_EXACT_SUBSTATS) ? 0u : 1u;
     P.fallback_ratio = o.fallback_ratio;
     P.seed = o.seed;
@@ -735,6 +738,7 @@ void zsort_default_opts(zsort_opts *o)
     o->wait_limit_ms = 2000;
     o->leaf_cap = LEAF_CAP;
     o->chunks_per_cta = 8;
+    o->ipt = IPT;
 }
 
 int zsort_pairs_ex(void *keys, uint32_t key_type, uint32_t *vals, uint64_t n, const zsort_opts *opts,
@@ -1074,6 +1078,8 @@ int zsort_pairs_noalloc(uint64_t *keys, uint32_t *vals, uint64_t n, int32_t *sta
     P.guard_level = o.guard_level;
     P.leaf_cap = o.leaf_cap;
     P.chunks_per_cta = o.chunks_per_cta;
+    P.ipt = o.ipt;
+    P.tile = (uint32_t)BLOCK * o.ipt;
     P.sub_sample = 1u;
     P.fallback_ratio = o.fallback_ratio;
     P.seed = o.seed;

@@ -16,9 +16,11 @@ namespace zs {
 // ---------------------------------------------------------------- constants
 constexpr int BLOCK = 256;                // threads per CTA
 constexpr int WARPS = BLOCK / 32;
-constexpr int IPT = 12;                   // items per thread of a streamed tile
-constexpr int TILE = BLOCK * IPT;         // 3072 pairs per streamed tile
-constexpr int WARP_SPAN = 32 * IPT;       // contiguous elements per warp and tile
+constexpr int IPT = 12;                   // items per thread of a streamed tile (default, largest)
+constexpr int IPT_SMALL = 8;              // the other choice of zsort_opts.ipt
+constexpr int TILE = BLOCK * IPT;         // 3072 pairs: the largest streamed tile (buffer size)
+constexpr int TILE_MIN = BLOCK * IPT_SMALL;  // 2048 pairs: the smallest
+constexpr int WARP_SPAN = 32 * IPT;       // contiguous elements per warp and tile of IPT items
 constexpr int LEAF_IPT = 16;              // items per thread of a leaf
 constexpr int LEAF_CAP = BLOCK * LEAF_IPT;  // 4096: a bucket (group) this small is finished in smem
 constexpr int LEAF_SPAN = 32 * LEAF_IPT;
@@ -180,6 +182,7 @@ struct Params {
     // options
     uint32_t kmax, leaf_target, large_min, learn_min, sample, mapper, guard_level;
     uint32_t leaf_cap, chunks_per_cta;
+    uint32_t ipt, tile;          // items per thread of a streamed tile, pairs per tile (256 ipt)
     uint32_t sub_sample;         // 1: large sub-arrays below the top take sampled statistics
     float fallback_ratio;
     unsigned long long seed;

@@ -476,17 +476,18 @@ __device__ bool stream_tiles(const Params &P, SmemTile &s, Pipe &pp, const uint6
                              bool bulk, unsigned long long start, unsigned long long len, Body body)
 {
     static_assert(!VALS, "streams of payloads go through the scatter's own loop");
-    const uint32_t nt = (uint32_t)((len + TILE - 1) / TILE);
+    const uint32_t tile = P.tile;  // 256 * ipt keys, at most TILE
+    const uint32_t nt = (uint32_t)((len + tile - 1) / tile);
     if (nt == 0) return true;
     auto tile_len = [&](uint32_t t) {
-        return (uint32_t)min((unsigned long long)TILE, len - (unsigned long long)t * TILE);
+        return (uint32_t)min((unsigned long long)tile, len - (unsigned long long)t * tile);
     };
     if (bulk && threadIdx.x == 0)
         for (uint32_t t = 0; t < KEY_STAGES - 1 && t < nt; t++)
-            stream_issue_keys(P, s, (int)t, keys, start + (unsigned long long)t * TILE, tile_len(t));
+            stream_issue_keys(P, s, (int)t, keys, start + (unsigned long long)t * tile, tile_len(t));
     for (uint32_t t = 0; t < nt; t++) {
         const int w = (int)(t % KEY_STAGES);
-        const unsigned long long a = start + (unsigned long long)t * TILE;
+        const unsigned long long a = start + (unsigned long long)t * tile;
         const uint32_t cnt = tile_len(t);
         unsigned long long *sk;
         if (bulk) {
@@ -506,7 +507,7 @@ __device__ bool stream_tiles(const Params &P, SmemTile &s, Pipe &pp, const uint6
             // every thread has left tile t - 1: its stage takes tile t + 2
             if (t + KEY_STAGES - 1 < nt && threadIdx.x == 0) {
                 const uint32_t tn = t + KEY_STAGES - 1;
-                stream_issue_keys(P, s, (int)(tn % KEY_STAGES), keys, start + (unsigned long long)tn * TILE,
+                stream_issue_keys(P, s, (int)(tn % KEY_STAGES), keys, start + (unsigned long long)tn * tile,
                                   tile_len(tn));
             }
             if (a + cnt > (P.n & ~1ull)) {  // the array's last key: a plain load (uniform branch)
@@ -528,9 +529,12 @@ __device__ bool stream_tiles(const Params &P, SmemTile &s, Pipe &pp, const uint6
     return true;
 }
 
+// Element of slot i of this thread in a tile of NI items per thread: warp w
+// holds the 32 * NI consecutive elements from w * 32 * NI on.
+template <int NI = IPT>
 __device__ __forceinline__ uint32_t slot_index(int i)
 {
-    return (threadIdx.x >> 5) * WARP_SPAN + i * 32 + (threadIdx.x & 31);
+    return (threadIdx.x >> 5) * (32 * NI) + i * 32 + (threadIdx.x & 31);
 }
 __device__ __forceinline__ uint32_t leaf_slot(int i)
 {
@@ -539,12 +543,14 @@ __device__ __forceinline__ uint32_t leaf_slot(int i)
 
 // ------------------------------------------------------------ tile bodies
 // Exact sums of the tile's keys into a per-thread accumulator.
+template <int NI>
 __device__ __forceinline__ void body_stats(LAcc &a, LAcc &b, uint32_t cnt, const unsigned long long *sk)
 {
+    static_assert(NI % 2 == 0, "the slots are taken in pairs");
     // two accumulators: the even and the odd slots form independent chains
 #pragma unroll
-    for (int i = 0; i < IPT; i += 2) {
-        const uint32_t p = slot_index(i), p1 = slot_index(i + 1);
+    for (int i = 0; i < NI; i += 2) {
+        const uint32_t p = slot_index<NI>(i), p1 = slot_index<NI>(i + 1);
         if (p < cnt) lacc_key(a, sk[p]);
         if (p1 < cnt) lacc_key(b, sk[p1]);
     }
@@ -552,27 +558,27 @@ __device__ __forceinline__ void body_stats(LAcc &a, LAcc &b, uint32_t cnt, const
 
 // Histogram of the tile's buckets into s.hist: one shared-memory atomic per
 // key, except when a whole warp slot shares one bucket (duplicate runs).
-template <bool MLP, bool IDS = false>
+template <int NI, bool MLP, bool IDS = false>
 __device__ __forceinline__ void body_hist(SmemTile &s, const MapK &mk, uint32_t cnt, const unsigned long long *sk,
                                           uint16_t *ids = nullptr)
 {
     const int lane = threadIdx.x & 31;
-    unsigned long long x[IPT];
-    uint32_t bb[IPT];
+    unsigned long long x[NI];
+    uint32_t bb[NI];
 #pragma unroll
-    for (int i = 0; i < IPT; i++) {
-        const uint32_t p = slot_index(i);
+    for (int i = 0; i < NI; i++) {
+        const uint32_t p = slot_index<NI>(i);
         x[i] = p < cnt ? sk[p] : mk.mn;
     }
-    map_tile<IPT, MLP>(mk, s.map, x, bb);
+    map_tile<NI, MLP>(mk, s.map, x, bb);
     if (IDS) {  // a learned map's buckets, for the scatter to read back
 #pragma unroll
-        for (int i = 0; i < IPT; i++)
-            if (slot_index(i) < cnt) __stcg(ids + slot_index(i), (unsigned short)bb[i]);
+        for (int i = 0; i < NI; i++)
+            if (slot_index<NI>(i) < cnt) __stcg(ids + slot_index<NI>(i), (unsigned short)bb[i]);
     }
 #pragma unroll
-    for (int i = 0; i < IPT; i++) {
-        const uint32_t b = slot_index(i) >= cnt ? INVALID : bb[i];
+    for (int i = 0; i < NI; i++) {
+        const uint32_t b = slot_index<NI>(i) >= cnt ? INVALID : bb[i];
         const uint32_t b0 = __shfl_sync(0xffffffffu, b, 0);
         if (__all_sync(0xffffffffu, b == b0)) {
             if (lane == 0 && b0 != INVALID) atomicAdd(&s.hist[b0], 32u);
@@ -587,15 +593,30 @@ __device__ __forceinline__ void body_hist(SmemTile &s, const MapK &mk, uint32_t 
 // A learned map (piecewise-linear or MLP) also writes every key's bucket to
 // ids[start, start+len): the scatter of the same chunk reads them back
 // instead of evaluating the map a second time.
-template <bool MLP>
+template <int NI, bool MLP>
 __device__ __noinline__ void hist_stream(const Params &P, SmemTile &s, Pipe &pp, const uint64_t *src, bool bulk,
                                          unsigned long long start, unsigned long long len, const MapK mk)
 {
     stream_tiles<false>(P, s, pp, src, nullptr, bulk, start, len,
                         [&](uint32_t t, uint32_t cnt, unsigned long long *sk, uint32_t *) {
-                            body_hist<MLP, true>(s, mk, cnt, sk, P.ids + start + (unsigned long long)t * TILE);
+                            body_hist<NI, MLP, true>(s, mk, cnt, sk, P.ids + start + (unsigned long long)t * P.tile);
                         });
 }
+
+// The Eq. 1 or range-map histogram of a stream (no bucket ids written),
+// inlined into its task at each items-per-thread choice.
+#define ZS_HIST_PLAIN(NI, src, bulk, start, len)                                                        \
+    stream_tiles<false>(P, s, pp, src, nullptr, bulk, start, len,                                       \
+                        [&](uint32_t, uint32_t cnt, unsigned long long *sk, uint32_t *) {               \
+                            body_hist<NI, false>(s, mk, cnt, sk);                                       \
+                        })
+// The exact sums of a stream into the task's two accumulators la, la2 (kept
+// in registers: the loop is inlined into the task).
+#define ZS_STATS(NI, src, bulk, start, len)                                                             \
+    stream_tiles<false>(P, s, pp, src, nullptr, bulk, start, len,                                       \
+                        [&](uint32_t, uint32_t cnt, unsigned long long *sk, uint32_t *) {               \
+                            body_stats<NI>(la, la2, cnt, sk);                                           \
+                        })
 
 // Stable scatter of [start, start+len) of a (sub)array whose map is in s.map
 // and whose running bucket cursors are in s.cursor.  Per tile: rank the
@@ -607,12 +628,13 @@ __device__ __noinline__ void hist_stream(const Params &P, SmemTile &s, Pipe &pp,
 // four barriers), its buffer takes the bulk copy of tile t + SC_STAGES - 1,
 // which streams in while tile t is ranked, staged and written.  Each warp
 // clears its own bucket counters.
-template <bool IDS, bool KV>
+template <int NI, bool IDS, bool KV>
 __device__ __noinline__ void scatter_stream(const Params &P, SmemTile &s, Pipe &pp, const uint64_t *srck,
                                             const uint32_t *srcv, bool bulk, unsigned long long start,
                                             unsigned long long len, uint64_t *dstk, uint32_t *dstv, uint32_t seglen)
 {
-    const uint32_t nt = (uint32_t)((len + TILE - 1) / TILE);
+    constexpr uint32_t TL = (uint32_t)(BLOCK * NI);  // pairs per tile
+    const uint32_t nt = (uint32_t)((len + TL - 1) / TL);
     if (nt == 0) return;
     const MapK mk = map_regs(s.map);
     const uint32_t k = mk.k;
@@ -621,25 +643,28 @@ __device__ __noinline__ void scatter_stream(const Params &P, SmemTile &s, Pipe &
     // neighbouring chunk) completes: keep those lines in L2 until then
     const unsigned long long pol_front = policy_evict_last();
     auto tile_cnt = [&](uint32_t t) {
-        return (uint32_t)min((unsigned long long)TILE, len - (unsigned long long)t * TILE);
+        return (uint32_t)min((unsigned long long)TL, len - (unsigned long long)t * TL);
     };
+    // a warp's peer table (k words, 16 bytes in) must fit its span of the
+    // tile's keys: always at 12 items per thread, for k <= 256 at 8
+    const bool table = 8u * 32u * NI >= 16u + 4u * k;
     rank_zero_warp(k, s);
     if (bulk && threadIdx.x == 0)
         for (uint32_t t = 0; t < SC_STAGES - 1 && t < nt; t++)
-            stream_issue<KV>(P, s, (int)t, srck, srcv, start + (unsigned long long)t * TILE, tile_cnt(t));
+            stream_issue<KV>(P, s, (int)t, srck, srcv, start + (unsigned long long)t * TL, tile_cnt(t));
     bool err = false;
     for (uint32_t t = 0; t < nt; t++) {
         const int w = (int)(t % SC_STAGES);
-        const unsigned long long a = start + (unsigned long long)t * TILE;
+        const unsigned long long a = start + (unsigned long long)t * TL;
         const uint32_t cnt = tile_cnt(t);
         unsigned long long *sk;
         uint32_t *sv;
         bool ok = true;
-        uint32_t b[IPT];
+        uint32_t b[NI];
         if (IDS) {  // the histogram pass's buckets: loads in flight during the tile's wait
 #pragma unroll
-            for (int i = 0; i < IPT; i++) {
-                const uint32_t p = slot_index(i);
+            for (int i = 0; i < NI; i++) {
+                const uint32_t p = slot_index<NI>(i);
                 b[i] = p < cnt ? (uint32_t)__ldcg(reinterpret_cast<const unsigned short *>(P.ids) + a + p) : 0u;
             }
         }
@@ -661,23 +686,26 @@ __device__ __noinline__ void scatter_stream(const Params &P, SmemTile &s, Pipe &
             }
             __syncthreads();
         }
-        unsigned long long x[IPT];
-        uint32_t v[IPT], pos[IPT], peers[IPT];
+        unsigned long long x[NI];
+        uint32_t v[NI], pos[NI], peers[NI];
 #pragma unroll
-        for (int i = 0; i < IPT; i++) {
-            const uint32_t p = slot_index(i);
+        for (int i = 0; i < NI; i++) {
+            const uint32_t p = slot_index<NI>(i);
             const bool in = p < cnt;
             x[i] = in ? sk[p] : mk.mn;
             v[i] = in && kv ? sv[p] : 0u;
         }
-        if (!IDS) map_tile<IPT, false>(mk, s.map, x, b);  // lanes past cnt: ignored by the ranking
+        if (!IDS) map_tile<NI, false>(mk, s.map, x, b);  // lanes past cnt: ignored by the ranking
         // the peer table lies inside this warp's own span of the tile's keys
         // (16 bytes in: past the alignment offset, so clear of the previous
         // warp's last key), which the warp has just loaded into registers;
         // the tile is staged there only after the scan's barriers
-        rank_peers_tbl<IPT>(b, cnt, reinterpret_cast<uint32_t *>(s.u.buf[w].key + (threadIdx.x >> 5) * WARP_SPAN + 2), k,
-                            peers);
-        rank_leaders<IPT>(b, peers, pos, s);
+        if (table)
+            rank_peers_tbl<NI>(b, cnt, reinterpret_cast<uint32_t *>(s.u.buf[w].key + (threadIdx.x >> 5) * (32 * NI) + 2),
+                               k, peers);
+        else
+            rank_peers<NI, 9>(b, cnt, peers);
+        rank_leaders<NI>(b, peers, pos, s);
         // every thread has left the previous tile: its buffer may be refilled
         if (__syncthreads_or(!ok)) {
             // a copy did not complete in time: give every copy that may still
@@ -695,14 +723,14 @@ __device__ __noinline__ void scatter_stream(const Params &P, SmemTile &s, Pipe &
         }
         if (bulk && t + SC_STAGES - 1 < nt && threadIdx.x == 0) {
             const uint32_t tn = t + SC_STAGES - 1;
-            stream_issue<KV>(P, s, (int)(tn % SC_STAGES), srck, srcv, start + (unsigned long long)tn * TILE,
+            stream_issue<KV>(P, s, (int)(tn % SC_STAGES), srck, srcv, start + (unsigned long long)tn * TL,
                              tile_cnt(tn));
         }
         rank_scan<true>(k, s);
-        rank_place<IPT>(b, pos, s);
+        rank_place<NI>(b, pos, s);
         rank_zero_warp(k, s);
 #pragma unroll
-        for (int i = 0; i < IPT; i++) {
+        for (int i = 0; i < NI; i++) {
             if (pos[i] != INVALID) {
                 sk[pos[i]] = x[i];
                 if (kv) sv[pos[i]] = v[i];
@@ -711,7 +739,7 @@ __device__ __noinline__ void scatter_stream(const Params &P, SmemTile &s, Pipe &
         }
         __syncthreads();
 #pragma unroll
-        for (int i = 0; i < IPT; i++) {
+        for (int i = 0; i < NI; i++) {
             const uint32_t p = threadIdx.x + i * BLOCK;
             if (p < cnt) {
                 const unsigned long long key = sk[p];
@@ -743,10 +771,15 @@ __device__ __forceinline__ void scatter_pick(const Params &P, SmemTile &s, Pipe 
         set_error(P, ST_INTERNAL);
         return;
     }
-    if (ids)  // learned: buckets from the histogram pass
-        scatter_stream<true, KV>(P, s, pp, srck, srcv, bulk, start, len, dstk, dstv, seglen);
+    const bool small = P.ipt == (uint32_t)IPT_SMALL;
+    if (ids && small)  // learned: buckets from the histogram pass
+        scatter_stream<IPT_SMALL, true, KV>(P, s, pp, srck, srcv, bulk, start, len, dstk, dstv, seglen);
+    else if (ids)
+        scatter_stream<IPT, true, KV>(P, s, pp, srck, srcv, bulk, start, len, dstk, dstv, seglen);
+    else if (small)
+        scatter_stream<IPT_SMALL, false, KV>(P, s, pp, srck, srcv, bulk, start, len, dstk, dstv, seglen);
     else
-        scatter_stream<false, KV>(P, s, pp, srck, srcv, bulk, start, len, dstk, dstv, seglen);
+        scatter_stream<IPT, false, KV>(P, s, pp, srck, srcv, bulk, start, len, dstk, dstv, seglen);
 }
 
 // ids: the buckets of a learned map come from the histogram pass (chunked
@@ -834,7 +867,7 @@ __device__ __noinline__ void classify_children(const Params &P, unsigned long lo
     unsigned long long part = 0;
     for (uint32_t g = threadIdx.x; g < ng; g += BLOCK) {
         const uint32_t len = L.lg_len[g];
-        const uint32_t tiles = (len + TILE - 1) / TILE;
+        const uint32_t tiles = (len + P.tile - 1) / P.tile;
         const uint32_t chunks = chunk_plan(P, tiles, len).chunks;
         const uint32_t kk = choose_k(P, len);
         L.lg_chunks[g] = chunks;
@@ -907,7 +940,7 @@ __device__ __noinline__ void classify_children(const Params &P, unsigned long lo
         S->status_base = sb0 + L.lg_need[g];
         S->len = len;
         S->k = L.lg_k[g];
-        S->tiles = (len + TILE - 1) / TILE;
+        S->tiles = (len + P.tile - 1) / P.tile;
         const ChunkPlan cp = chunk_plan(P, S->tiles, len);
         S->chunk_tiles = cp.ct;
         S->chunk_tiles_small = cp.ct_small;
@@ -989,11 +1022,11 @@ __device__ __forceinline__ Chunk chunk_of(const Params &P, uint32_t sid, uint32_
     ch.k = __ldcg(&S->k);
     ch.chunks = __ldcg(&S->chunks);
     ch.sbase = __ldcg(&S->status_base);
-    const unsigned long long big_span = (unsigned long long)__ldcg(&S->chunk_tiles) * TILE;
+    const unsigned long long big_span = (unsigned long long)__ldcg(&S->chunk_tiles) * P.tile;
     const uint32_t big = __ldcg(&S->chunks_big);
     unsigned long long span = big_span, rel = (unsigned long long)c * big_span;
     if (c >= big) {  // the short chunks at the end
-        span = (unsigned long long)__ldcg(&S->chunk_tiles_small) * TILE;
+        span = (unsigned long long)__ldcg(&S->chunk_tiles_small) * P.tile;
         rel = (unsigned long long)big * big_span + (unsigned long long)(c - big) * span;
     }
     ch.start = ch.off + rel;
@@ -1012,8 +1045,10 @@ __device__ __noinline__ void task_lstats(const Params &P, uint32_t sid, uint32_t
     lacc_init(la);
     lacc_init(la2);
     const uint64_t *src = keys_of(P, ch.buf);
-    stream_tiles<false>(P, s, pp, src, nullptr, bulk_ok(P, ch.buf), ch.start, ch.len,
-                        [&](uint32_t, uint32_t cnt, unsigned long long *sk, uint32_t *) { body_stats(la, la2, cnt, sk); });
+    if (P.ipt == (uint32_t)IPT_SMALL)
+        ZS_STATS(IPT_SMALL, src, bulk_ok(P, ch.buf), ch.start, ch.len);
+    else
+        ZS_STATS(IPT, src, bulk_ok(P, ch.buf), ch.start, ch.len);
     Acc a = lacc_sums(la);
     acc_merge(a, lacc_sums(la2));
     acc_block_reduce(a, s.acc);
@@ -1231,7 +1266,7 @@ __device__ uint32_t cta_lsd_sort64(unsigned long long *A, unsigned long long *B,
             if (t + 1 < nt) {
 #pragma unroll
                 for (int i = 0; i < IPT; i++) {
-                    const uint32_t p = t0 + TILE + slot_index(i);
+                    const uint32_t p = t0 + TILE + slot_index<IPT>(i);
                     nx[i] = p < m ? __ldcg(src + p) : 0ull;
                 }
             }
@@ -1595,7 +1630,7 @@ __device__ __noinline__ void task_dump(const Params &P, uint32_t sid, uint32_t c
     uint32_t *out = P.plan_out;
     stream_tiles<false>(P, s, pp, keys_of(P, ch.buf), nullptr, bulk_ok(P, ch.buf), ch.start, ch.len,
                         [&](uint32_t t, uint32_t cnt, unsigned long long *sk, uint32_t *) {
-                            const unsigned long long a = ch.start + (unsigned long long)t * TILE;
+                            const unsigned long long a = ch.start + (unsigned long long)t * P.tile;
                             for (uint32_t p = threadIdx.x; p < cnt; p += BLOCK) __stcg(out + a + p, map_key_any(s.map, sk[p]));
                         });
 }
@@ -1615,15 +1650,19 @@ __device__ __noinline__ void task_lhist(const Params &P, uint32_t sid, uint32_t 
     for (uint32_t q = threadIdx.x; q < k; q += BLOCK) s.hist[q] = 0;
     __syncthreads();
     const uint64_t *src = keys_of(P, ch.buf);
-    if (mk.kind == MAP_MLP)
-        hist_stream<true>(P, s, pp, src, bulk_ok(P, ch.buf), ch.start, ch.len, mk);
+    const bool small = P.ipt == (uint32_t)IPT_SMALL, bulk = bulk_ok(P, ch.buf);
+    if (mk.kind == MAP_MLP && small)
+        hist_stream<IPT_SMALL, true>(P, s, pp, src, bulk, ch.start, ch.len, mk);
+    else if (mk.kind == MAP_MLP)
+        hist_stream<IPT, true>(P, s, pp, src, bulk, ch.start, ch.len, mk);
+    else if (mk.kind == MAP_PWL && small)
+        hist_stream<IPT_SMALL, false>(P, s, pp, src, bulk, ch.start, ch.len, mk);
     else if (mk.kind == MAP_PWL)
-        hist_stream<false>(P, s, pp, src, bulk_ok(P, ch.buf), ch.start, ch.len, mk);
+        hist_stream<IPT, false>(P, s, pp, src, bulk, ch.start, ch.len, mk);
+    else if (small)
+        ZS_HIST_PLAIN(IPT_SMALL, src, bulk, ch.start, ch.len);
     else
-        stream_tiles<false>(P, s, pp, src, nullptr, bulk_ok(P, ch.buf), ch.start, ch.len,
-                            [&](uint32_t, uint32_t cnt, unsigned long long *sk, uint32_t *) {
-                                body_hist<false>(s, mk, cnt, sk);
-                            });
+        ZS_HIST_PLAIN(IPT, src, bulk, ch.start, ch.len);
     uint32_t *status = P.status + ch.sbase;
     uint32_t *row = status + (size_t)c * k;
     uint32_t *offs = status + (size_t)ch.chunks * k + (size_t)c * k;
@@ -1767,8 +1806,11 @@ __device__ __noinline__ void task_mpart(const Params &P, const Item it, SmemTile
     LAcc la, la2;
     lacc_init(la);
     lacc_init(la2);
-    stream_tiles<false>(P, s, pp, srck, nullptr, bulk, off, len,
-                        [&](uint32_t, uint32_t cnt, unsigned long long *sk, uint32_t *) { body_stats(la, la2, cnt, sk); });
+    const bool small = P.ipt == (uint32_t)IPT_SMALL;
+    if (small)
+        ZS_STATS(IPT_SMALL, srck, bulk, off, len);
+    else
+        ZS_STATS(IPT, srck, bulk, off, len);
     Acc a = lacc_sums(la);
     acc_merge(a, lacc_sums(la2));
     acc_block_reduce(a, s.acc);
@@ -1804,8 +1846,10 @@ __device__ __noinline__ void task_mpart(const Params &P, const Item it, SmemTile
     const MapK mk = map_regs(s.map);
     for (uint32_t q = threadIdx.x; q < k; q += BLOCK) s.hist[q] = 0;
     __syncthreads();
-    stream_tiles<false>(P, s, pp, srck, nullptr, bulk, off, len,
-                        [&](uint32_t, uint32_t cnt, unsigned long long *sk, uint32_t *) { body_hist<false>(s, mk, cnt, sk); });
+    if (small)
+        ZS_HIST_PLAIN(IPT_SMALL, srck, bulk, off, len);
+    else
+        ZS_HIST_PLAIN(IPT, srck, bulk, off, len);
     block_exclusive_scan(s.hist, s.bs, k, s.wsum);
     for (uint32_t q = threadIdx.x; q < k; q += BLOCK) s.cursor[q] = s.bs[q];
     __syncthreads();

@@ -37,10 +37,11 @@ std::vector<Knob> knobs()
         {"leaf_cap", &zsort_opts::leaf_cap, {2048, 3072, 4096}},
         {"large_min", &zsort_opts::large_min, {32768, 65536, 131072, 262144}},
         {"chunks_per_cta", &zsort_opts::chunks_per_cta, {4, 8, 16}},
+        {"ipt", &zsort_opts::ipt, {8, 12}},
     };
 }
 
-// Range checks of the five tuned fields (as the library validates them).
+// Range checks of the six tuned fields (as the library validates them).
 bool tuned_fields_valid(const zsort_opts &o)
 {
     if (o.kmax < 16 || o.kmax > 512 || (o.kmax & (o.kmax - 1))) return false;
@@ -48,6 +49,7 @@ bool tuned_fields_valid(const zsort_opts &o)
     if (o.leaf_cap < 256 || o.leaf_cap > 4096) return false;
     if (o.large_min < 4096 || o.large_min >= (1u << 30)) return false;
     if (o.chunks_per_cta < 1 || o.chunks_per_cta > 64) return false;
+    if (o.ipt != 8 && o.ipt != 12) return false;
     return true;
 }
 
@@ -115,6 +117,7 @@ bool parse_entry(const std::string &line, Entry *e, bool *bad)
     bool ok = field_u32(rest, "kmax", &e->o.kmax) && field_u32(rest, "leaf_target", &e->o.leaf_target) &&
               field_u32(rest, "leaf_cap", &e->o.leaf_cap) && field_u32(rest, "large_min", &e->o.large_min) &&
               field_u32(rest, "chunks_per_cta", &e->o.chunks_per_cta) && field_f64(rest, "ms", &e->ms);
+    if (ok && !field_u32(rest, "ipt", &e->o.ipt)) e->o.ipt = 12;  // entries written before the knob existed
     if (!ok || !tuned_fields_valid(e->o)) {
         *bad = true;
         return false;
@@ -157,9 +160,9 @@ bool write_cache(const char *path, const std::vector<Entry> &entries)
         const Entry &e = entries[i];
         std::fprintf(f,
                      "\"%s\": {\"kmax\": %u, \"leaf_target\": %u, \"leaf_cap\": %u, \"large_min\": %u, "
-                     "\"chunks_per_cta\": %u, \"ms\": %.4f}%s\n",
+                     "\"chunks_per_cta\": %u, \"ipt\": %u, \"ms\": %.4f}%s\n",
                      e.cls.c_str(), e.o.kmax, e.o.leaf_target, e.o.leaf_cap, e.o.large_min, e.o.chunks_per_cta,
-                     e.ms, i + 1 < entries.size() ? "," : "");
+                     e.o.ipt, e.ms, i + 1 < entries.size() ? "," : "");
     }
     std::fprintf(f, "}\n");
     const bool ok = std::fflush(f) == 0;
@@ -178,6 +181,7 @@ void copy_tuned(const zsort_opts &from, zsort_opts *to)
     to->leaf_cap = from.leaf_cap;
     to->large_min = from.large_min;
     to->chunks_per_cta = from.chunks_per_cta;
+    to->ipt = from.ipt;
 }
 
 int sample_keys(const uint64_t *keys, uint64_t n, std::vector<uint64_t> *s, cudaStream_t st)

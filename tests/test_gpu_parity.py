@@ -657,3 +657,38 @@ def test_fresh_workspace_on_a_side_stream_sorts_at_once():
         _check_order_payload_stability(kd, kb, vb, "u64")
     del kd, vd, kb, vb
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("family", ["uniform", "normal", "zipf", "nearly_sorted", "descending"])
+@pytest.mark.parametrize("n", [4097, 65_537, 200_003, 3_000_001])
+def test_eight_items_per_thread(family, n):
+    """zsort_opts.ipt = 8 (tiles of 2048 pairs, the autotuner's other choice):
+    the statistics, histogram and scatter passes run their 8-item
+    instantiations, the scatter with ballots where k = 512 leaves no room
+    for a warp's peer table; the output is the oracle's."""
+    keys = inputs.FAMILIES[family](n, 70 + n)
+    assert_same_as_oracle(keys, opts=z.default_opts(ipt=8))
+
+
+@pytest.mark.parametrize("mapper", [z.MAP_ZSCORE, z.MAP_LEARNED, z.MAP_MLP])
+def test_eight_items_per_thread_maps_keys_only_segmented(mapper):
+    """ipt = 8 with every map (the learned maps' bucket ids are written per
+    2048-pair tile), keys alone, and a segmented batch."""
+    keys = inputs.lognormal(3_000_000, 71)
+    opts = z.default_opts(ipt=8, mapper=mapper, learn_min=1 << 20)
+    assert_same_as_oracle(keys, opts=opts)
+    kd = torch.from_numpy(keys.view(np.int64)).to(DEV)
+    z.sort_pairs(kd, None, opts=opts)
+    assert np.array_equal(kd.cpu().numpy().view(np.uint64), np.sort(keys))
+    sk, sv, off, _ = inputs.segmented(200, 72, lo=1, hi=300_000)
+    kp, vp = to_dev(sk, sv)
+    z.sort_segmented(kp, vp, torch.from_numpy(off.view(np.int64)).to(DEV), opts=opts)
+    ok_k, ok_v = oracle.zsort_segmented(sk, sv, off)
+    assert np.array_equal(kp.cpu().numpy().view(np.uint64), ok_k)
+    assert np.array_equal(vp.cpu().numpy().view(np.uint32), ok_v)
+
+
+def test_invalid_items_per_thread_is_rejected():
+    kd = torch.zeros(100, dtype=torch.int64, device=DEV)
+    with pytest.raises(z.ZsortError):
+        z.sort_pairs(kd, None, opts=z.default_opts(ipt=10))

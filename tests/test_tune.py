@@ -86,9 +86,10 @@ def test_class_edge_inputs(lib):
 
 
 # ------------------------------------------------------------ cache (host)
-def tuned(kmax=512, leaf_target=2048, leaf_cap=4096, large_min=65536, chunks=8):
+def tuned(kmax=512, leaf_target=2048, leaf_cap=4096, large_min=65536, chunks=8, ipt=12):
     o = z.default_opts()
     o.kmax, o.leaf_target, o.leaf_cap, o.large_min, o.chunks_per_cta = kmax, leaf_target, leaf_cap, large_min, chunks
+    o.ipt = ipt
     return o
 
 
@@ -107,9 +108,9 @@ def test_cache_round_trip_and_update(lib, tmp_path):
     assert (o.kmax, o.chunks_per_cta, o.leaf_cap, ms) == (512, 16, 4096, 14.25)
     # other fields come from the base, not the file
     assert o.mapper == z.MAP_ZSCORE and o.struct_size == ctypes.sizeof(z.Opts)
-    z.tune_cache_put(path, "sm152/n28/s0/flat", tuned(kmax=256, leaf_target=1024), 13.0)
+    z.tune_cache_put(path, "sm152/n28/s0/flat", tuned(kmax=256, leaf_target=1024, ipt=8), 13.0)
     o, ms = z.tune_cache_get(path, "sm152/n28/s0/flat")
-    assert (o.kmax, o.leaf_target, o.chunks_per_cta, ms) == (256, 1024, 8, 13.0)
+    assert (o.kmax, o.leaf_target, o.chunks_per_cta, o.ipt, ms) == (256, 1024, 8, 8, 13.0)
     o2, ms2 = z.tune_cache_get(path, "sm152/n31/s14/flat")
     assert (o2.leaf_cap, o2.large_min, ms2) == (3072, 131072, 203.5)
     # the file is a JSON object of the two entries
@@ -117,7 +118,7 @@ def test_cache_round_trip_and_update(lib, tmp_path):
         doc = json.load(f)
     assert set(doc) == {"sm152/n28/s0/flat", "sm152/n31/s14/flat"}
     assert doc["sm152/n28/s0/flat"] == {"kmax": 256, "leaf_target": 1024, "leaf_cap": 4096,
-                                        "large_min": 65536, "chunks_per_cta": 8, "ms": 13.0}
+                                        "large_min": 65536, "chunks_per_cta": 8, "ipt": 8, "ms": 13.0}
     assert not os.path.exists(path + ".tmp")
 
 
@@ -127,6 +128,8 @@ def test_cache_rejects_bad_values(lib, tmp_path):
         z.tune_cache_put(path, "a", tuned(kmax=1000), 1.0)
     with pytest.raises(z.ZsortError):
         z.tune_cache_put(path, "a", tuned(leaf_cap=8192), 1.0)
+    with pytest.raises(z.ZsortError):
+        z.tune_cache_put(path, "a", tuned(ipt=10), 1.0)
     with pytest.raises(z.ZsortError):
         z.tune_cache_put(path, 'bad"name', tuned(), 1.0)
     assert not os.path.exists(path)
@@ -223,3 +226,13 @@ def test_knob_extremes_keep_parity(lib, leaf_cap, chunks):
     ok, ov = oracle.zsort_pairs(keys, vals)
     assert np.array_equal(k.cpu().numpy().view(np.uint64), ok)
     assert np.array_equal(v.cpu().numpy().view(np.uint32), ov)
+
+
+def test_cache_entry_without_ipt_reads_as_the_default(lib, tmp_path):
+    """Entries written before items per thread became a knob parse with the
+    default of 12."""
+    path = tmp_path / "tune.json"
+    path.write_text('{\n"old": {"kmax": 256, "leaf_target": 2048, "leaf_cap": 4096, "large_min": 65536, '
+                    '"chunks_per_cta": 8, "ms": 2.0}\n}\n')
+    o, ms = z.tune_cache_get(str(path), "old")
+    assert (o.kmax, o.ipt, ms) == (256, 12, 2.0)
