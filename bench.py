@@ -350,7 +350,7 @@ def configs_measure(z, torch, dev, stream, reps: int = 3):
         ms = statistics.median(ts)
         row = {"n": n, "key_type": key_type, "value": n / (ms / 1e3), "unit": UNIT, "ms": round(ms, 3),
                "bytes_per_pair": round(st["bytes_algorithmic"] / n, 2), "max_level": st["max_level"],
-               "top_map": ["zscore", "learned_pwl", "range", "mlp"][st["top_map"]],
+               "top_map": ["zscore", "learned_pwl", "range", "mlp", "learned_split"][st["top_map"]],
                "learned_accepted": st["learned_accepted"], "learned_rejected": st["learned_rejected"],
                "sampled_stats": st["sampled_stats"], "guard_levels": st["guard_levels"]}
         del kd, vd, kb, vb, o
@@ -642,7 +642,7 @@ def main():
             for label, mp in (("zscore", z.MAP_ZSCORE), ("learned_pwl", z.MAP_LEARNED), ("mlp", z.MAP_MLP)):
                 b, info = z.map_buckets(kd, z.default_opts(mapper=mp))
                 cnt = torch.bincount(b.to(torch.int64), minlength=info.k)
-                row[label] = {"map_used": ["zscore", "learned_pwl", "range", "mlp"][info.map], "k": info.k,
+                row[label] = {"map_used": ["zscore", "learned_pwl", "range", "mlp", "learned_split"][info.map], "k": info.k,
                               "max_over_mean": round(float(cnt.max()) * info.k / n, 2)}
                 del b, cnt
             imb[name] = row

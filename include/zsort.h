@@ -68,14 +68,18 @@ enum {
 enum {
     ZSORT_MAP_ZSCORE = 0,  /* Eq. 1: floor(((x - mean)/sd + |z_min|) * k/4)   */
     ZSORT_MAP_LEARNED = 1, /* piecewise-linear CDF, 256 pieces, FP32, trained
-                              on a sample; Eq. 1 is the fallback             */
+                              on a sample of keys normalised to binary32;
+                              when it fails the load test, the same CDF with
+                              exact-key breakpoints (ZSORT_MAPINFO_SPLIT),
+                              then Eq. 1                                     */
     ZSORT_MAP_MLP = 2      /* 2-layer MLP with positive weights and 32
                               clamp(., 0, 1) hidden units, FP32, fitted to
                               the same sample's 257 quantiles: f(u) =
                               sum_h a_h clamp(w_h u + b_h, 0, 1), a, w >= 0,
                               bucket = trunc(k (f(u) - f(0)) / (f(u_max) -
-                              f(0))); monotone by construction; Eq. 1 is the
-                              fallback                                       */
+                              f(0))); monotone by construction; when it
+                              fails the load test, the exact-key CDF
+                              (ZSORT_MAPINFO_SPLIT), then Eq. 1              */
 };
 
 /* Map actually used at the top level (zsort_map_info.map). */
@@ -83,7 +87,12 @@ enum {
     ZSORT_MAPINFO_ZSCORE = 0,
     ZSORT_MAPINFO_LEARNED = 1,
     ZSORT_MAPINFO_RANGE = 2,  /* the progress guard's exact range map */
-    ZSORT_MAPINFO_MLP = 3
+    ZSORT_MAPINFO_MLP = 3,
+    ZSORT_MAPINFO_SPLIT = 4   /* the learned CDF with exact-key breakpoints (the
+                                 sample's 256-quantile keys) and binary32
+                                 interpolation inside each piece, relative to
+                                 its lower key; tried when the normalised map
+                                 fails the load test */
 };
 
 /* Key types for zsort_pairs_ex. */
@@ -205,7 +214,7 @@ typedef struct {
     double top_sd;              /* top level: population standard deviation     */
     uint64_t top_min, top_max;  /* top level: exact min and max                 */
     uint32_t top_k;             /* top level: buckets                           */
-    uint32_t top_map;           /* top level: map used (ZSORT_MAP_*, 2 = range) */
+    uint32_t top_map;           /* top level: map used (ZSORT_MAPINFO_*)           */
     /* device time of the persistent kernel's tasks, summed over CTAs (ns);
        index = task type: 1 statistics tile or sample, 2 learned-map training, 3
        histogram tile, 4 look-back scatter tile, 5 single-CTA partition,

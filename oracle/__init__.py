@@ -130,6 +130,12 @@ def _load():
         lib.oracle_pwl_bucket.restype = ctypes.c_uint32
         lib.oracle_pwl_bucket.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
                                           ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32]
+        lib.oracle_split_train.restype = None
+        lib.oracle_split_train.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
+                                           ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p]
+        lib.oracle_split_buckets.restype = None
+        lib.oracle_split_buckets.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p]
         lib.oracle_mlp_train.restype = None
         lib.oracle_mlp_train.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p]
         lib.oracle_mlp_buckets.restype = None
@@ -296,6 +302,25 @@ def learned_map(keys, seed: int, m: int, k: int, P: int = P_PIECES):
     sample = k_arr[pos.astype(np.int64)]
     q = pwl_train(sample, mn, mx, P)
     return mn, mx, q, sample
+
+
+def split_train(sample_keys, mn: int, mx: int, P: int = P_PIECES):
+    """Exact-key breakpoints b[0..P] (uint64) and stored slopes r[0..P) of the
+    learned map's second form."""
+    srt = np.ascontiguousarray(sample_keys, dtype=np.uint64)
+    b = np.empty(P + 1, dtype=np.uint64)
+    r = np.empty(P, dtype=np.float32)
+    _load().oracle_split_train(_ptr(srt), srt.size, mn, mx, P, _ptr(b), _ptr(r))
+    return b, r
+
+
+def split_buckets(keys, b, r, k: int, P: int = P_PIECES):
+    kk = np.ascontiguousarray(keys, dtype=np.uint64)
+    bb = np.ascontiguousarray(b, dtype=np.uint64)
+    rr = np.ascontiguousarray(r, dtype=np.float32)
+    out = np.empty(kk.size, dtype=np.uint32)
+    _load().oracle_split_buckets(_ptr(kk), kk.size, _ptr(bb), _ptr(rr), P, k, _ptr(out))
+    return out
 
 
 MLP_H = 32

@@ -22,6 +22,11 @@
  *   oracle_pwl_bucket        the learned monotone piecewise-linear bucket map
  *                            that replaces the z-score map (not in the paper;
  *                            restated from its written definition)
+ *   oracle_split_train, oracle_split_bucket
+ *                            the learned map with exact-key breakpoints, the
+ *                            second choice when the FP32 normalisation of the
+ *                            first collapses the keys (not in the paper;
+ *                            restated from its written definition below)
  *   oracle_mlp_train, oracle_mlp_bucket
  *                            the alternative learned map: a 2-layer MLP with
  *                            positive weights fitted to the same quantile
@@ -487,6 +492,12 @@ float oracle_pwl_normalise(uint64_t key, uint64_t mn, uint64_t mx)
     return f * ldexpf(1.0f, -e);
 }
 
+static int cmp_u64(const void *a, const void *b)
+{
+    uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+    return (x > y) - (x < y);
+}
+
 static int cmp_float(const void *a, const void *b)
 {
     float x = *(const float *)a, y = *(const float *)b;
@@ -538,6 +549,61 @@ uint32_t oracle_pwl_bucket(uint64_t key, uint64_t mn, uint64_t mx,
     uint32_t w = (uint32_t)t;
     if (w > K - 1) w = K - 1;
     return s * K + w;
+}
+
+/* Learned map with exact-key breakpoints.  The piecewise-linear map above
+ * normalises keys to binary32 first, so keys closer together than the
+ * binary32 spacing at their distance from the minimum become one value (a
+ * dense interval of width 2^20 near 2^63 collapses to a single u).  This map
+ * keeps the breakpoints as keys: b[0] = mn, b[P] = mx, b[j] = the j-th
+ * P-quantile key of the sorted sample, sorted[floor(j*m/P)], for 0 < j < P.
+ * Piece s = #{ 0 < j < P : b[j] <= key } (keys below mn take piece 0, keys
+ * above mx piece P-1); inside it the interpolation is binary32 relative to
+ * the piece's own lower key: frac = fl32(fl32(key - b[s]) * r[s]) with the
+ * stored slope r[s] = fl32(1 / fl32(b[s+1] - b[s])) (0 for an empty piece),
+ * clipped to [0, 1 - 2^-24]; bucket = s*K + min(K-1, floor(frac*K)),
+ * K = k / P.  Monotone: the piece is, and each piece owns its K buckets. */
+void oracle_split_train(const uint64_t *sample, uint64_t m, uint64_t mn, uint64_t mx, uint32_t P,
+                        uint64_t *b, float *r)
+{
+    uint64_t *srt = (uint64_t *)malloc((size_t)m * sizeof(uint64_t));
+    memcpy(srt, sample, (size_t)m * sizeof(uint64_t));
+    qsort(srt, (size_t)m, sizeof(uint64_t), cmp_u64);
+    b[0] = mn;
+    for (uint32_t j = 1; j < P; j++) b[j] = srt[(uint64_t)j * m / P];
+    b[P] = mx;
+    for (uint32_t j = 0; j < P; j++) {
+        if (b[j + 1] > b[j]) {
+            volatile float w = (float)(b[j + 1] - b[j]);
+            r[j] = 1.0f / w;
+        } else {
+            r[j] = 0.0f;
+        }
+    }
+    free(srt);
+}
+
+uint32_t oracle_split_bucket(uint64_t key, const uint64_t *b, const float *r, uint32_t P, uint32_t k)
+{
+    uint32_t s = 0;
+    for (uint32_t j = 1; j < P; j++)
+        if (b[j] <= key) s = j;
+    uint32_t K = k / P;
+    volatile float d = (float)(key > b[s] ? key - b[s] : 0);
+    volatile float frac = d * r[s];
+    float f = frac;
+    if (f < 0.0f) f = 0.0f;
+    if (f > 0.99999994f) f = 0.99999994f; /* 1 - 2^-24 */
+    volatile float t = f * (float)K;
+    uint32_t w = (uint32_t)t;
+    if (w > K - 1) w = K - 1;
+    return s * K + w;
+}
+
+void oracle_split_buckets(const uint64_t *keys, uint64_t n, const uint64_t *b, const float *r, uint32_t P,
+                          uint32_t k, uint32_t *out)
+{
+    for (uint64_t i = 0; i < n; i++) out[i] = oracle_split_bucket(keys[i], b, r, P, k);
 }
 
 /* Level-1 cluster of every key under Eq. 1 (Alg. 1 statistics, R1-R5), as

@@ -27,7 +27,7 @@ OK = 0
 ERR_INVALID, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_BAD_OFFSETS, ERR_CAPACITY, ERR_INTERNAL = (
     -1, -2, -3, -4, -5, -6, -7)
 MAP_ZSCORE, MAP_LEARNED, MAP_MLP = 0, 1, 2
-MAPINFO_ZSCORE, MAPINFO_LEARNED, MAPINFO_RANGE, MAPINFO_MLP = 0, 1, 2, 3
+MAPINFO_ZSCORE, MAPINFO_LEARNED, MAPINFO_RANGE, MAPINFO_MLP, MAPINFO_SPLIT = 0, 1, 2, 3, 4
 KEY_TYPES = {"u64": 0, "i64": 1, "f64": 2}
 NOT_TUNED = 1
 TUNE_FORCE = 1

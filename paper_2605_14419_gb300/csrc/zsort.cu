@@ -999,10 +999,11 @@ int zsort_map_buckets(const uint64_t *keys, uint64_t n, const zsort_opts *opts, 
     ce = cudaMemcpy(&S, ws->P.segs, sizeof(Seg), cudaMemcpyDeviceToHost);
     if (ce != cudaSuccess) return cuda_err(ce);
     std::memset(info, 0, sizeof(*info));
-    info->map = S.kind == MAP_Z     ? ZSORT_MAPINFO_ZSCORE
-                : S.kind == MAP_PWL ? ZSORT_MAPINFO_LEARNED
-                : S.kind == MAP_MLP ? ZSORT_MAPINFO_MLP
-                                    : ZSORT_MAPINFO_RANGE;
+    info->map = S.kind == MAP_Z       ? ZSORT_MAPINFO_ZSCORE
+                : S.kind == MAP_PWL   ? ZSORT_MAPINFO_LEARNED
+                : S.kind == MAP_MLP   ? ZSORT_MAPINFO_MLP
+                : S.kind == MAP_SPLIT ? ZSORT_MAPINFO_SPLIT
+                                      : ZSORT_MAPINFO_RANGE;
     info->k = S.k;
     info->min = S.mn;
     info->max = S.mx;

@@ -47,7 +47,7 @@ constexpr int ST_BAD_OFFSETS = -5;
 constexpr int ST_CAPACITY = -6;
 constexpr int ST_INTERNAL = -7;
 
-enum MapKind : uint32_t { MAP_Z = 0, MAP_PWL = 1, MAP_RANGE = 2, MAP_MLP = 3 };
+enum MapKind : uint32_t { MAP_Z = 0, MAP_PWL = 1, MAP_RANGE = 2, MAP_MLP = 3, MAP_SPLIT = 4 };
 constexpr int MLP_H = 32;                 // hidden units of the MLP map
 constexpr int MLP_ITERS = 128;            // its training iterations
 constexpr int MLP_TABLE = 3 * MLP_H + 2;  // w[H], b[H], a[H], f0, inv
@@ -453,6 +453,7 @@ struct MapSm {
     uint32_t bin_lo, bin_sh;     // learned map: bin of u = (bits(u) - bin_lo) >> bin_sh, clamped
     uint32_t steps;              // learned map: 2^steps > most pieces a bin touches, minus one
     float mlp[MLP_TABLE];        // MLP map: w = omega^2, b, a = alpha^2 per unit, f0, inv
+    unsigned long long bq[PWL_P + 1];  // exact-key map: breakpoint keys (slopes in r)
 };
 
 // fl32(d), round to nearest even, without the 64-bit conversion instruction:
@@ -500,6 +501,31 @@ __device__ __forceinline__ uint32_t pwl_bucket_u(const MapSm &m, float u)
     uint32_t lo = m.lo8[pwl_bin(m, u)];
     for (uint32_t st = m.steps ? 1u << (m.steps - 1) : 0u; st; st >>= 1) lo = pwl_lift(m, u, lo, st);
     return pwl_finish(m, u, lo);
+}
+
+// Exact-key learned map (MAP_SPLIT): piece s = the last breakpoint key
+// bq[s] <= key (binary lifting over bq[1..P-1]); inside it the binary32
+// interpolation relative to the piece's own lower key, frac = fl32(key -
+// bq[s]) * r[s], clipped to [0, 1 - 2^-24]; bucket = s * K + floor(frac * K).
+__device__ __forceinline__ uint32_t split_lift(const MapSm &m, unsigned long long key, uint32_t lo, uint32_t st)
+{
+    const uint32_t j = lo + st;  // <= P - 1: the strides sum to P - 1
+    return m.bq[j] <= key ? j : lo;
+}
+__device__ __forceinline__ uint32_t split_finish(const MapSm &m, unsigned long long key, uint32_t s)
+{
+    const unsigned long long b = m.bq[s];
+    float frac = __fmul_rn(u64_to_f32_rn(key > b ? key - b : 0ull), m.r[s]);
+    frac = fminf(fmaxf(frac, 0.0f), 0x1.fffffep-1f);
+    uint32_t w = __float2uint_rz(__fmul_rn(frac, (float)m.K));
+    w = w < m.K ? w : m.K - 1;
+    return s * m.K + w;
+}
+__device__ __forceinline__ uint32_t split_bucket(const MapSm &m, unsigned long long key)
+{
+    uint32_t lo = 0;
+    for (uint32_t st = PWL_P / 2; st; st >>= 1) lo = split_lift(m, key, lo, st);
+    return split_finish(m, key, lo);
 }
 
 // The scalar part of a map, held in registers by the tile loops (the tables
@@ -567,6 +593,7 @@ __device__ __forceinline__ uint32_t map_key(const MapK &r, const MapSm &m, unsig
         if (r.rmult == 0) return (uint32_t)d;  // range < k: counting map
         return __umulhi((uint32_t)(d >> r.rshift), r.rmult);
     }
+    if (r.kind == MAP_SPLIT) return split_bucket(m, key);
     return pwl_bucket_u(m, __fmul_rn(u64_to_f32_rn(d), r.escale));
 }
 
@@ -613,6 +640,15 @@ __device__ __forceinline__ void map_tile(const MapK &mk, const MapSm &m, const u
         }
 #pragma unroll
         for (int i = 0; i < NI; i++) b[i] = pwl_finish(m, u[i], b[i]);
+    } else if (mk.kind == MAP_SPLIT) {  // phase by phase over the NI keys, as above
+#pragma unroll
+        for (int i = 0; i < NI; i++) b[i] = 0;
+        for (uint32_t st = PWL_P / 2; st; st >>= 1) {
+#pragma unroll
+            for (int i = 0; i < NI; i++) b[i] = split_lift(m, x[i], b[i], st);
+        }
+#pragma unroll
+        for (int i = 0; i < NI; i++) b[i] = split_finish(m, x[i], b[i]);
     } else {
 #pragma unroll
         for (int i = 0; i < NI; i++) b[i] = map_key(mk, m, x[i]);

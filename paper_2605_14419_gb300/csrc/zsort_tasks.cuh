@@ -405,6 +405,13 @@ __device__ void load_seg_map(const Params &P, uint32_t sid, SmemTile &s)
         __syncthreads();
         build_pwl_bins(s.map, &s.span_max);
     }
+    if (kind == MAP_SPLIT) {  // breakpoint keys in the training slot's selection area, slopes in the table
+        const unsigned long long *bq =
+            P.trainbuf + (size_t)__ldcg(&S->train_slot) * 2 * SAMPLE_MAX + SAMPLE_MAX;
+        const float *t = P.pwl + (size_t)sid * PWL_STRIDE;
+        for (int j = threadIdx.x; j <= PWL_P; j += BLOCK) s.map.bq[j] = __ldcg(bq + j);
+        for (int j = threadIdx.x; j < PWL_P; j += BLOCK) s.map.r[j] = __ldcg(t + PWL_P + 1 + j);
+    }
     __syncthreads();
 }
 
@@ -766,7 +773,7 @@ __device__ __forceinline__ void scatter_pick(const Params &P, SmemTile &s, Pipe 
                                              unsigned long long len, uint64_t *dstk, uint32_t *dstv, uint32_t seglen,
                                              uint32_t k, bool ids)
 {
-    const bool learned = s.map.kind == MAP_MLP || s.map.kind == MAP_PWL;
+    const bool learned = s.map.kind == MAP_MLP || s.map.kind == MAP_PWL || s.map.kind == MAP_SPLIT;
     if (learned != ids) {  // only chunked partitions learn maps, and their histograms write ids
         set_error(P, ST_INTERNAL);
         return;
@@ -1610,12 +1617,63 @@ __device__ __noinline__ void task_lfit(const Params &P, uint32_t sid, SmemTile &
             mz = max(mz, (uint32_t)s.red64[WARPS + w]);
         }
         const bool ok = (float)ml <= P.fallback_ratio * (float)m / (float)k && ml <= mz;
-        const uint32_t learned = mlp ? (uint32_t)MAP_MLP : (uint32_t)MAP_PWL;
-        S->kind = ok ? learned : MAP_Z;
         S->max_learned = ml;
         S->max_z = mz;
-        atomicAdd(ok ? &P.ctl->n_learn_ok : &P.ctl->n_learn_rej, 1ull);
-        if (__ldcg(&S->level) == 0 && sid == 0) P.ctl->top_map = ok ? learned : MAP_Z;
+        s.flag = ok ? 1u : 0u;
+        s.red64[0] = mz;
+    }
+    __syncthreads();
+    uint32_t kind = s.flag ? (mlp ? (uint32_t)MAP_MLP : (uint32_t)MAP_PWL) : (uint32_t)MAP_Z;
+    if (!s.flag) {
+        // Second try, when binary32 normalisation collapsed the sample (a
+        // dense interval far from the minimum becomes one u): the same CDF
+        // with exact-key breakpoints -- the selected sample keys, the exact
+        // min and max -- and binary32 interpolation inside each piece,
+        // relative to its own lower key.  The breakpoint keys stay in the
+        // training slot's selection area, the slopes replace r in the table.
+        const uint32_t mz0 = (uint32_t)s.red64[0];
+        unsigned long long *sel = P.trainbuf + (size_t)slot * 2 * SAMPLE_MAX + SAMPLE_MAX;
+        for (int j = threadIdx.x; j <= PWL_P; j += BLOCK) {
+            const unsigned long long b = j == 0 ? mn : (j == PWL_P ? mx : __ldcg(sel + j));
+            s.map.bq[j] = b;
+            if (j == 0 || j == PWL_P) __stcg(sel + j, b);
+        }
+        for (uint32_t q = threadIdx.x; q < k; q += BLOCK) s.hist[q] = 0;
+        __syncthreads();
+        for (int j = threadIdx.x; j < PWL_P; j += BLOCK) {
+            const unsigned long long lo = s.map.bq[j], hi = s.map.bq[j + 1];
+            const float r = hi > lo ? __fdiv_rn(1.0f, u64_to_f32_rn(hi - lo)) : 0.0f;
+            s.map.r[j] = r;
+            t[PWL_P + 1 + j] = r;
+        }
+        __syncthreads();
+        for (uint32_t i0 = 0; i0 < m; i0 += BLOCK * IPT) {
+            unsigned long long x[IPT];
+#pragma unroll
+            for (int u = 0; u < IPT; u++) {
+                const uint32_t i = i0 + threadIdx.x + u * BLOCK;
+                x[u] = i < m ? __ldcg(X + i) : mn;
+            }
+#pragma unroll
+            for (int u = 0; u < IPT; u++)
+                if (i0 + threadIdx.x + u * BLOCK < m) atomicAdd(&s.hist[split_bucket(s.map, x[u])], 1u);
+        }
+        __syncthreads();
+        uint32_t ms = 0;
+        for (uint32_t q = threadIdx.x; q < k; q += BLOCK) ms = max(ms, s.hist[q]);
+        ms = __reduce_max_sync(0xffffffffu, ms);
+        if ((threadIdx.x & 31) == 0) s.red64[1 + (threadIdx.x >> 5)] = ms;
+        __threadfence();  // the slopes and the breakpoint keys before the histogram tasks are published
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < WARPS; w++) ms = max(ms, (uint32_t)s.red64[1 + w]);
+            if ((float)ms <= P.fallback_ratio * (float)m / (float)k && ms <= mz0) kind = MAP_SPLIT;
+        }
+    }
+    if (threadIdx.x == 0) {
+        S->kind = kind;
+        atomicAdd(kind != MAP_Z ? &P.ctl->n_learn_ok : &P.ctl->n_learn_rej, 1ull);
+        if (__ldcg(&S->level) == 0 && sid == 0) P.ctl->top_map = kind;
         publish1(P, P.plan_out ? T_DUMP : T_LHIST, sid, chunks);
     }
 }
@@ -1655,9 +1713,9 @@ __device__ __noinline__ void task_lhist(const Params &P, uint32_t sid, uint32_t 
         hist_stream<IPT_SMALL, true>(P, s, pp, src, bulk, ch.start, ch.len, mk);
     else if (mk.kind == MAP_MLP)
         hist_stream<IPT, true>(P, s, pp, src, bulk, ch.start, ch.len, mk);
-    else if (mk.kind == MAP_PWL && small)
+    else if ((mk.kind == MAP_PWL || mk.kind == MAP_SPLIT) && small)
         hist_stream<IPT_SMALL, false>(P, s, pp, src, bulk, ch.start, ch.len, mk);
-    else if (mk.kind == MAP_PWL)
+    else if (mk.kind == MAP_PWL || mk.kind == MAP_SPLIT)
         hist_stream<IPT, false>(P, s, pp, src, bulk, ch.start, ch.len, mk);
     else if (small)
         ZS_HIST_PLAIN(IPT_SMALL, src, bulk, ch.start, ch.len);
@@ -1773,7 +1831,7 @@ __device__ __noinline__ void task_lscatter(const Params &P, uint32_t sid, uint32
     uint64_t *dstk = keys_of(P, ch.buf ^ 1u) + ch.off;
     uint32_t *dstv = vals_of(P, ch.buf ^ 1u) + ch.off;
     scatter_dispatch(P, s, pp, keys_of(P, ch.buf), vals_of(P, ch.buf), bulk_ok(P, ch.buf), ch.start, ch.len, dstk,
-                     dstv, ch.seglen, k, s.map.kind == MAP_MLP || s.map.kind == MAP_PWL);
+                     dstv, ch.seglen, k, s.map.kind == MAP_MLP || s.map.kind == MAP_PWL || s.map.kind == MAP_SPLIT);
     if (threadIdx.x == 0) atomicAdd(&P.ctl->bytes, 2ull * elem_bytes(P) * ch.len);
 }
 

@@ -188,12 +188,24 @@ def _map_case(gen, n, seed):
     return keys, kd
 
 
+def _dense_i64_encoded(n, seed):
+    """The int64 dense-interval law in the order-preserving unsigned encoding:
+    most keys within 2^19 of 2^63, so binary32 normalisation collapses them."""
+    return inputs.dense_interval_i64(n, seed).view(np.uint64) ^ np.uint64(2 ** 63)
+
+
+def _sample_max_load(buckets, k):
+    return int(np.bincount(buckets.astype(np.int64), minlength=k).max())
+
+
 @pytest.mark.parametrize("gen", [inputs.lognormal, inputs.gaussian_mixture, inputs.uniform,
-                                 inputs.dense_interval_u64, inputs.zipf])
+                                 inputs.dense_interval_u64, inputs.zipf, _dense_i64_encoded])
 def test_learned_map_buckets_bit_exact(gen):
     """Learned map (training sample, breakpoints, buckets) against the oracle's
     definition, bit for bit; the Eq. 1 fallback decision is checked from the
-    load-test numbers the device reports."""
+    load-test numbers the device reports.  When the normalised map fails its
+    load test the device tries the exact-key breakpoints: its buckets and
+    its accept / reject decision are checked against the oracle's."""
     n, m = 400_000, 65536
     keys, kd = _map_case(gen, n, 13)
     opts = z.default_opts(mapper=z.MAP_LEARNED, learn_min=m, sample=m, kmax=512)
@@ -208,12 +220,22 @@ def test_learned_map_buckets_bit_exact(gen):
     q = oracle.pwl_train(keys[pos], mn, mx)
     assert np.array_equal(np.frombuffer(bytes(info.q), dtype=np.float32), q)
     k = info.k
-    if info.map == z.MAP_LEARNED:
+    if info.map == z.MAPINFO_LEARNED:
         ob = oracle.pwl_buckets(keys, mn, mx, q, k)
         assert np.array_equal(gb.cpu().numpy().view(np.uint32), ob)
-    else:  # rejected by the load test: its rule, from the reported loads
-        assert (info.learned_max_load > opts.fallback_ratio * m / k
-                or info.learned_max_load > info.zscore_max_load)
+        return
+    # rejected by the load test: its rule, from the reported loads
+    assert (info.learned_max_load > opts.fallback_ratio * m / k
+            or info.learned_max_load > info.zscore_max_load)
+    b, r = oracle.split_train(keys[pos], mn, mx)
+    split_load = _sample_max_load(oracle.split_buckets(keys[pos], b, r, k), k)
+    split_ok = split_load <= opts.fallback_ratio * m / k and split_load <= info.zscore_max_load
+    assert info.map == (z.MAPINFO_SPLIT if split_ok else z.MAPINFO_ZSCORE)
+    if split_ok:
+        ob = oracle.split_buckets(keys, b, r, k)
+        assert np.array_equal(gb.cpu().numpy().view(np.uint32), ob)
+    if gen is _dense_i64_encoded:
+        assert info.map == z.MAPINFO_SPLIT
 
 
 def _top_keys(n, seed):
@@ -366,10 +388,30 @@ def test_mlp_map_bit_exact(gen):
     if info.map == z.MAPINFO_MLP:
         ob = oracle.mlp_buckets(keys, mn, mx, p, k)
         assert np.array_equal(gb.cpu().numpy().view(np.uint32), ob)
-    else:
-        assert info.map == z.MAPINFO_ZSCORE
+    else:  # rejected: then the exact-key map, or Eq. 1
+        assert info.map in (z.MAPINFO_SPLIT, z.MAPINFO_ZSCORE)
         assert (info.learned_max_load > opts.fallback_ratio * m / k
                 or info.learned_max_load > info.zscore_max_load)
+
+
+@pytest.mark.parametrize("mapper", [z.MAP_LEARNED, z.MAP_MLP])
+def test_exact_key_map_sorts_the_collapsing_int64_law(mapper):
+    """Keys packed within 2^19 of 2^63 (the int64 dense interval, encoded):
+    both normalised maps fail the load test, the exact-key map takes the top
+    level, and the sort equals the oracle's, pairs and keys only."""
+    keys = _dense_i64_encoded(3_000_000, 6)
+    opts = z.default_opts(mapper=mapper, learn_min=1 << 20)
+    vals = inputs.index_payload(keys.size)
+    k, v = to_dev(keys, vals)
+    z.sort_pairs(k, v, opts=opts)
+    st = z.last_stats()
+    assert st["top_map"] == z.MAPINFO_SPLIT
+    ok, ov = oracle.zsort_pairs(keys, vals)
+    assert np.array_equal(k.cpu().numpy().view(np.uint64), ok)
+    assert np.array_equal(v.cpu().numpy().view(np.uint32), ov)
+    kk = torch.from_numpy(keys.view(np.int64)).to(DEV)
+    z.sort_keys(kk, opts=opts)
+    assert np.array_equal(kk.cpu().numpy().view(np.uint64), ok)
 
 
 @pytest.mark.parametrize("gen", [inputs.lognormal, inputs.uniform, inputs.gaussian_mixture])

@@ -384,6 +384,46 @@ def test_pwl_balanced_on_its_sample_and_monotone():
     assert pb[0] == 0 and pb[-1] <= 1023
 
 
+def test_split_map_closed_form_on_even_sample():
+    """Exact-key map on a sample of keys base + i*step (i < m): the
+    breakpoints are the keys at ranks j m / P and every piece has the same
+    width, so the bucket of base + d (d < (P-1) m / P * step) is
+    floor(d * k / (m * step)) -- the same closed form as the normalised map,
+    here at 2^62 + ..., where binary32 normalisation would round."""
+    m, k, step, base = 65536, 512, 3, 2 ** 62 + 12345
+    sample = np.uint64(base) + np.arange(m, dtype=np.uint64) * np.uint64(step)
+    b, r = oracle.split_train(sample, base, base + (m - 1) * step)
+    assert np.array_equal(b[:256], (np.uint64(base) + np.arange(256, dtype=np.uint64) * np.uint64(256 * step)))
+    d = np.arange(0, 255 * 256 * step, 97, dtype=np.uint64)
+    got = oracle.split_buckets(np.uint64(base) + d, b, r, k)
+    assert np.array_equal(got, (d * np.uint64(k) // np.uint64(m * step)).astype(np.uint32))
+
+
+def test_split_map_resolves_a_dense_interval_that_fp32_collapses():
+    """90% of the keys in [2^63 - 2^19, 2^63 + 2^19) (the int64 law of the
+    adversarial workload, encoded): normalised to binary32 the interval is one
+    value and the map piles it into one bucket; with exact-key breakpoints
+    the sample's largest bucket stays within 4x the mean load, and the map is
+    monotone over the keys and over probes around every breakpoint."""
+    keys = inputs.dense_interval_i64(400_000, 4).view(np.uint64) ^ np.uint64(2 ** 63)
+    mn, mx = int(keys.min()), int(keys.max())
+    m, k = 65536, 512
+    pos = oracle.sample_positions(17, keys.size, m).astype(np.int64)
+    sample = keys[pos]
+    q = oracle.pwl_train(sample, mn, mx)
+    pwl = oracle.pwl_buckets(sample, mn, mx, q, k)
+    assert np.bincount(pwl.astype(np.int64), minlength=k).max() > 0.5 * m
+    b, r = oracle.split_train(sample, mn, mx)
+    sb = oracle.split_buckets(sample, b, r, k)
+    assert np.bincount(sb.astype(np.int64), minlength=k).max() <= 4 * m / k
+    order = np.argsort(keys, kind="stable")
+    kb = oracle.split_buckets(keys[order], b, r, k)
+    assert np.all(np.diff(kb.astype(np.int64)) >= 0) and kb[0] == 0
+    probes = np.unique(np.concatenate([b, b[1:] - np.uint64(1), b[:-1] + np.uint64(1)]))
+    pb = oracle.split_buckets(probes, b, r, k)
+    assert np.all(np.diff(pb.astype(np.int64)) >= 0)
+
+
 def test_segmented_oracle():
     keys, vals, off, _ = inputs.segmented(40, 3, lo=2, hi=5000)
     k, v = oracle.zsort_segmented(keys, vals, off)
