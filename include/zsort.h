@@ -25,7 +25,8 @@
  *     that later calls do not allocate.
  *   - Calls are stream ordered and asynchronous: they return once the work
  *     is enqueued on `stream` (NULL = the legacy default stream).  Calls on
- *     different streams use different workspaces and may overlap.
+ *     different streams use different workspaces and may overlap; calls on
+ *     one stream come from one host thread at a time.
  *   - Host-detectable errors (bad arguments, allocation failure, launch
  *     failure) are returned at once and nothing is enqueued.  Errors found
  *     on the device (a wait that timed out, decreasing segment offsets, a
@@ -221,7 +222,7 @@ typedef struct {
        6 shared-memory finish, 7 copy */
     uint64_t task_ns[8];
     uint64_t task_count[8];
-    uint64_t handler_ns;        /* tasks whose phase-completion work ran (incl.)  */
+    uint64_t handler_ns;        /* phase-completion work, after its last task     */
     uint64_t idle_ns;           /* time CTAs spent waiting for work               */
     uint64_t busy_window_ns;    /* first task start to last task end              */
     uint64_t sampled_stats;     /* sub-arrays whose statistics came from a sample */
@@ -241,13 +242,22 @@ int zsort_pairs(uint64_t *keys, uint32_t *vals, uint64_t n, zsort_stream_t strea
 int zsort_keys(uint64_t *keys, uint64_t n, zsort_stream_t stream);
 
 /* 128-bit keys (UUIDs, hashes; the paper's motivation, section
- * "Introduction"): key i is the pair of words keys[2i] (low 64 bits) and
- * keys[2i+1] (high 64 bits), compared as an unsigned 128-bit number; sorted
- * in place with vals (may be NULL), stably.  Done as two stable 64-bit
- * sorts, least significant word first (an LSD radix sort over 64-bit
- * digits, each digit sorted by this library's zSort with the input index as
- * its payload), then one gather of keys and payloads.  Allocates about
- * 36 bytes per key of stream-ordered scratch (cudaMallocAsync) for the call.
+ * "Introduction": zSort's pass count does not grow with the key width):
+ * key i is the pair of words keys[2i] (low 64 bits) and keys[2i+1] (high 64
+ * bits), compared as an unsigned 128-bit number; sorted in place with vals
+ * (may be NULL), stably.  With d = key - min (exact, 128 bits) and s =
+ * max(0, bitlen(max - min) - 64), the window d >> s fits 64 bits and,
+ * with the s bits below it, orders like the key.  One stable zSort of
+ * (window, input index); then only the keys in runs of equal windows (none
+ * when the keys' top 64 significant bits differ, as for hashes) are sorted
+ * by the bits below the window, run by run, in one segmented zSort of
+ * those keys alone; then one gather of keys and payloads.  Keys that share
+ * windows in bulk (a few distinct high words over a 2^128 range) make the
+ * second sort as long as the first.  The call waits for the stream once,
+ * to read the size of the tied runs.  Scratch: 44 bytes per key (28 without
+ * payloads) kept with the stream's workspace (grown on demand, freed by
+ * zsort_release), plus 20 bytes per tied key of stream-ordered scratch
+ * (cudaMallocAsync).
  * n <= ZSORT_MAX_N; opts may be NULL. */
 int zsort_pairs_u128(uint64_t *keys, uint32_t *vals, uint64_t n, const zsort_opts *opts, zsort_stream_t stream);
 

@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(BLOCK, 2) k_persistent(const __grid_constant__
         }
         if (threadIdx.x == 0) {
             unsigned long long t2 = globaltimer();
-            if (s.flag2) atomicAdd(&P.ctl->handler_ns, t2 - t_task0);
+            if (s.flag2) atomicAdd(&P.ctl->handler_ns, t2 - t_task1);  // the completion work alone
             atomicMax(&P.ctl->t_last, t2);
             if (P.trace) {
                 trace_task(P, type, arg, tile0, count, t_task0, t_task1);
@@ -319,6 +319,8 @@ struct Workspace {
     int sms = 0;
     int occ = 0;
     TraceRec *trace = nullptr;  // task trace buffer (ZSORT_TRACE_CAP records), on first traced call
+    void *aux = nullptr;        // scratch of the 128-bit path, grown on demand
+    size_t aux_bytes = 0;
 };
 
 // Names the host-side span of a public call in profiler timelines (NVTX).
@@ -636,34 +638,316 @@ int encode(void *keys, unsigned long long n, uint32_t type, int inverse, cudaStr
     return cuda_err(cudaGetLastError());
 }
 
-// 128-bit keys: the word pairs (lo, hi) and their order, see zsort_pairs_u128.
-__global__ void k128_split(const uint64_t *keys, unsigned long long n, uint64_t *lo, uint32_t *idx)
+// 128-bit keys, sorted by one zSort of a 64-bit window of each key (see
+// zsort_pairs_u128).  A key is the word pair (lo, hi); d = key - min is taken
+// exactly in 128 bits; the window is d >> s and the remainder the s bits
+// below it, s = max(0, bitlen(max - min) - 64), so that (window, remainder)
+// orders like the key and every window fits 64 bits.
+struct U128Win {
+    unsigned long long mn_lo, mn_hi;
+    uint32_t s, pad;
+    unsigned long long tied, groups;  // keys in runs of equal windows, runs
+};
+
+__device__ __forceinline__ bool lt128(unsigned long long alo, unsigned long long ahi, unsigned long long blo,
+                                      unsigned long long bhi)
+{
+    return ahi < bhi || (ahi == bhi && alo < blo);
+}
+
+// Warp-wide 128-bit min and max (every lane gets them).
+__device__ __forceinline__ void k128_warp_minmax(unsigned long long &mnl, unsigned long long &mnh,
+                                                 unsigned long long &mxl, unsigned long long &mxh)
+{
+    for (int o = 16; o; o >>= 1) {
+        const unsigned long long al = __shfl_xor_sync(0xffffffffu, mnl, o), ah = __shfl_xor_sync(0xffffffffu, mnh, o);
+        const unsigned long long bl = __shfl_xor_sync(0xffffffffu, mxl, o), bh = __shfl_xor_sync(0xffffffffu, mxh, o);
+        if (lt128(al, ah, mnl, mnh)) mnl = al, mnh = ah;
+        if (lt128(mxl, mxh, bl, bh)) mxl = bl, mxh = bh;
+    }
+}
+
+// Per block: the 128-bit min and max of its keys, as (lo, hi, lo, hi) in part[4b..].
+__global__ void k128_minmax(const uint64_t *keys, unsigned long long n, unsigned long long *part)
+{
+    __shared__ unsigned long long sm[4][BLOCK / 32];
+    unsigned long long mnl = ~0ull, mnh = ~0ull, mxl = 0, mxh = 0;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long lo = keys[2 * i], hi = keys[2 * i + 1];
+        if (lt128(lo, hi, mnl, mnh)) mnl = lo, mnh = hi;
+        if (lt128(mxl, mxh, lo, hi)) mxl = lo, mxh = hi;
+    }
+    k128_warp_minmax(mnl, mnh, mxl, mxh);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) sm[0][warp] = mnl, sm[1][warp] = mnh, sm[2][warp] = mxl, sm[3][warp] = mxh;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < BLOCK / 32; w++) {
+            if (lt128(sm[0][w], sm[1][w], mnl, mnh)) mnl = sm[0][w], mnh = sm[1][w];
+            if (lt128(mxl, mxh, sm[2][w], sm[3][w])) mxl = sm[2][w], mxh = sm[3][w];
+        }
+        unsigned long long *p = part + 4ull * blockIdx.x;
+        p[0] = mnl, p[1] = mnh, p[2] = mxl, p[3] = mxh;
+    }
+}
+
+// One block of 1024 threads: the min and max over the blocks' parts, and the
+// window shift.
+__global__ void k128_window_shift(const unsigned long long *part, uint32_t nparts, U128Win *W)
+{
+    __shared__ unsigned long long sm[4][32];
+    unsigned long long mnl = ~0ull, mnh = ~0ull, mxl = 0, mxh = 0;
+    for (uint32_t b = threadIdx.x; b < nparts; b += blockDim.x) {
+        const unsigned long long *p = part + 4ull * b;
+        if (lt128(p[0], p[1], mnl, mnh)) mnl = p[0], mnh = p[1];
+        if (lt128(mxl, mxh, p[2], p[3])) mxl = p[2], mxh = p[3];
+    }
+    k128_warp_minmax(mnl, mnh, mxl, mxh);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) sm[0][warp] = mnl, sm[1][warp] = mnh, sm[2][warp] = mxl, sm[3][warp] = mxh;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    for (int w = 1; w < (int)(blockDim.x >> 5); w++) {
+        if (lt128(sm[0][w], sm[1][w], mnl, mnh)) mnl = sm[0][w], mnh = sm[1][w];
+        if (lt128(mxl, mxh, sm[2][w], sm[3][w])) mxl = sm[2][w], mxh = sm[3][w];
+    }
+    const unsigned long long dl = mxl - mnl, dh = mxh - mnh - (mxl < mnl ? 1ull : 0ull);
+    const uint32_t bits = dh ? 128u - (uint32_t)__clzll((long long)dh) : 64u - (uint32_t)__clzll((long long)dl);
+    W->mn_lo = mnl;
+    W->mn_hi = mnh;
+    W->s = bits > 64u ? bits - 64u : 0u;
+    W->tied = 0;
+    W->groups = 0;
+}
+
+// d = key - min in 128 bits; the window d >> s and the remainder below it.
+__device__ __forceinline__ void k128_split_key(unsigned long long lo, unsigned long long hi, const U128Win &W,
+                                               unsigned long long *win, unsigned long long *rem)
+{
+    const unsigned long long dl = lo - W.mn_lo, dh = hi - W.mn_hi - (lo < W.mn_lo ? 1ull : 0ull);
+    const uint32_t s = W.s;
+    if (s == 0) {
+        *win = dl;  // dh == 0: the range fits 64 bits
+        *rem = 0;
+    } else if (s == 64) {
+        *win = dh;
+        *rem = dl;
+    } else {
+        *win = (dl >> s) | (dh << (64u - s));
+        *rem = dl & ((1ull << s) - 1ull);
+    }
+}
+
+// The window of every key with its input index, and a copy of the keys and
+// payloads as records (the final gather's source): (lo, hi) with no
+// payloads, (lo, hi, payload, 0) with them, so that one record is one
+// 16- or 32-byte aligned piece and the gather reads one sector a key.
+__global__ void k128_window(const uint64_t *keys, const uint32_t *vals, unsigned long long n, const U128Win *Wp,
+                            uint64_t *win, uint32_t *idx, uint64_t *rec)
+{
+    const U128Win W = *Wp;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long lo = keys[2 * i], hi = keys[2 * i + 1];
+        unsigned long long w, r;
+        k128_split_key(lo, hi, W, &w, &r);
+        win[i] = w;
+        idx[i] = (uint32_t)i;
+        if (vals) {
+            ulonglong2 *p = reinterpret_cast<ulonglong2 *>(rec + 4 * i);
+            p[0] = make_ulonglong2(lo, hi);
+            p[1] = make_ulonglong2((unsigned long long)vals[i], 0ull);
+        } else {
+            reinterpret_cast<ulonglong2 *>(rec)[i] = make_ulonglong2(lo, hi);
+        }
+    }
+}
+
+// Runs of equal windows in the sorted windows: element i of a run of two or
+// more counts as tied (low 32 bits) and, if it starts the run, as a run head
+// (high 32 bits).  TIE_PER consecutive elements per thread.
+constexpr int TIE_PER = 16;
+constexpr unsigned long long TIE_TILE = (unsigned long long)BLOCK * TIE_PER;
+__device__ __forceinline__ unsigned long long k128_tie_bits(const uint64_t *win, unsigned long long n,
+                                                            unsigned long long i)
+{
+    const unsigned long long w = win[i];
+    const bool eqp = i > 0 && win[i - 1] == w, eqn = i + 1 < n && win[i + 1] == w;
+    const bool tied = eqp || eqn;
+    return (tied ? 1ull : 0ull) | (tied && !eqp ? 1ull << 32 : 0ull);
+}
+
+// Block-wide exclusive scan of one value per thread; returns the block total.
+__device__ __forceinline__ unsigned long long k128_block_scan(unsigned long long v, unsigned long long *excl,
+                                                             unsigned long long *wsum)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    unsigned long long before = 0, total = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+        before += w < warp ? wsum[w] : 0ull;
+        total += wsum[w];
+    }
+    __syncthreads();
+    *excl = before + x - v;
+    return total;
+}
+
+// The block's count (the same TIE_TILE elements as k128_tie_emit's block,
+// read here in coalesced rows: the count needs no order).
+__global__ void k128_tie_count(const uint64_t *win, unsigned long long n, const U128Win *Wp, unsigned long long *bsum)
+{
+    __shared__ unsigned long long wsum[BLOCK / 32];
+    unsigned long long c = 0;
+    if (Wp->s != 0) {  // s == 0: equal windows are equal keys, already in input order
+        const unsigned long long i0 = blockIdx.x * TIE_TILE + threadIdx.x;
+#pragma unroll 4
+        for (int u = 0; u < TIE_PER; u++) {
+            const unsigned long long i = i0 + (unsigned long long)u * BLOCK;
+            if (i < n) c += k128_tie_bits(win, n, i);
+        }
+    }
+    unsigned long long excl;
+    const unsigned long long t = k128_block_scan(c, &excl, wsum);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = t;
+}
+
+// One block: exclusive scan of the block counts; the totals into W.
+__global__ void k128_tie_scan(unsigned long long *bsum, unsigned long long nb, U128Win *W)
+{
+    __shared__ unsigned long long wsum[32];
+    const unsigned long long per = (nb + blockDim.x - 1) / blockDim.x, b0 = threadIdx.x * per;
+    unsigned long long sum = 0;
+    for (unsigned long long b = b0; b < b0 + per && b < nb; b++) sum += bsum[b];
+    unsigned long long excl;
+    const unsigned long long total = k128_block_scan(sum, &excl, wsum);
+    for (unsigned long long b = b0; b < b0 + per && b < nb; b++) {
+        const unsigned long long v = bsum[b];
+        bsum[b] = excl;
+        excl += v;
+    }
+    if (threadIdx.x == 0) {
+        W->tied = total & 0xffffffffull;
+        W->groups = total >> 32;
+    }
+}
+
+// The tied keys, compacted in sorted order: remainder, sorted position (the
+// segmented sort's payload, and a second copy that it leaves in place), and
+// each run's start as a segment offset.
+__global__ void k128_tie_emit(const uint64_t *win, const uint32_t *idx, const uint64_t *rec, uint32_t rs,
+                              unsigned long long n, const unsigned long long *bofs, const U128Win *Wp, uint64_t *ck,
+                              uint32_t *cv, uint32_t *pre, uint64_t *off)
+{
+    __shared__ unsigned long long wsum[BLOCK / 32];
+    const U128Win W = *Wp;
+    const unsigned long long i0 = blockIdx.x * TIE_TILE + (unsigned long long)threadIdx.x * TIE_PER;
+    unsigned long long bits[TIE_PER], c = 0;
+#pragma unroll
+    for (int u = 0; u < TIE_PER; u++) {
+        bits[u] = i0 + u < n ? k128_tie_bits(win, n, i0 + u) : 0ull;
+        c += bits[u];
+    }
+    unsigned long long pos;
+    k128_block_scan(c, &pos, wsum);
+    pos += bofs[blockIdx.x];
+#pragma unroll
+    for (int u = 0; u < TIE_PER; u++) {
+        if (bits[u] & 1ull) {
+            const unsigned long long i = i0 + u, src = idx[i];
+            const uint32_t j = (uint32_t)(pos & 0xffffffffull);
+            unsigned long long w, r;
+            k128_split_key(rec[rs * src], rec[rs * src + 1], W, &w, &r);
+            ck[j] = r;
+            cv[j] = (uint32_t)i;
+            pre[j] = (uint32_t)i;
+            if (bits[u] >> 32) off[pos >> 32] = j;
+        }
+        pos += bits[u];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) off[W.groups] = W.tied;
+}
+
+// After the runs are sorted by remainder: the index of each tied position,
+// through a copy (gather, then scatter) so that no thread reads an entry
+// another one rewrites.
+__global__ void k128_tie_gather(const uint32_t *cv, const uint32_t *idx, unsigned long long t, uint32_t *tmp)
+{
+    for (unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; j < t;
+         j += (unsigned long long)gridDim.x * blockDim.x)
+        tmp[j] = idx[cv[j]];
+}
+__global__ void k128_tie_place(const uint32_t *pre, const uint32_t *tmp, unsigned long long t, uint32_t *idx)
+{
+    for (unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; j < t;
+         j += (unsigned long long)gridDim.x * blockDim.x)
+        idx[pre[j]] = tmp[j];
+}
+
+// The keys and payloads in sorted order, into the caller's arrays.
+__global__ void k128_gather(const uint64_t *rec, const uint32_t *idx, unsigned long long n, uint64_t *keys,
+                            uint32_t *vals)
 {
     for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * blockDim.x) {
-        lo[i] = keys[2 * i];
-        idx[i] = (uint32_t)i;
+        const unsigned long long src = idx[i];
+        if (vals) {
+            const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(rec + 4 * src);
+            const ulonglong2 kv = p[0], pv = p[1];
+            keys[2 * i] = kv.x;
+            keys[2 * i + 1] = kv.y;
+            vals[i] = (uint32_t)pv.x;
+        } else {
+            const ulonglong2 kv = reinterpret_cast<const ulonglong2 *>(rec)[src];
+            keys[2 * i] = kv.x;
+            keys[2 * i + 1] = kv.y;
+        }
     }
 }
-__global__ void k128_gather_hi(const uint64_t *keys, unsigned long long n, const uint32_t *idx, uint64_t *hi,
-                               uint32_t *pos)
+
+// The stream's 128-bit scratch, at least bytes long (kept between calls: the
+// call after the first one allocates nothing).  Growing it waits for the
+// stream, whose earlier calls may still use the old area.  Takes g_mu.
+int aux_scratch(cudaStream_t stream, size_t bytes, unsigned char **out)
 {
-    for (unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
-         j += (unsigned long long)gridDim.x * blockDim.x) {
-        hi[j] = keys[2 * (unsigned long long)idx[j] + 1];
-        pos[j] = (uint32_t)j;
+    std::lock_guard<std::mutex> lock(g_mu);
+    int dev = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce != cudaSuccess) return cuda_err(ce);
+    Workspace *ws = nullptr;
+    for (Workspace *w : g_ws)
+        if (w->device == dev && w->stream == stream) ws = w;
+    if (!ws) {
+        ws = new Workspace();
+        ws->device = dev;
+        ws->stream = stream;
+        g_ws.push_back(ws);
     }
-}
-__global__ void k128_gather_out(const uint64_t *keys, const uint32_t *vals, unsigned long long n,
-                                const uint32_t *idx, const uint32_t *pos, uint64_t *ok, uint32_t *ov)
-{
-    for (unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
-         j += (unsigned long long)gridDim.x * blockDim.x) {
-        const unsigned long long src = idx[pos[j]];
-        ok[2 * j] = keys[2 * src];
-        ok[2 * j + 1] = keys[2 * src + 1];
-        if (vals) ov[j] = vals[src];
+    if (ws->aux_bytes < bytes) {
+        if (ws->aux) {
+            ce = cudaStreamSynchronize(stream);
+            if (ce != cudaSuccess) return cuda_err(ce);
+            cudaFree(ws->aux);
+            ws->aux = nullptr;
+            ws->aux_bytes = 0;
+        }
+        ce = cudaMalloc(&ws->aux, bytes);
+        if (ce != cudaSuccess) {
+            cudaGetLastError();
+            ws->aux = nullptr;
+            return ZSORT_ERR_NOMEM;
+        }
+        ws->aux_bytes = bytes;
     }
+    *out = static_cast<unsigned char *>(ws->aux);
+    return ZSORT_OK;
 }
 
 Workspace *find_ws(cudaStream_t stream)
@@ -774,41 +1058,77 @@ int zsort_pairs_u128(uint64_t *keys, uint32_t *vals, uint64_t n, const zsort_opt
     if (n <= 1) return ZSORT_OK;
     if (!keys) return ZSORT_ERR_INVALID;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    // scratch: one 64-bit word and one index per key, twice the keys and the
-    // payloads for the gathered result
     auto a16 = [](size_t x) { return (x + 15) & ~size_t(15); };  // bulk copies want 16-byte bases
-    const size_t o_idx = a16(n * 8), o_pos = a16(o_idx + n * 4), o_ok = a16(o_pos + n * 4);
-    const size_t o_ov = o_ok + n * 16, bytes = o_ov + (vals ? n * 4 : 0);
-    unsigned char *t = nullptr;
-    cudaError_t ce = cudaMallocAsync(reinterpret_cast<void **>(&t), bytes, st);
-    if (ce != cudaSuccess) return cuda_err(ce);
-    uint64_t *word = reinterpret_cast<uint64_t *>(t);
-    uint32_t *idx = reinterpret_cast<uint32_t *>(t + o_idx);
-    uint32_t *pos = reinterpret_cast<uint32_t *>(t + o_pos);
-    uint64_t *ok = reinterpret_cast<uint64_t *>(t + o_ok);
-    uint32_t *ov = vals ? reinterpret_cast<uint32_t *>(t + o_ov) : nullptr;
     const unsigned int grid = (unsigned int)std::min<unsigned long long>(div_up(n, 256), 4096);
-    int rc = ZSORT_OK;
-    // 1. stable sort of (low word, index)
-    k128_split<<<grid, 256, 0, st>>>(keys, n, word, idx);
+    const unsigned int nparts = (unsigned int)std::min<unsigned long long>(div_up(n, 256), 1024);
+    const unsigned long long nb = div_up(n, TIE_TILE);
+    // scratch: records of keys (and payloads), windows, indices, block counts
+    const uint32_t rs = vals ? 4u : 2u;  // 64-bit words a record
+    const size_t o_win = a16(n * rs * 8), o_idx = a16(o_win + n * 8);
+    const size_t o_part = a16(o_idx + n * 4), o_bs = a16(o_part + (size_t)nparts * 32);
+    const size_t o_w = a16(o_bs + nb * 8), bytes = o_w + sizeof(U128Win);
+    unsigned char *t = nullptr;
+    int rc = aux_scratch(st, bytes, &t);
+    if (rc != ZSORT_OK) return rc;
+    cudaError_t ce = cudaSuccess;
+    uint64_t *rec = reinterpret_cast<uint64_t *>(t);  // 256-byte aligned: a record never spans a sector
+    uint64_t *win = reinterpret_cast<uint64_t *>(t + o_win);
+    uint32_t *idx = reinterpret_cast<uint32_t *>(t + o_idx);
+    unsigned long long *part = reinterpret_cast<unsigned long long *>(t + o_part);
+    unsigned long long *bsum = reinterpret_cast<unsigned long long *>(t + o_bs);
+    U128Win *W = reinterpret_cast<U128Win *>(t + o_w);
+    // 1. min, max and the window shift; every key's window; one stable zSort
+    //    of (window, input index)
+    k128_minmax<<<nparts, BLOCK, 0, st>>>(keys, n, part);
+    k128_window_shift<<<1, 1024, 0, st>>>(part, nparts, W);
+    k128_window<<<grid, 256, 0, st>>>(keys, vals, n, W, win, idx, rec);
     rc = cuda_err(cudaGetLastError());
-    if (rc == ZSORT_OK) rc = launch(word, idx, n, nullptr, 1, o, st);
-    // 2. stable sort of (high word in that order, position): equal high words
-    //    keep the low-word order, so the result orders (high, low, input index)
+    if (rc == ZSORT_OK) rc = launch(win, idx, n, nullptr, 1, o, st);
+    // 2. runs of equal windows (none for keys whose top 64 significant bits
+    //    differ): counted on the device, the counts read back once
+    U128Win hw{};
     if (rc == ZSORT_OK) {
-        k128_gather_hi<<<grid, 256, 0, st>>>(keys, n, idx, word, pos);
+        k128_tie_count<<<(unsigned int)nb, BLOCK, 0, st>>>(win, n, W, bsum);
+        k128_tie_scan<<<1, 1024, 0, st>>>(bsum, nb, W);
         rc = cuda_err(cudaGetLastError());
     }
-    if (rc == ZSORT_OK) rc = launch(word, pos, n, nullptr, 1, o, st);
-    // 3. the keys and payloads in that order, back into the caller's arrays
+    if (rc == ZSORT_OK) rc = cuda_err(cudaMemcpyAsync(&hw, W, sizeof(hw), cudaMemcpyDeviceToHost, st));
+    if (rc == ZSORT_OK) rc = cuda_err(cudaStreamSynchronize(st));
+    // 3. the tied keys, compacted, each run sorted by the remainder below the
+    //    window (one segmented zSort), their indices put back in that order
+    if (rc == ZSORT_OK && hw.tied) {
+        const unsigned long long T = hw.tied, G = hw.groups;
+        const size_t c_cv = a16(T * 8), c_pre = a16(c_cv + T * 4), c_tmp = a16(c_pre + T * 4);
+        const size_t c_off = a16(c_tmp + T * 4), cbytes = c_off + (G + 1) * 8;
+        unsigned char *c = nullptr;
+        ce = cudaMallocAsync(reinterpret_cast<void **>(&c), cbytes, st);
+        if (ce != cudaSuccess) {
+            rc = cuda_err(ce);
+        } else {
+            uint64_t *ck = reinterpret_cast<uint64_t *>(c);
+            uint32_t *cv = reinterpret_cast<uint32_t *>(c + c_cv);
+            uint32_t *pre = reinterpret_cast<uint32_t *>(c + c_pre);
+            uint32_t *tmp = reinterpret_cast<uint32_t *>(c + c_tmp);
+            uint64_t *off = reinterpret_cast<uint64_t *>(c + c_off);
+            const unsigned int tg = (unsigned int)std::min<unsigned long long>(div_up(T, 256), 4096);
+            k128_tie_emit<<<(unsigned int)nb, BLOCK, 0, st>>>(win, idx, rec, rs, n, bsum, W, ck, cv, pre, off);
+            rc = cuda_err(cudaGetLastError());
+            if (rc == ZSORT_OK) rc = launch(ck, cv, T, off, G, o, st);
+            if (rc == ZSORT_OK) {
+                k128_tie_gather<<<tg, 256, 0, st>>>(cv, idx, T, tmp);
+                k128_tie_place<<<tg, 256, 0, st>>>(pre, tmp, T, idx);
+                rc = cuda_err(cudaGetLastError());
+            }
+            const int rf = cuda_err(cudaFreeAsync(c, st));
+            if (rc == ZSORT_OK) rc = rf;
+        }
+    }
+    // 4. keys and payloads in that order, into the caller's arrays
     if (rc == ZSORT_OK) {
-        k128_gather_out<<<grid, 256, 0, st>>>(keys, vals, n, idx, pos, ok, ov);
+        k128_gather<<<grid, 256, 0, st>>>(rec, idx, n, keys, vals);
         rc = cuda_err(cudaGetLastError());
     }
-    if (rc == ZSORT_OK) rc = cuda_err(cudaMemcpyAsync(keys, ok, n * 16, cudaMemcpyDeviceToDevice, st));
-    if (rc == ZSORT_OK && vals) rc = cuda_err(cudaMemcpyAsync(vals, ov, n * 4, cudaMemcpyDeviceToDevice, st));
-    const int rf = cuda_err(cudaFreeAsync(t, st));
-    return rc != ZSORT_OK ? rc : rf;
+    return rc;
 }
 
 int zsort_keys(uint64_t *keys, uint64_t n, zsort_stream_t stream)
@@ -879,6 +1199,7 @@ int zsort_release(void)
         if (w->graph.valid) cudaGraphExecDestroy(w->graph.exec);
         if (w->block && cudaFree(w->block) != cudaSuccess) rc = ZSORT_ERR_CUDA;
         if (w->trace && cudaFree(w->trace) != cudaSuccess) rc = ZSORT_ERR_CUDA;
+        if (w->aux && cudaFree(w->aux) != cudaSuccess) rc = ZSORT_ERR_CUDA;
         delete w;
     }
     g_ws.swap(keep);

@@ -512,6 +512,53 @@ def test_u128_keys_match_the_stable_order(n, hi_d, lo_d, with_vals):
         assert np.array_equal(v.cpu().numpy().view(np.uint32), order.astype(np.uint32))
 
 
+def u128_window_case(n, s, nwin, seed, dup):
+    """Keys min + (w << s | r) with w drawn from nwin windows (0 and 2^64 - 1
+    among them, so that the range's bit length is 64 + s) and r below 2^s:
+    runs of equal windows resolved by the bits below them; dup draws r from
+    five values, so that equal keys repeat."""
+    rng = np.random.default_rng(seed)
+    wins = rng.integers(0, 2 ** 64, nwin, dtype=np.uint64, endpoint=False)
+    wins[0] = 0
+    if nwin > 1:
+        wins[-1] = np.uint64(2 ** 64 - 1)
+    w = rng.choice(wins, n)
+    r = rng.integers(0, 2 ** s, n, dtype=np.uint64, endpoint=False) if s < 64 else \
+        rng.integers(0, 2 ** 64, n, dtype=np.uint64, endpoint=False)
+    if dup:
+        r = r % np.uint64(5)
+    if s == 64:
+        dhi, dlo = w, r
+        mn_lo = np.uint64(0)
+    else:
+        dlo = (w << np.uint64(s)) | r
+        dhi = w >> np.uint64(64 - s)
+        mn_lo = np.uint64(rng.integers(0, 2 ** 64, dtype=np.uint64, endpoint=False))
+    lo = dlo + mn_lo
+    hi = dhi + (lo < mn_lo).astype(np.uint64)
+    return hi, lo
+
+
+@pytest.mark.parametrize("s", [1, 17, 40, 63, 64])
+@pytest.mark.parametrize("nwin,dup", [(2, False), (100, False), (150_000, False), (100, True)])
+def test_u128_window_runs_resolved_below_the_window(s, nwin, dup):
+    """The 128-bit path's tie resolution: many keys share a 64-bit window
+    (two runs of half the keys each, 100 long runs, ~150,000 short ones, and
+    equal keys repeated), at window shifts 1..64; the result is numpy's
+    stable lexsort on (high, low), keys and payloads."""
+    n = 300_001
+    hi, lo = u128_window_case(n, s, nwin, 1000 * s + nwin, dup)
+    words = np.empty(2 * n, dtype=np.uint64)
+    words[0::2], words[1::2] = lo, hi
+    k = torch.from_numpy(words.view(np.int64)).to(DEV)
+    v = torch.arange(n, dtype=torch.int32, device=DEV)
+    z.sort_pairs_u128(k, v)
+    order = np.lexsort((lo, hi))
+    got = k.cpu().numpy().view(np.uint64)
+    assert np.array_equal(got[0::2], lo[order]) and np.array_equal(got[1::2], hi[order])
+    assert np.array_equal(v.cpu().numpy().view(np.uint32), order.astype(np.uint32))
+
+
 def test_leaf_with_interleaved_repeated_keys_takes_the_network():
     """Leaves whose sub-buckets mix two adjacent keys, each repeated ~1500
     times in random order (the insertion sort's move budget runs out), plus
