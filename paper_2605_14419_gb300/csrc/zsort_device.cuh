@@ -695,7 +695,7 @@ struct LeafBuf {
 struct LeafArea {
     LeafBuf leaf;
     uint16_t sidx[LEAF_CAP];
-    uint32_t cnt[LEAF_M2_MAX + 1];
+    __align__(16) uint32_t cnt[LEAF_M2_MAX + 1];
 };
 
 constexpr int KEY_STAGES = 3;  // key-only streams: tiles in flight per CTA
@@ -732,6 +732,7 @@ static_assert(sizeof(KeyRing) <= sizeof(TileBuf) * SC_STAGES, "the key stages fi
 static_assert(sizeof(ChildList) <= sizeof(TileBuf) * SC_STAGES, "child lists fit the tile buffers");
 static_assert(sizeof(SmemTile) <= 112 * 1024, "two CTAs per SM");
 static_assert(IPT % 2 == 0, "the statistics loop takes the slots in pairs");
+static_assert(LEAF_M2_MAX <= 8 * BLOCK && LEAF_M2_MAX % 8 == 0, "the leaf's sub-bucket scan: 8 counters a thread");
 
 // ------------------------------------------------------------ block scan
 // Exclusive scan of in[0..nb) into out (may alias); returns the total.
@@ -780,62 +781,51 @@ __device__ uint32_t block_exclusive_scan(const uint32_t *in, uint32_t *out, uint
     return total;
 }
 
-// In-place exclusive scan of a[0..nb) by rows of 32 consecutive entries:
-// every warp takes a run of rows, lane l reads entry l of a row (no bank
-// conflicts), first summing its warp's rows, then -- once the warps' totals
-// are known -- scanning them with a running offset.  SCAN_ROWS rows are in
-// flight at a time, so their loads, reductions and shuffles overlap.
-// Returns the total.
-constexpr int SCAN_ROWS = 4;
-__device__ uint32_t block_exclusive_scan_rows(uint32_t *a, uint32_t nb, uint32_t *wsum)
+// In-place exclusive scan of a[0..nb) (nb a multiple of 8, at most
+// 8 * BLOCK; a 16-byte aligned): thread t owns a[8t, 8t + 8), read and
+// written as two 16-byte vectors (a warp's vector accesses meet each bank
+// once per 128 bytes), then one warp scan of the threads' sums and one
+// barrier for the warps' totals.  a[nb] receives the total, which is also
+// returned.
+__device__ uint32_t block_exclusive_scan_vec8(uint32_t *a, uint32_t nb, uint32_t *wsum)
 {
-    const uint32_t full = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t rows = (nb + 31) / 32, per = (rows + WARPS - 1) / WARPS;
-    const uint32_t r0 = min(rows, warp * per), r1 = min(rows, r0 + per);
-    uint32_t tot = 0;
-    for (uint32_t r = r0; r < r1; r += SCAN_ROWS) {
-        uint32_t v[SCAN_ROWS];
-#pragma unroll
-        for (int g = 0; g < SCAN_ROWS; g++) {
-            const uint32_t idx = (r + g) * 32 + lane;
-            v[g] = r + g < r1 && idx < nb ? a[idx] : 0u;
-        }
-#pragma unroll
-        for (int g = 0; g < SCAN_ROWS; g++) tot += __reduce_add_sync(full, v[g]);
+    const uint32_t b = threadIdx.x * 8u;
+    uint4 x0 = make_uint4(0u, 0u, 0u, 0u), x1 = x0;
+    if (b < nb) {
+        x0 = reinterpret_cast<const uint4 *>(a + b)[0];
+        x1 = reinterpret_cast<const uint4 *>(a + b)[1];
     }
-    if (lane == 0) wsum[warp] = tot;
+    const uint32_t sum = x0.x + x0.y + x0.z + x0.w + x1.x + x1.y + x1.z + x1.w;
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[warp] = incl;
     __syncthreads();
-    uint32_t run = 0, total = 0;
+    uint32_t run = incl - sum, total = 0;
 #pragma unroll
     for (int w = 0; w < WARPS; w++) {
         const uint32_t ws = wsum[w];
         run += w < warp ? ws : 0u;
         total += ws;
     }
-    for (uint32_t r = r0; r < r1; r += SCAN_ROWS) {
-        uint32_t v[SCAN_ROWS], x[SCAN_ROWS];
-#pragma unroll
-        for (int g = 0; g < SCAN_ROWS; g++) {
-            const uint32_t idx = (r + g) * 32 + lane;
-            v[g] = r + g < r1 && idx < nb ? a[idx] : 0u;
-            x[g] = v[g];
-        }
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-#pragma unroll
-            for (int g = 0; g < SCAN_ROWS; g++) {
-                const uint32_t y = __shfl_up_sync(full, x[g], o);
-                if (lane >= o) x[g] += y;
-            }
-        }
-#pragma unroll
-        for (int g = 0; g < SCAN_ROWS; g++) {
-            const uint32_t idx = (r + g) * 32 + lane;
-            if (r + g < r1 && idx < nb) a[idx] = run + x[g] - v[g];
-            run += __shfl_sync(full, x[g], 31);
-        }
+    if (b < nb) {
+        uint4 y0, y1;
+        y0.x = run; run += x0.x;
+        y0.y = run; run += x0.y;
+        y0.z = run; run += x0.z;
+        y0.w = run; run += x0.w;
+        y1.x = run; run += x1.x;
+        y1.y = run; run += x1.y;
+        y1.z = run; run += x1.z;
+        y1.w = run;
+        reinterpret_cast<uint4 *>(a + b)[0] = y0;
+        reinterpret_cast<uint4 *>(a + b)[1] = y1;
     }
+    if (threadIdx.x == 0) a[nb] = total;
     __syncthreads();
     return total;
 }

@@ -2022,8 +2022,7 @@ __device__ __forceinline__ void finish_fast(SmemTile &s, unsigned long long *key
 {
     uint32_t *cnt = s.u.la.cnt;
     uint16_t *sidx = s.u.la.sidx;  // leaf position of each staged pair
-    if (threadIdx.x == 0) cnt[M2] = len;  // sentinel: end of the last sub-bucket
-    block_exclusive_scan_rows(cnt, M2, s.wsum);
+    block_exclusive_scan_vec8(cnt, M2, s.wsum);  // and cnt[M2] = len: the end of the last sub-bucket
 #pragma unroll
     for (int j = 0; j < LEAF_IPT; j++) {
         const uint32_t p = threadIdx.x + j * BLOCK;
