@@ -59,6 +59,7 @@ __global__ void __launch_bounds__(BLOCK, 2) k_persistent(const __grid_constant__
     extern __shared__ __align__(128) unsigned char smraw[];
     SmemTile &s = *reinterpret_cast<SmemTile *>(smraw);
     if (threadIdx.x == 0) {
+        s.drain = 0u;
         for (int w = 0; w < KEY_STAGES; w++) mbar_init(&s.bar[w]);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }

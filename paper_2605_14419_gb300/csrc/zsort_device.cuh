@@ -724,6 +724,7 @@ struct SmemTile {
     unsigned long long bar[KEY_STAGES];  // mbarriers of the tile buffers / key stages
     uint32_t task[8];
     uint32_t flag, flag2, n_leaf, n_med, n_large, n_large_ok, item_base, e_base, span_max;
+    uint32_t drain;  // scatter: warps done with the current tile's buffer (0 between tiles)
     unsigned long long red64[WARPS * 2];
 };
 static_assert(SC_STAGES <= KEY_STAGES, "one mbarrier per streamed tile buffer");
@@ -1064,6 +1065,18 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p)
 __device__ __forceinline__ void mbar_init(unsigned long long *bar)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+// Hint: bring the u16 entries [e0, e1) of arr into L2 with one bulk
+// prefetch, trimmed to whole 16-byte pieces inside that range (the bulk
+// prefetch wants a 16-byte aligned address and size; arr is 16-byte aligned).
+__device__ __forceinline__ void bulk_prefetch_l2_inside(const uint16_t *arr, unsigned long long e0,
+                                                        unsigned long long e1)
+{
+    const unsigned long long b0 = (e0 * 2ull + 15ull) & ~15ull, b1 = (e1 * 2ull) & ~15ull;
+    if (b1 > b0)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(reinterpret_cast<const char *>(arr) + b0),
+                     "r"((uint32_t)(b1 - b0))
+                     : "memory");
 }
 __device__ __forceinline__ void fence_proxy_async()
 {

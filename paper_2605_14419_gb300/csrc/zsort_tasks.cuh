@@ -631,10 +631,13 @@ __device__ __noinline__ void hist_stream(const Params &P, SmemTile &s, Pipe &pp,
 // tile's own buffer with their buckets, then write each bucket's run at its
 // cursor (coalesced within runs; a staged bucket is cheaper to read back
 // than any map is to recompute).  Tiles stream through a ring of SC_STAGES
-// buffers: once every thread has left tile t - 1 (the first of the tile's
-// four barriers), its buffer takes the bulk copy of tile t + SC_STAGES - 1,
-// which streams in while tile t is ranked, staged and written.  Each warp
-// clears its own bucket counters.
+// buffers: the last warp to finish writing tile t out (a counter in shared
+// memory, no CTA barrier) refills its buffer with the bulk copy of tile
+// t + SC_STAGES, which then has the whole of tile t + 1 to arrive.  Where
+// the buckets come from the histogram pass (IDS), the same warp also
+// prefetches that tile's bucket ids into L2, since their loads at the top
+// of the tile no longer wait behind a copy.  Each warp clears its own
+// bucket counters.
 template <int NI, bool IDS, bool KV>
 __device__ __noinline__ void scatter_stream(const Params &P, SmemTile &s, Pipe &pp, const uint64_t *srck,
                                             const uint32_t *srcv, bool bulk, unsigned long long start,
@@ -657,7 +660,7 @@ __device__ __noinline__ void scatter_stream(const Params &P, SmemTile &s, Pipe &
     const bool table = 8u * 32u * NI >= 16u + 4u * k;
     rank_zero_warp(k, s);
     if (bulk && threadIdx.x == 0)
-        for (uint32_t t = 0; t < SC_STAGES - 1 && t < nt; t++)
+        for (uint32_t t = 0; t < SC_STAGES && t < nt; t++)
             stream_issue<KV>(P, s, (int)t, srck, srcv, start + (unsigned long long)t * TL, tile_cnt(t));
     bool err = false;
     for (uint32_t t = 0; t < nt; t++) {
@@ -720,18 +723,13 @@ __device__ __noinline__ void scatter_stream(const Params &P, SmemTile &s, Pipe &
             // wait before leaving, so that no copy lands in a reused buffer
             if (bulk) {
                 mbar_wait(&s.bar[w], (pp.uses[w] - 1u) & 1u, P.wait_ns);
-                for (uint32_t tn = t + 1; tn < nt && tn < t + SC_STAGES - 1; tn++) {
+                for (uint32_t tn = t + 1; tn < nt && tn < t + SC_STAGES; tn++) {  // issued in earlier tiles
                     const int wn = (int)(tn % SC_STAGES);
                     mbar_wait(&s.bar[wn], pp.uses[wn] & 1u, P.wait_ns);
                 }
             }
             err = true;
             break;
-        }
-        if (bulk && t + SC_STAGES - 1 < nt && threadIdx.x == 0) {
-            const uint32_t tn = t + SC_STAGES - 1;
-            stream_issue<KV>(P, s, (int)(tn % SC_STAGES), srck, srcv, start + (unsigned long long)tn * TL,
-                             tile_cnt(tn));
         }
         rank_scan<true>(k, s);
         rank_place<NI>(b, pos, s);
@@ -760,6 +758,23 @@ __device__ __noinline__ void scatter_stream(const Params &P, SmemTile &s, Pipe &
             }
         }
         fence_proxy_async();  // this thread's smem accesses before the buffer's next bulk write
+        // the last warp out of this tile's buffer refills it with tile
+        // t + SC_STAGES (the branch is uniform over the CTA: every warp
+        // arrives, and the counter is back at 0 for the next tile)
+        if (bulk && t + SC_STAGES < nt) {
+            __syncwarp();
+            if ((threadIdx.x & 31) == 0) {
+                __threadfence_block();
+                if (atomicAdd(&s.drain, 1u) == (uint32_t)WARPS - 1u) {
+                    s.drain = 0u;
+                    __threadfence_block();
+                    const uint32_t tn = t + SC_STAGES;
+                    const unsigned long long e0 = start + (unsigned long long)tn * TL;
+                    stream_issue<KV>(P, s, w, srck, srcv, e0, tile_cnt(tn));
+                    if (IDS) bulk_prefetch_l2_inside(P.ids, e0, e0 + tile_cnt(tn));
+                }
+            }
+        }
     }
     if (err) set_error(P, ST_TIMEOUT);
     __syncthreads();
