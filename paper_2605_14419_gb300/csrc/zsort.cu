@@ -60,6 +60,8 @@ __global__ void __launch_bounds__(BLOCK, 2) k_persistent(const __grid_constant__
     SmemTile &s = *reinterpret_cast<SmemTile *>(smraw);
     if (threadIdx.x == 0) {
         s.drain = 0u;
+        s.local_base = 0u;
+        s.local_n = 0u;
         for (int w = 0; w < KEY_STAGES; w++) mbar_init(&s.bar[w]);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -69,9 +71,22 @@ __global__ void __launch_bounds__(BLOCK, 2) k_persistent(const __grid_constant__
     unsigned long long t_idle0 = 0, t_task0 = 0, t_task1 = 0;
     const uint32_t ep = threadIdx.x < 32 ? call_epoch(P) : 0u;  // this call's queue epoch (set before launch)
     for (;;) {
-        if (threadIdx.x < 32) {  // warp 0 finds the next work
+        if (threadIdx.x < 32) {  // warp 0 finds the next work: this CTA's stash first, then the queue
             t_idle0 = globaltimer();
-            dequeue(P, ep, s.task);
+            uint32_t local = 0;
+            if (threadIdx.x == 0 && s.local_n) {
+                const uint32_t c = min(s.local_n, (uint32_t)LOCAL_CLAIM);
+                s.task[0] = T_FINISH;
+                s.task[1] = s.local_base;
+                s.task[2] = 0;
+                s.task[3] = INVALID;  // no queue entry
+                s.task[4] = 0;
+                s.task[5] = c;
+                s.local_base += c;
+                s.local_n -= c;
+                local = 1;
+            }
+            if (!__shfl_sync(0xffffffffu, local, 0)) dequeue(P, ep, s.task);
             t_task0 = globaltimer();
             if (threadIdx.x == 0) {
                 atomicAdd(&P.ctl->idle_ns, t_task0 - t_idle0);
@@ -116,8 +131,12 @@ __global__ void __launch_bounds__(BLOCK, 2) k_persistent(const __grid_constant__
             atomicAdd(&P.ctl->task_ns[ti], t1 - t_task0);
             atomicAdd(&P.ctl->task_cnt[ti], (unsigned long long)count);
             __threadfence();
-            uint32_t old = atomicAdd(&P.tdone[e], count);
-            s.flag2 = (old + count == ntiles) ? 1u : 0u;
+            if (e != INVALID) {
+                const uint32_t old = atomicAdd(&P.tdone[e], count);
+                s.flag2 = (old + count == ntiles) ? 1u : 0u;
+            } else {
+                s.flag2 = 0u;  // stashed leaves: no entry, no completion work
+            }
             atomicAdd(&P.ctl->progress, 1ull);
             atomicAdd(&P.ctl->tasks, (unsigned long long)count);
         }

@@ -66,6 +66,7 @@ enum TaskType : uint32_t {
                      // after both the statistics and the sample)
     T_SSTATS = 10    // large sub-array: statistics and Eq. 1 map from a sample (one CTA)
 };
+constexpr uint32_t LOCAL_CLAIM = 8;  // stashed leaves taken per task (the next one is prefetched)
 constexpr uint32_t SUB_SAMPLE = 4096;     // keys of a sub-array's statistics sample
 
 // ---------------------------------------------------------------- records
@@ -725,6 +726,7 @@ struct SmemTile {
     uint32_t task[8];
     uint32_t flag, flag2, n_leaf, n_med, n_large, n_large_ok, item_base, e_base, span_max;
     uint32_t drain;  // scatter: warps done with the current tile's buffer (0 between tiles)
+    uint32_t local_base, local_n;  // leaves a medium partition kept for this CTA: items [base, base + n)
     unsigned long long red64[WARPS * 2];
 };
 static_assert(SC_STAGES <= KEY_STAGES, "one mbarrier per streamed tile buffer");

@@ -827,7 +827,8 @@ __device__ void scatter_dispatch(const Params &P, SmemTile &s, Pipe &pp, const u
 // lumped with its neighbours level after level -- is partitioned with the
 // exact range map, which separates the other values from it at once.
 __device__ __noinline__ void classify_children(const Params &P, unsigned long long poff, uint32_t k,
-                                  uint32_t child_buf, uint32_t child_level, uint32_t plen, SmemTile &s)
+                                  uint32_t child_buf, uint32_t child_level, uint32_t plen, SmemTile &s,
+                                  bool keep_leaves = false)
 {
     ChildList &L = s.u.children;
     // 1. thread 0 walks the buckets in order: leaf groups, medium and large
@@ -1002,7 +1003,10 @@ __device__ __noinline__ void classify_children(const Params &P, unsigned long lo
         }
         s.red64[2] = e;
         s.red64[3] = ((unsigned long long)cnt << 32) | nsample;
-        if (nl) {
+        if (nl && keep_leaves) {  // finished by this CTA next, from its stash
+            s.local_base = base;
+            s.local_n = nl;
+        } else if (nl) {
             const uint32_t el = q_reserve(P, 1, queue_of(T_FINISH));
             if (el != INVALID) {
                 q_write(P, el, T_FINISH, base, nl);
@@ -1934,7 +1938,9 @@ __device__ __noinline__ void task_mpart(const Params &P, const Item it, SmemTile
         atomicAdd(&P.ctl->bytes, (16ull + 2ull * elem_bytes(P)) * len);
         note_level(P, level);
     }
-    classify_children(P, off, k, buf ^ 1u, level + 1, len, s);
+    // the leaves stay with this CTA: they are few, still in L2, and one small
+    // queue entry per medium made the leaf phase's claims contend
+    classify_children(P, off, k, buf ^ 1u, level + 1, len, s, true);
 }
 
 // ------------------------------------------------------------ FINISH
