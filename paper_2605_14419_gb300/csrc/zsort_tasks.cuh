@@ -1938,9 +1938,13 @@ __device__ __noinline__ void task_mpart(const Params &P, const Item it, SmemTile
         atomicAdd(&P.ctl->bytes, (16ull + 2ull * elem_bytes(P)) * len);
         note_level(P, level);
     }
-    // the leaves stay with this CTA: they are few, still in L2, and one small
-    // queue entry per medium made the leaf phase's claims contend
-    classify_children(P, off, k, buf ^ 1u, level + 1, len, s, true);
+    // the leaves stay with this CTA (still in L2) when the medium is small
+    // against a CTA's share of the whole call: there are then many mediums,
+    // and one small queue entry each made the leaf phase's claims contend.
+    // In a small call a medium's leaves go to the queue, where other CTAs
+    // can take them at once.
+    const bool keep = (unsigned long long)len * P.nctas * 4ull <= P.n;
+    classify_children(P, off, k, buf ^ 1u, level + 1, len, s, keep);
 }
 
 // ------------------------------------------------------------ FINISH
