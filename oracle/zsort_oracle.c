@@ -26,7 +26,7 @@
  *                            the learned map with exact-key breakpoints, the
  *                            second choice when the FP32 normalisation of the
  *                            first collapses the keys (not in the paper;
- *                            restated from its written definition below)
+ *                            reading R12)
  *   oracle_mlp_train, oracle_mlp_bucket
  *                            the alternative learned map: a 2-layer MLP with
  *                            positive weights fitted to the same quantile
@@ -68,6 +68,16 @@
  *       fixed positive number), so either sorts exactly; they can differ in
  *       the last bit of frac and so in the bucket of a key that sits on a
  *       sub-bucket edge.  The stored-slope form is the definition here.
+ *   R12 The learned map's second form, for keys that binary32 normalisation
+ *       collapses, keeps R11's model (the same 256 quantiles of the same
+ *       sample) but holds its breakpoints as keys: b[0] = min, b[P] = max,
+ *       b[j] = the sample key of rank j m / P, and r[s] = fl32(1 /
+ *       fl32(b[s+1] - b[s])) (0 for an empty piece).  A key's piece is the
+ *       last b[j] <= key among j = 1..P-1, and it is interpolated from its
+ *       piece's own lower key, frac = fl32(fl32(key - b[s]) * r[s]), clipped
+ *       to [0, 1 - 2^-24]; bucket = s * (k/P) + min(k/P - 1, floor(frac *
+ *       k/P)).  Monotone in the key inside a piece for the same reason as
+ *       R11, and across pieces because the pieces' buckets are ordered.
  */
 #include <math.h>
 #include <stdint.h>
