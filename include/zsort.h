@@ -250,8 +250,8 @@ int zsort_keys(uint64_t *keys, uint64_t n, zsort_stream_t stream);
  * with the s bits below it, orders like the key.  One stable zSort of
  * (window, input index); then only the keys in runs of equal windows (none
  * when the keys' top 64 significant bits differ, as for hashes) are sorted
- * by the bits below the window, run by run, in one segmented zSort of
- * those keys alone; then one gather of keys and payloads.  Keys that share
+ * by the bits below the window, run by run, in segmented zSorts of those
+ * keys alone (2^20 runs a launch); then one gather of keys and payloads.  Keys that share
  * windows in bulk (a few distinct high words over a 2^128 range) make the
  * second sort as long as the first.  The call waits for the stream once,
  * to read the size of the tied runs.  Scratch: 44 bytes per key (28 without

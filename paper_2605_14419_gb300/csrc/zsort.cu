@@ -788,6 +788,7 @@ __global__ void k128_window(const uint64_t *keys, const uint32_t *vals, unsigned
 // more counts as tied (low 32 bits) and, if it starts the run, as a run head
 // (high 32 bits).  TIE_PER consecutive elements per thread.
 constexpr int TIE_PER = 16;
+constexpr unsigned long long U128_RUNS_PER_LAUNCH = 1ull << 20;
 constexpr unsigned long long TIE_TILE = (unsigned long long)BLOCK * TIE_PER;
 __device__ __forceinline__ unsigned long long k128_tie_bits(const uint64_t *win, unsigned long long n,
                                                             unsigned long long i)
@@ -1133,7 +1134,11 @@ int zsort_pairs_u128(uint64_t *keys, uint32_t *vals, uint64_t n, const zsort_opt
             const unsigned int tg = (unsigned int)std::min<unsigned long long>(div_up(T, 256), 4096);
             k128_tie_emit<<<(unsigned int)nb, BLOCK, 0, st>>>(win, idx, rec, rs, n, bsum, W, ck, cv, pre, off);
             rc = cuda_err(cudaGetLastError());
-            if (rc == ZSORT_OK) rc = launch(ck, cv, T, off, G, o, st);
+            // at most U128_RUNS_PER_LAUNCH runs a launch, so that the
+            // workspace's per-segment bookkeeping stays bounded however the
+            // keys tie (the runs of one launch are a contiguous slice)
+            for (unsigned long long g0 = 0; rc == ZSORT_OK && g0 < G; g0 += U128_RUNS_PER_LAUNCH)
+                rc = launch(ck, cv, T, off + g0, std::min<unsigned long long>(U128_RUNS_PER_LAUNCH, G - g0), o, st);
             if (rc == ZSORT_OK) {
                 k128_tie_gather<<<tg, 256, 0, st>>>(cv, idx, T, tmp);
                 k128_tie_place<<<tg, 256, 0, st>>>(pre, tmp, T, idx);

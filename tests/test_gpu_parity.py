@@ -559,6 +559,24 @@ def test_u128_window_runs_resolved_below_the_window(s, nwin, dup):
     assert np.array_equal(v.cpu().numpy().view(np.uint32), order.astype(np.uint32))
 
 
+def test_u128_more_window_runs_than_one_launch_takes():
+    """1,057,674 runs of equal windows, more than the 2^20 runs one launch
+    takes (4 million keys over 2 million windows at shift 40): the runs are
+    sorted in two slices; the result is still numpy's stable lexsort on
+    (high, low)."""
+    n = 4_000_001
+    hi, lo = u128_window_case(n, 40, n // 2, 77, False)
+    words = np.empty(2 * n, dtype=np.uint64)
+    words[0::2], words[1::2] = lo, hi
+    k = torch.from_numpy(words.view(np.int64)).to(DEV)
+    v = torch.arange(n, dtype=torch.int32, device=DEV)
+    z.sort_pairs_u128(k, v)
+    order = np.lexsort((lo, hi))
+    got = k.cpu().numpy().view(np.uint64)
+    assert np.array_equal(got[0::2], lo[order]) and np.array_equal(got[1::2], hi[order])
+    assert np.array_equal(v.cpu().numpy().view(np.uint32), order.astype(np.uint32))
+
+
 def test_leaf_with_interleaved_repeated_keys_takes_the_network():
     """Leaves whose sub-buckets mix two adjacent keys, each repeated ~1500
     times in random order (the insertion sort's move budget runs out), plus
