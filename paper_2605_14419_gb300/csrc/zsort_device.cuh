@@ -66,6 +66,8 @@ enum TaskType : uint32_t {
                      // after both the statistics and the sample)
     T_SSTATS = 10    // large sub-array: statistics and Eq. 1 map from a sample (one CTA)
 };
+constexpr int WARP_DISTINCT_MAX = 32;  // stable leaf path: distinct keys a warp's counting sort takes
+constexpr uint32_t LEAF_INSERT_MAX = 16;  // stable leaf path: sub-buckets this short sorted by insertion
 constexpr uint32_t LOCAL_CLAIM = 8;  // stashed leaves taken per task (the next one is prefetched)
 constexpr uint32_t SUB_SAMPLE = 4096;     // keys of a sub-array's statistics sample
 
@@ -731,6 +733,8 @@ struct SmemTile {
 };
 static_assert(SC_STAGES <= KEY_STAGES, "one mbarrier per streamed tile buffer");
 static_assert(sizeof(LeafArea) <= sizeof(TileBuf) * SC_STAGES, "a leaf fits the tile buffers");
+static_assert(WARPS * (WARP_DISTINCT_MAX + 16) * 8 <= sizeof(LeafArea::cnt) && WARP_DISTINCT_MAX <= 32,
+              "the warps' distinct-key tables fit the leaf's sub-bucket counters");
 static_assert(sizeof(KeyRing) <= sizeof(TileBuf) * SC_STAGES, "the key stages fit the tile buffers");
 static_assert(sizeof(ChildList) <= sizeof(TileBuf) * SC_STAGES, "child lists fit the tile buffers");
 static_assert(sizeof(SmemTile) <= 112 * 1024, "two CTAs per SM");

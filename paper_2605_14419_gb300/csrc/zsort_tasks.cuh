@@ -2102,6 +2102,86 @@ __device__ __forceinline__ void finish_fast(SmemTile &s, unsigned long long *key
     }
 }
 
+// Stable order of the sub-bucket key/val[a, a+c) (staged in input order) by
+// one warp, when it holds at most WARP_DISTINCT_MAX distinct keys: the
+// distinct keys in ascending order (one warp minimum above the last, per
+// key), their counts and starts, then every pair placed in input order at
+// its key's running cursor -- a stable counting sort -- and written straight
+// to dk/dv at the same leaf positions.  Returns false, having written
+// nothing, when the sub-bucket holds more distinct keys.  dtab / dcur: the
+// warp's own shared memory (WARP_DISTINCT_MAX keys, as many cursors).
+template <bool KV>
+__device__ bool warp_distinct_sort(const unsigned long long *key, const uint32_t *val, uint32_t a, uint32_t c,
+                                   unsigned long long *dtab, uint32_t *dcur, uint64_t *dk, uint32_t *dv)
+{
+    const uint32_t full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    uint32_t D = 0;
+    unsigned long long last = 0;
+    for (;;) {
+        unsigned long long m = ~0ull;
+        bool any = false;
+        for (uint32_t j = lane; j < c; j += 32) {
+            const unsigned long long x = key[a + j];
+            if ((D == 0 || x > last) && (!any || x < m)) {
+                m = x;
+                any = true;
+            }
+        }
+        if (!__any_sync(full, any)) break;
+        if (D == (uint32_t)WARP_DISTINCT_MAX) return false;
+        unsigned long long mx = 0;
+        warp_minmax64(m, mx);  // lanes without a key offer ~0, never below a real one
+        if (lane == 0) dtab[D] = m;
+        last = m;
+        D++;
+    }
+    __syncwarp();
+    auto index_of = [&](unsigned long long x) {  // position of x among the D sorted keys
+        uint32_t lo = 0, hi = D - 1;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (dtab[mid] < x)
+                lo = mid + 1;
+            else
+                hi = mid;
+        }
+        return lo;
+    };
+    if (lane < (int)D) dcur[lane] = 0u;
+    __syncwarp();
+    for (uint32_t j = lane; j < c; j += 32) atomicAdd(&dcur[index_of(key[a + j])], 1u);
+    __syncwarp();
+    const uint32_t cnt = lane < (int)D ? dcur[lane] : 0u;
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(full, incl, o);
+        if (lane >= o) incl += y;
+    }
+    __syncwarp();
+    if (lane < (int)D) dcur[lane] = incl - cnt;  // start of each key's run
+    __syncwarp();
+    const uint32_t lt = (1u << lane) - 1u;
+    for (uint32_t j0 = 0; j0 < c; j0 += 32) {
+        const uint32_t j = j0 + lane;
+        const bool valid = j < c;
+        const unsigned long long x = valid ? key[a + j] : 0ull;
+        const uint32_t d = valid ? index_of(x) : 0xffffu;
+        const uint32_t peers = __match_any_sync(full, d) & __ballot_sync(full, valid);
+        const uint32_t base = valid ? dcur[d] : 0u;
+        __syncwarp();
+        if (valid && (peers & lt) == 0u) dcur[d] = base + __popc(peers);  // the lowest lane of the key advances it
+        __syncwarp();
+        if (valid) {
+            const uint32_t p = a + base + __popc(peers & lt);
+            __stcg(dk + p, x);
+            if (KV) __stcg(dv + p, val[a + j]);
+        }
+    }
+    return true;
+}
+
 // Stable leaf path, for leaves with a large sub-bucket (typically many equal
 // keys): sub-buckets by the range map placed in input order by the ballot
 // ranking, then insertion sort per sub-bucket (no moves among equal keys); a
@@ -2131,7 +2211,10 @@ __device__ __noinline__ void finish_stable(const Params &P, SmemTile &s, unsigne
             val[pos[i]] = v[i];
         }
     }
-    if (threadIdx.x == 0) s.flag = 0;
+    if (threadIdx.x == 0) {
+        s.flag = 0;
+        s.flag2 = 0;
+    }
     for (uint32_t q = threadIdx.x; q < M; q += BLOCK) s.hist[q] = 0;
     __syncthreads();
     // a sub-bucket is in order (stably: equal keys are in input order) unless
@@ -2145,26 +2228,43 @@ __device__ __noinline__ void finish_stable(const Params &P, SmemTile &s, unsigne
         }
     }
     __syncthreads();
-    // insertion sort (bounded moves) of each inverted sub-bucket; those that
-    // need more moves -- several distinct keys, each repeated many times --
-    // are listed and sorted by a CTA-wide network one after the other (an
-    // unfinished insertion sort keeps equal keys in input order, so sorting
-    // on the current position stays stable)
-    uint32_t *fail = s.bs;  // failed sub-buckets
-    for (uint32_t q = threadIdx.x; q < M; q += BLOCK) {
-        const uint32_t c = s.tcount[q];
-        if (c >= 2 && s.hist[q] && !insertion_sort_budget(key + s.tstart[q], val + s.tstart[q], c, 1024))
-            fail[atomicAdd(&s.flag, 1u)] = q;
+    uint32_t *inv = s.bs;       // inverted sub-buckets
+    uint32_t *fail = s.cursor;  // those left to the network
+    for (uint32_t q = threadIdx.x; q < M; q += BLOCK)
+        if (s.hist[q] && s.tcount[q] >= 2) inv[atomicAdd(&s.flag, 1u)] = q;
+    __syncthreads();
+    // each inverted sub-bucket: a short one by insertion (one lane), a longer
+    // one by its warp as a stable counting sort over its distinct keys,
+    // written straight to the output (hist = 2 marks it written); one with
+    // more than WARP_DISTINCT_MAX distinct keys goes to the network below.
+    // Several distinct keys, each repeated many times (the duplicate-heavy
+    // leaves of small Zipf arrays), are what made insertion run long.
+    const uint32_t ninv = s.flag;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long *dtab = reinterpret_cast<unsigned long long *>(s.u.la.cnt) + warp * (WARP_DISTINCT_MAX + 16);
+    uint32_t *dcur = reinterpret_cast<uint32_t *>(dtab + WARP_DISTINCT_MAX);
+    for (uint32_t f = warp; f < ninv; f += WARPS) {
+        const uint32_t q = inv[f], a = s.tstart[q], c = s.tcount[q];
+        if (c <= LEAF_INSERT_MAX) {
+            if (lane == 0) insertion_sort_budget(key + a, val + a, c, 0xffffffffu);
+        } else if (warp_distinct_sort<KV>(key, val, a, c, dtab, dcur, dk, dv)) {
+            if (lane == 0) s.hist[q] = 2u;
+        } else if (lane == 0) {
+            fail[atomicAdd(&s.flag2, 1u)] = q;
+        }
+        __syncwarp();
     }
     __syncthreads();
-    const uint32_t nfail = s.flag;
+    const uint32_t nfail = s.flag2;
     for (uint32_t f = 0; f < nfail; f++) {
         const uint32_t q = fail[f];
         bitonic_range(s, key, val, s.tstart[q], s.tcount[q]);
     }
     if (threadIdx.x == 0 && nfail) atomicAdd(&P.ctl->n_leaf_fb, 1ull);
     for (uint32_t p = threadIdx.x; p < len; p += BLOCK) {
-        __stcg(dk + p, key[p]);
+        const unsigned long long kp = key[p];
+        if (s.hist[leaf_sub(kp, mn, rshift, rmult)] == 2u) continue;  // written by its warp
+        __stcg(dk + p, kp);
         if (KV) __stcg(dv + p, val[p]);
     }
 }

@@ -577,19 +577,21 @@ def test_u128_more_window_runs_than_one_launch_takes():
     assert np.array_equal(v.cpu().numpy().view(np.uint32), order.astype(np.uint32))
 
 
-def test_leaf_with_interleaved_repeated_keys_takes_the_network():
-    """Leaves whose sub-buckets mix two adjacent keys, each repeated ~1500
-    times in random order (the insertion sort's move budget runs out), plus
-    a few far keys that widen the range: sorted by the per-sub-bucket
-    sorting network, stably."""
-    rng = np.random.default_rng(51)
+def _repeated_key_leaves(distinct, seed):
+    """40 leaves' worth of keys, far apart: in each, `distinct` adjacent keys
+    repeated ~3000 / distinct times in random order, plus a few far keys that
+    widen the leaf's range so that the adjacent keys share one sub-bucket."""
+    rng = np.random.default_rng(seed)
     parts = []
-    for g in range(40):  # 40 leaves' worth, far apart
+    for g in range(40):
         base = np.uint64(g) << np.uint64(56)
-        x = base + rng.integers(0, 2, 3000).astype(np.uint64) * np.uint64(1)
-        x[::997] = base + np.uint64(1 << 40)  # widen each leaf's range
+        x = base + rng.integers(0, distinct, 3000).astype(np.uint64)
+        x[::997] = base + np.uint64(1 << 40)
         parts.append(x)
-    keys = np.concatenate(parts)
+    return np.concatenate(parts)
+
+
+def _sort_and_fallbacks(keys):
     vals = inputs.index_payload(keys.size)
     k, v = to_dev(keys, vals)
     stream = torch.cuda.Stream()
@@ -599,7 +601,22 @@ def test_leaf_with_interleaved_repeated_keys_takes_the_network():
     ok, ov = oracle.zsort_pairs(keys, vals)
     assert np.array_equal(k.cpu().numpy().view(np.uint64), ok)
     assert np.array_equal(v.cpu().numpy().view(np.uint32), ov)
-    assert fb > 0
+    return fb
+
+
+@pytest.mark.parametrize("distinct", [2, 7, 32])
+def test_leaf_with_few_repeated_keys_takes_the_warp_counting_sort(distinct):
+    """Leaves whose sub-buckets mix up to 32 distinct keys, each repeated
+    many times in random order: sorted stably by a warp's counting sort over
+    the distinct keys, with no sorting network."""
+    assert _sort_and_fallbacks(_repeated_key_leaves(distinct, 51 + distinct)) == 0
+
+
+def test_leaf_with_many_repeated_keys_takes_the_network():
+    """Sub-buckets of 64 distinct keys, each repeated ~47 times in random
+    order: more than a warp's counting sort takes, so sorted by the
+    per-sub-bucket sorting network, stably."""
+    assert _sort_and_fallbacks(_repeated_key_leaves(64, 52)) > 0
 
 
 def _child_stress(n_bulk, n_run, n_out, seed):
