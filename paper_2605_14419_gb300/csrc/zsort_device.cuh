@@ -735,6 +735,9 @@ static_assert(SC_STAGES <= KEY_STAGES, "one mbarrier per streamed tile buffer");
 static_assert(sizeof(LeafArea) <= sizeof(TileBuf) * SC_STAGES, "a leaf fits the tile buffers");
 static_assert(WARPS * (WARP_DISTINCT_MAX + 16) * 8 <= sizeof(LeafArea::cnt) && WARP_DISTINCT_MAX <= 32,
               "the warps' distinct-key tables fit the leaf's sub-bucket counters");
+static_assert(offsetof(LeafArea, cnt) == offsetof(LeafArea, sidx) + sizeof(LeafArea::sidx) &&
+                  WARPS * NB_MAX * 4 <= sizeof(LeafArea::sidx) + sizeof(LeafArea::cnt),
+              "the stable leaf path's per-warp peer tables fit the contiguous sidx + cnt arrays");
 static_assert(sizeof(KeyRing) <= sizeof(TileBuf) * SC_STAGES, "the key stages fit the tile buffers");
 static_assert(sizeof(ChildList) <= sizeof(TileBuf) * SC_STAGES, "child lists fit the tile buffers");
 static_assert(sizeof(SmemTile) <= 112 * 1024, "two CTAs per SM");
@@ -1035,29 +1038,6 @@ __device__ __forceinline__ void rank_zero_warp(uint32_t nb, SmemTile &s)
     __syncwarp();
     for (uint32_t q = lane; q < nb / 8; q += 32) row[q] = make_uint4(0u, 0u, 0u, 0u);
     __syncwarp();
-}
-
-// Stable multisplit of one tile in one call (its own barriers).  On return
-// s.tcount / s.tstart hold the per-bucket counts and starts.
-template <int NI, int NBITS>
-__device__ void tile_rank(const uint32_t (&b)[NI], uint32_t (&pos)[NI], uint32_t nb, uint32_t cnt, SmemTile &s)
-{
-    rank_zero_warp(nb, s);
-    __syncthreads();
-    uint32_t peers[NI];
-    rank_peers<NI, NBITS>(b, cnt, peers);
-    rank_leaders<NI>(b, peers, pos, s);
-    __syncthreads();
-    rank_scan<false>(nb, s);
-    rank_place<NI>(b, pos, s);
-}
-
-// Bits of the ranking ballots for nb buckets (nb a power of two, 16..1024),
-// grouped so that few instantiations exist: 7 (<=128), 8, 9, 10.
-__device__ __forceinline__ int rank_bits(uint32_t nb)
-{
-    const int e = 31 - __clz((int)nb);
-    return e < 7 ? 7 : e;
 }
 
 // ------------------------------------------------------------ bulk copies

@@ -2203,7 +2203,20 @@ __device__ __noinline__ void finish_stable(const Params &P, SmemTile &s, unsigne
         v[i] = p < len ? val[p] : 0u;
         b[i] = p < len ? leaf_sub(x[i], mn, rshift, rmult) : 0u;
     }
-    tile_rank<LEAF_IPT, 9>(b, pos, M, len, s);
+    // stable multisplit of the leaf into its M sub-buckets: peers from a
+    // per-warp OR table (M words) in the leaf's position and counter arrays,
+    // which this path does not use until its network
+    rank_zero_warp(M, s);
+    __syncthreads();
+    {
+        uint32_t peers[LEAF_IPT];
+        uint32_t *tbl = reinterpret_cast<uint32_t *>(s.u.la.sidx) + (threadIdx.x >> 5) * NB_MAX;
+        rank_peers_tbl<LEAF_IPT>(b, len, tbl, M, peers);
+        rank_leaders<LEAF_IPT>(b, peers, pos, s);
+    }
+    __syncthreads();
+    rank_scan<false>(M, s);
+    rank_place<LEAF_IPT>(b, pos, s);
 #pragma unroll
     for (int i = 0; i < LEAF_IPT; i++) {
         if (pos[i] != INVALID) {
