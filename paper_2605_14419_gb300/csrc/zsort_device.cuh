@@ -858,14 +858,15 @@ __device__ __forceinline__ void warp_minmax64(unsigned long long &mn, unsigned l
 // Stable multisplit of one tile of N = BLOCK * NI elements, cnt of them
 // valid.  Element (warp w, slot i, lane l) is the tile's element
 // w*32*NI + i*32 + l, so (w, i, l) order is input order.  In each slot the
-// warp's lanes with equal buckets are found from NBITS ballots (one per bit
-// of the bucket id); their rank is the count of earlier equal lanes plus
-// the warp's running count for that bucket.  Warp prefixes per bucket and a
-// block scan over buckets then give each element its position in the tile
-// ordered by (bucket, input position).  Buckets must be below 2^NBITS;
-// lanes past cnt are ignored (their bucket value does not matter).
-// On return s.tcount / s.tstart hold the per-bucket counts and starts.
-// The ranking in steps, so that a tile loop can place its own barriers:
+// warp's lanes with equal buckets are found from a per-warp shared-memory OR
+// table of the buckets (rank_peers_tbl), or, where no room for the table
+// exists, from NBITS ballots, one per bit of the bucket id (rank_peers);
+// their rank is the count of earlier equal lanes plus the warp's running
+// count for that bucket.  Warp prefixes per bucket and a block scan over
+// buckets then give each element its position in the tile ordered by
+// (bucket, input position).  Lanes past cnt are ignored (their bucket value
+// does not matter).  The ranking in steps, so that a tile loop can place its
+// own barriers:
 //   rank_peers    (registers)  lanes of the warp with an equal bucket, per slot
 //   rank_leaders  (smem)       the group leader reads and advances the warp's
 //                              counter of the bucket (row warp of wcnt, so the

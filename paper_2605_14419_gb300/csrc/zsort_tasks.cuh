@@ -627,7 +627,8 @@ __device__ __noinline__ void hist_stream(const Params &P, SmemTile &s, Pipe &pp,
 
 // Stable scatter of [start, start+len) of a (sub)array whose map is in s.map
 // and whose running bucket cursors are in s.cursor.  Per tile: rank the
-// pairs by (bucket, position) with ballots, stage them in that order in the
+// pairs by (bucket, position) with the warps' peer tables (ballots where a
+// table does not fit), stage them in that order in the
 // tile's own buffer with their buckets, then write each bucket's run at its
 // cursor (coalesced within runs; a staged bucket is cheaper to read back
 // than any map is to recompute).  Tiles stream through a ring of SC_STAGES
@@ -2183,9 +2184,11 @@ __device__ bool warp_distinct_sort(const unsigned long long *key, const uint32_t
 }
 
 // Stable leaf path, for leaves with a large sub-bucket (typically many equal
-// keys): sub-buckets by the range map placed in input order by the ballot
-// ranking, then insertion sort per sub-bucket (no moves among equal keys); a
-// bitonic sort on (key, position) if a sub-bucket needs too many moves.
+// keys): sub-buckets by the range map, placed in input order by the
+// multisplit; then every sub-bucket with an out-of-order neighbour pair is
+// sorted by one warp -- insertion when short, else a stable counting sort
+// over its distinct keys -- and only one with more than WARP_DISTINCT_MAX
+// distinct keys by a bitonic network on (key, position).
 template <bool KV>
 __device__ __noinline__ void finish_stable(const Params &P, SmemTile &s, unsigned long long *key, uint32_t *val,
                                            uint32_t len, unsigned long long mn, unsigned long long mx,
